@@ -1,0 +1,374 @@
+"""Benchmark of the lattice Boltzmann time step on GB300.
+
+Default workload: the FV body-force channel, 256 x 512 cells, tanh wall
+refinement (delta = 2) on y, FP32 arithmetic on f - w storage, Re = 10.
+One bench step = one FV time step (one fused kernel launch).  The state is
+9.4 MB, far below the 129 MB L2, so a 256 MiB buffer is written between timed
+steps and each step is timed alone with CUDA events on the launching stream.
+
+Extra lines in the same JSON object (not the headline): ST on 8192^2 (FP32,
+BF16 and FP16 deviation storage; state larger than L2), FV on 4096^2 FP32 and
+FV thermal RB 1024^2 with FP16 storage.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & % HBM roofline (FV and ST) vs FP64 oracle error; serving p50/p99 latency"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int, period_ms: int = 100):
+        self.gpu, self.period = gpu_index, period_ms
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", str(self.period)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 6:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[2:6]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------- GPU --
+
+def make_grid(lb, w, stream):
+    grid = dict(w.grid)
+    store = grid.pop("store")
+    g = lb.Grid(store=store, stream=stream, **grid)
+    g.init(**w.params, **w.init)
+    return g
+
+
+def time_steps(lb, torch, g, scheme, steps, warmup, flush=None):
+    """Per-step CUDA-event durations (ms) of `steps` single-step launches."""
+    step = lb.lb_step_fv if scheme == "fv" else lb.lb_step_st
+    for _ in range(warmup):
+        step(g.handle, 1)
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(steps)]
+    n0 = lb.lb_kernel_launches()
+    for a, b in evs:
+        if flush is not None:
+            flush.zero_()
+        a.record()
+        step(g.handle, 1)
+        b.record()
+    torch.cuda.synchronize()
+    launches = lb.lb_kernel_launches() - n0
+    return [a.elapsed_time(b) for a, b in evs], launches
+
+
+def roofline(bytes_per_step, mean_ms, peak, peak_kind, traffic=None):
+    achieved = bytes_per_step / (mean_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": traffic,
+            "peak_source": f"{peak_kind} hbm_gbs"}
+
+
+def extra_lines(lb, torch, cfg, stream, peak, peak_kind, flush):
+    out = {}
+    specs = [("st8192_f32", cfg.st_sweep(8192, lb.LB_STORE_F32), 20, None),
+             ("st8192_bf16dev", cfg.st_sweep(8192, lb.LB_STORE_BF16DEV), 20, None),
+             ("st8192_f16dev", cfg.st_sweep(8192, lb.LB_STORE_F16DEV), 20, None),
+             ("fv4096_f32", _fv_big(cfg, 4096), 10, None),
+             ("fv_rb1024_f16dev", cfg.rayleigh_benard(1024, 1e8), 20, flush)]
+    for name, w, k, fl in specs:
+        g = make_grid(lb, w, stream)
+        ms, _ = time_steps(lb, torch, g, w.scheme, k, 3, fl)
+        mean = sum(ms) / len(ms)
+        bpc = cfg.bytes_per_cell(w.grid["store"], w.grid.get("thermal", False))
+        out[name] = {"mlups": round(w.cells / (mean * 1e-3) / 1e6, 1), "ms_per_step": round(mean, 5),
+                     "bytes_per_cell": bpc,
+                     "roofline": roofline(bpc * w.cells, mean, peak, peak_kind),
+                     "cells": w.cells, "l2": "flushed" if fl is not None else "state > L2"}
+        g.close()
+        torch.cuda.empty_cache()
+    return out
+
+
+def _fv_big(cfg, n):
+    """Periodic n x n FV TGV, FP32 (flow only), dt = 0.5: FV kernel at scale."""
+    from paper_1505_03271_gb300 import LB_INIT_TGV, LB_STORE_F32
+    return cfg.Workload("fv%d" % n, dict(nx=n, ny=n, store=LB_STORE_F32),
+                        dict(tau=0.3, dt=0.5), dict(kind=LB_INIT_TGV, u0=0.01), 10, "fv")
+
+
+def e2e_measure(lb, torch, w, stream, reps=3, inner=1000):
+    """Through the public API with host buffers: per iteration, upload rho, ux,
+    uy from pinned host memory (lb_init FIELDS), advance `inner` FV steps,
+    read u_x back to host (lb_moments)."""
+    nx, ny = w.grid["nx"], w.grid["ny"]
+    grid = dict(w.grid)
+    store = grid.pop("store")
+    g = lb.Grid(store=store, stream=stream, **grid)
+    pin = lambda: torch.empty((ny, nx), dtype=torch.float64, pin_memory=True).numpy()
+    rho, ux, uy, out = pin(), pin(), pin(), pin()
+    from paper_1505_03271_gb300 import configs as cfg
+    xi = cfg.faces(ny, w.grid["ly"], w.grid["sy"], w.grid["stretch_y"])
+    yc = 0.5 * (xi[1:] + xi[:-1])
+    rho[:] = 1.0
+    ux[:] = (4 * w.init["u0"] * yc * (w.grid["ly"] - yc) / w.grid["ly"] ** 2)[:, None]
+    uy[:] = 0.0
+    times = []
+    for r in range(reps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.init(**w.params, kind=lb.LB_INIT_FIELDS, rho=rho, ux=ux, uy=uy)
+        lb.lb_step_fv(g.handle, inner)
+        lb.lb_moments(g.handle, None, out, None, None)
+        t1 = time.perf_counter()
+        if r > 0:
+            times.append(t1 - t0)
+    g.close()
+    t = min(times)
+    return {"value": round(w.cells * inner / t / 1e6, 1), "unit": "MLUPS",
+            "h2d_bytes_per_step": 3 * 8 * nx * ny, "d2h_bytes_per_step": 8 * nx * ny,
+            "lb_steps_per_step": inner,
+            "note": "step = lb_init from pinned host rho,ux,uy + %d FV steps + u_x to host" % inner}
+
+
+# ------------------------------------------------------------------ oracle --
+
+def oracle_sample(w, budget_s=15.0, steps_cap=None):
+    """Oracle FV/ST steps on the workload for about budget_s seconds."""
+    import oracle as O
+    threads = os.cpu_count() or 1
+    O.set_threads(threads)
+    grid = dict(w.grid)
+    grid.pop("store")
+    r = O.RefGrid(grid["nx"], grid["ny"], grid.get("lx"), grid.get("ly"), grid.get("sx", 0),
+                  grid.get("sy", 0), grid.get("stretch_x", 0.0), grid.get("stretch_y", 0.0),
+                  grid.get("bcx", 0), grid.get("bcy", 0), grid.get("thermal", False))
+    r.set_params(**w.params)
+    kind = {0: O.INIT_TGV, 1: O.INIT_SHEAR, 2: O.INIT_POISEUILLE, 3: O.INIT_RB}[w.init["kind"]]
+    r.init_preset(kind, w.init.get("u0", 0.0), w.init.get("amp", 0.0), w.init.get("mode", 1),
+                  w.init.get("seed", 0))
+    step = r.step_fv if w.scheme == "fv" else r.step_st
+    done, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < budget_s and (steps_cap is None or done < steps_cap):
+        step(1)
+        done += 1
+    el = time.perf_counter() - t0
+    return r, done, el, threads
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1505_03271_gb300 import configs as cfg
+    w = cfg.channel()
+    import oracle as O
+    O.build()
+    O.set_threads(os.cpu_count() or 1)
+    grid = dict(w.grid)
+    grid.pop("store")
+    r = O.RefGrid(grid["nx"], grid["ny"], grid["lx"], grid["ly"], 0, grid["sy"], 0.0,
+                  grid["stretch_y"], 0, grid["bcy"], False)
+    r.set_params(**w.params)
+    r.init_preset(O.INIT_POISEUILLE, w.init["u0"])
+    # each reference step: one oracle FV step of the full channel
+    for _ in range(args.warmup):
+        r.step_fv(1)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r.step_fv(1)
+    el = time.perf_counter() - t0
+    v = w.cells * args.steps / el / 1e6
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "MLUPS",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(el / args.steps * 1e3, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": _config(w),
+            "cpu_baseline": {"value": round(v, 3), "unit": "MLUPS", "cores": O.get_threads(),
+                             "kind": "oracle", "sample": "%d full FV steps of the channel" % args.steps},
+            "e2e": {"value": round(v, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def case_workload(cfg, name):
+    """Workloads that --case selects (the default, 'channel', is the headline)."""
+    import paper_1505_03271_gb300 as lb
+    table = {
+        "channel": lambda: cfg.channel(),
+        "st8192": lambda: cfg.st_sweep(8192, lb.LB_STORE_F32),
+        "st4096": lambda: cfg.st_sweep(4096, lb.LB_STORE_F32),
+        "st4096_f16dev": lambda: cfg.st_sweep(4096, lb.LB_STORE_F16DEV),
+        "fv4096": lambda: _fv_big(cfg, 4096),
+        "fv2048": lambda: _fv_big(cfg, 2048),
+        "rb1024": lambda: cfg.rayleigh_benard(1024, 1e8),
+    }
+    return table[name]()
+
+
+def _config(w, case="channel"):
+    if case != "channel":
+        return {"workload": w.name, "cells": w.cells, "scheme": w.scheme,
+                "store": w.grid["store"], "thermal": bool(w.grid.get("thermal", False)),
+                "l2": "flushed: 256 MiB write between timed steps"}
+    return {"workload": "FV channel %dx%d, tanh delta=2 walls on y, tau=0.2 (ST tau~=0.7), Re=10, "
+                        "FP32 math on f-w storage (BASELINE configs[1])" % (w.grid["nx"], w.grid["ny"]),
+            "cells": w.cells, "scheme": "fv semi-implicit + Heun + QUICK",
+            "dt": round(w.params["dt"], 6), "l2": "flushed: 256 MiB write between timed steps"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extra", action="store_true", help="headline only (for profiling)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
+    ap.add_argument("--case", default="channel",
+                    help="workload to time: channel (headline), st8192, st4096, st4096_f16dev, "
+                         "fv4096, fv2048, rb1024")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import paper_1505_03271_gb300 as lb
+    from paper_1505_03271_gb300 import configs as cfg
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    lb.load()
+    stream = torch.cuda.current_stream().cuda_stream
+    peak, peak_kind = load_peaks()
+    w = case_workload(cfg, args.case)
+    g = make_grid(lb, w, stream)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]) if \
+        os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local
+    barrier()
+    with ClockSampler(gpu_index) as clk:
+        ms, launches = time_steps(lb, torch, g, w.scheme, args.steps, args.warmup, flush)
+    barrier()
+    total_s = sum(ms) * 1e-3
+    if dist is not None:
+        t = torch.tensor([total_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    mean_ms = total_s * 1e3 / args.steps
+    value = w.cells * args.steps * world / total_s / 1e6
+    bpc = cfg.bytes_per_cell(w.grid["store"], w.grid.get("thermal", False))
+    dtype = "f64" if w.grid["store"] == lb.LB_STORE_F64 else "f32"
+    line = {"metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(mean_ms, 5),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+            "data": "synthetic", "config": _config(w, args.case), "gpu_launches": launches,
+            "roofline": roofline(bpc * w.cells, mean_ms, peak, peak_kind),
+            "clocks": clk.summary()}
+    line["config"]["parallelism"] = "replicas" if world > 1 else "single"
+    if not args.no_extra and args.case == "channel":
+        line["e2e"] = e2e_measure(lb, torch, w, stream)
+        line["extra"] = extra_lines(lb, torch, cfg, stream, peak, peak_kind, flush)
+    if rank == 0 and world == 1 and not args.no_cpu and args.case == "channel":
+        import oracle as O
+        O.build()
+        r, done, el, thr = oracle_sample(w, budget_s=15.0)
+        # error of the GPU against the oracle after the same number of steps
+        g2 = make_grid(lb, w, stream)
+        lb.lb_step_fv(g2.handle, done)
+        _, ux, uy, _ = g2.moments()
+        _, vx, vy, _ = r.moments()
+        err = float(np.sqrt(((ux - vx) ** 2 + (uy - vy) ** 2).sum() / (vx**2 + vy**2).sum()))
+        line["cpu_baseline"] = {"value": round(w.cells * done / el / 1e6, 3), "unit": "MLUPS",
+                                "cores": thr, "kind": "oracle",
+                                "sample": "%d FV steps of the full channel (%.1f s)" % (done, el)}
+        line["oracle_error"] = {"rel_l2_u": err, "steps": done}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,179 @@
+/*
+ * lb.h -- C ABI of the GB300 lattice Boltzmann library (libpaper_gb300.so).
+ *
+ * The library advances a two-dimensional D2Q9 lattice Boltzmann state by the
+ * two time-integration schemes of Shrestha, Mompean & Calzavarini,
+ * "Finite Volume vs. Streaming-based Lattice Boltzmann algorithm for
+ * fluid-dynamics simulations: a one-to-one accuracy and performance study"
+ * (arXiv:1505.03271):
+ *   - the finite-volume (FV) step: QUICK face fluxes on a stretched Cartesian
+ *     grid, semi-implicit BGK collision and Heun predictor-corrector
+ *     advection (Sec. II B, Eqs. (fv), (semi), (semi-heun));
+ *   - the streaming (ST) step: fused collide-and-stream on the uniform unit
+ *     lattice (Sec. II A, Eq. (ST)),
+ * for the flow populations f and, optionally, the thermal populations g of the
+ * double-population model with Boussinesq buoyancy (Sec. IV, Eq. (LBg)).
+ *
+ * General conventions
+ *   - Every call returns an lb_status and never aborts.  On failure
+ *     lb_last_error() returns a message (per calling thread).  A failed call
+ *     leaves the grid as it was, except LB_ERR_UNSTABLE (see lb_conservation).
+ *   - The library owns all device memory of a grid; callers own every host
+ *     array they pass.  Host arrays are row-major [ny][nx] (x fastest);
+ *     population arrays are [9][ny][nx], population index slowest, in the
+ *     D2Q9 order c_0=(0,0), c_1..4=(1,0),(0,1),(-1,0),(0,-1),
+ *     c_5..8=(1,1),(-1,1),(-1,-1),(1,-1).
+ *   - Step calls are asynchronous on the grid's CUDA stream; calls that return
+ *     host data synchronise that stream.
+ *   - Units: lattice units, c_s^2 = 1/3.  lb_params.tau is the physical
+ *     relaxation time, nu = tau c_s^2 (Sec. II, below Eq. (LB)); the schemes
+ *     relax with tau~ = tau + dt/2 (Sec. II A, below Eq. (ST)).
+ *   - The y axis carries the plates of a thermal grid: T_bot at y = 0 and
+ *     T_top at y = ly; gravity points to -y.
+ */
+#ifndef LB_H
+#define LB_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lb_grid lb_grid; /* opaque, owned by the library */
+
+typedef enum {
+    LB_OK = 0,
+    LB_ERR_ARG = 1,      /* invalid argument or unsupported combination       */
+    LB_ERR_OOM = 2,      /* device or host allocation failed                   */
+    LB_ERR_CUDA = 3,     /* a CUDA call failed (message has the CUDA error)     */
+    LB_ERR_STATE = 4,    /* call not valid in the grid's current state          */
+    LB_ERR_UNSTABLE = 5, /* non-finite values found: the run has diverged       */
+    LB_ERR_TIMEOUT = 6   /* a bounded device-side wait gave up                  */
+} lb_status;
+
+typedef enum { LB_AXIS_UNIFORM = 0, LB_AXIS_TANH = 1, LB_AXIS_SINH = 2 } lb_spacing;
+typedef enum { LB_BC_PERIODIC = 0, LB_BC_WALLS = 1 } lb_bc;
+typedef enum {
+    LB_STORE_F64 = 0,    /* FP64 storage, FP64 arithmetic                      */
+    LB_STORE_F32 = 1,    /* FP32 storage of f - w (and g - w T0), FP32 math    */
+    LB_STORE_F16DEV = 2, /* FP16 storage of f - w (and g - w T0), FP32 math    */
+    LB_STORE_BF16DEV = 3 /* BF16 storage of f - w (and g - w T0), FP32 math    */
+} lb_store;
+
+/* Grid description.  Face coordinates of each axis follow Eq. (grids) of
+ * Sec. III B: uniform xi_i = i L / n; tanh xi_i = L/2 (1 + tanh((2i/n - 1)
+ * delta) / tanh(delta)) with stretch = delta (the paper's s1 = tanh(delta));
+ * sinh with stretch = s2 and n even.  Cell centres are the face midpoints.
+ * Walls (LB_BC_WALLS) sit on the first and last face of that axis.        */
+typedef struct {
+    int nx, ny;          /* cells per axis, >= 1 (>= 2 on a wall axis)         */
+    double lx, ly;       /* domain lengths                                     */
+    int sx, sy;          /* lb_spacing per axis                                */
+    double stretch_x, stretch_y;
+    int bcx, bcy;        /* lb_bc per axis; thermal grids need bcx periodic     */
+    int thermal;         /* 0: flow only; 1: flow + thermal populations        */
+    int store;           /* lb_store                                           */
+    void* cuda_stream;   /* cudaStream_t to enqueue on; NULL = default stream  */
+} lb_grid_desc;
+
+/* Physical parameters (Sec. II, Eq. (LB); Sec. IV, Eq. (LBg) and buoyancy
+ * a = -beta (T - T0) g with g = -grav y^).                                  */
+typedef struct {
+    double tau, dt, tau_g;   /* relaxation times (physical) and time step       */
+    double ax, ay;           /* external acceleration                          */
+    double beta, grav;       /* thermal expansion and gravity: a_y += beta grav (T - T0) */
+    double T0, T_bot, T_top; /* reference temperature, plate temperatures      */
+} lb_params;
+
+typedef enum {
+    LB_INIT_TGV = 0,        /* Taylor-Green vortex of amplitude u0; if amp != 0 a
+                               shear wave amp sin(2 pi mode y / ly) is added to u_x */
+    LB_INIT_SHEAR = 1,      /* u_x = amp sin(2 pi mode y / ly) (Sec. III A)        */
+    LB_INIT_POISEUILLE = 2, /* u_x = 4 u0 y (ly - y) / ly^2 (Sec. III B)           */
+    LB_INIT_RB = 3,         /* rest, linear conductive T, barometric rho, plus the
+                               seeded perturbation amp (T_bot - T_top)(2U - 1) (Sec. IV) */
+    LB_INIT_FIELDS = 4      /* from host arrays rho, ux, uy, T                     */
+} lb_init_kind;
+
+typedef struct {
+    int kind;                 /* lb_init_kind                                   */
+    int mode;                 /* shear-wave mode number                         */
+    double u0, amp;
+    unsigned long long seed;  /* RB perturbation: U = SplitMix64(seed ^ (j nx + i)) */
+    const double *rho, *ux, *uy, *T; /* LB_INIT_FIELDS: host [ny][nx]; NULL = 1, 0, 0, T0 */
+} lb_init_desc;
+
+/* Create a grid: allocates two population buffers per population set (the
+ * state and the next state), the 1-D metric of each axis (face weights of
+ * the QUICK interpolation, Sec. II B 3) and reduction scratch.
+ * LB_ERR_ARG on an invalid description, LB_ERR_OOM if device memory runs out.
+ * *out is written only on success. */
+lb_status lb_create_grid(const lb_grid_desc* desc, lb_grid** out);
+
+/* Set parameters and initial state: f~ = f_eq(rho, u) - dt/2 F (Appendix A,
+ * tilded variables at equilibrium) and g~ = (T/rho) f_eq (Eq. (LBg)).
+ * Clears the poisoned flag.  LB_ERR_ARG on bad parameters (tau <= 0,
+ * dt <= 0, a thermal preset on a flow-only grid, NULL arrays where needed). */
+lb_status lb_init(lb_grid* grid, const lb_params* params, const lb_init_desc* init);
+
+/* Advance nsteps FV time steps (Sec. II B 2, Eq. (semi-heun)): the advected
+ * field h = f~ + dt/(2 tau~)(f_eq - f~) + dt/2 F of Eq. (semi) is
+ * interpolated to the faces by QUICK (Sec. II B 3), walls use the double
+ * reflection of Sec. II B 5 on h (thermal field: anti-reflection through
+ * T_wall), the predictor f~* is Eq. (semi) and the corrector averages the
+ * two flux divergences.  One fused kernel launch per step.
+ * LB_ERR_STATE if the grid has no parameters or is poisoned. */
+lb_status lb_step_fv(lb_grid* grid, int nsteps);
+
+/* Advance nsteps ST time steps, Eq. (ST) with dt = dx = 1: collide and push
+ * each population to its neighbour; walls use half-way bounce-back (f) and
+ * anti-bounce-back through the plate temperature (g).  Requires uniform axes
+ * with unit spacing and dt = 1 (LB_ERR_ARG otherwise), since streaming ties
+ * the mesh to the lattice (Sec. II A).  One kernel launch per step. */
+lb_status lb_step_st(lb_grid* grid, int nsteps);
+
+/* Macroscopic fields: rho = sum f~, u = sum c f~ / rho + dt/2 a (Sec. II B 4),
+ * T = sum g~ (Eq. (LBg)).  Host outputs [ny][nx]; any may be NULL. Synchronous. */
+lb_status lb_moments(lb_grid* grid, double* rho, double* ux, double* uy, double* T);
+
+/* Volume integrals with FP64 accumulation: sum V rho, sum V rho u_x,
+ * sum V rho u_y, sum V T (V = dx_i dy_j).  Synchronous.  If any is not
+ * finite the grid is marked poisoned and LB_ERR_UNSTABLE is returned (the
+ * stability limits of Sec. III C were exceeded); lb_init clears the mark. */
+lb_status lb_conservation(lb_grid* grid, double* mass, double* momx, double* momy, double* heat);
+
+/* Nusselt numbers of a thermal grid (Sec. IV): volume
+ * Nu = 1 + H <u_y (T - T0)>_V / (kappa (T_bot - T_top)), kappa = tau_g c_s^2;
+ * and at each plate from the second-order one-sided gradient of the
+ * x-averaged temperature through the wall value and the first two nodes.
+ * LB_ERR_STATE on a flow-only grid.  Synchronous. */
+lb_status lb_nusselt(lb_grid* grid, double* nu_vol, double* nu_bot, double* nu_top);
+
+/* Copy the tilded populations from/to host FP64 arrays [9][ny][nx]
+ * (g may be NULL; it is required on lb_set_populations of a thermal grid
+ * unless only f is to change).  The copy rounds to the grid's storage type.
+ * Setting populations requires parameters (lb_init first). Synchronous. */
+lb_status lb_set_populations(lb_grid* grid, const double* f, const double* g);
+lb_status lb_get_populations(lb_grid* grid, double* f, double* g);
+
+/* Copy a w x h window of the populations, starting at cell (x0, y0), to host
+ * FP64 arrays [9][h][w] (g may be NULL).  Indices wrap modulo nx, ny, so a
+ * window may cross a periodic edge.  Lets callers sample grids too large to
+ * copy whole.  LB_ERR_ARG if w or h is < 1 or larger than the grid. */
+lb_status lb_get_window(lb_grid* grid, int x0, int y0, int w, int h, double* f, double* g);
+
+/* Wait for all work queued on the grid's stream. */
+lb_status lb_sync(lb_grid* grid);
+
+/* Free the grid and its device memory (NULL is a no-op). */
+lb_status lb_destroy(lb_grid* grid);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char* lb_last_error(void);
+
+/* Number of kernels this library has launched since it was loaded. */
+unsigned long long lb_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LB_H */

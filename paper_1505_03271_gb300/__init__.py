@@ -1,0 +1,277 @@
+"""GB300 lattice Boltzmann library: FV (QUICK + semi-implicit + Heun) and ST
+(collide-and-stream) time steps of arXiv:1505.03271 as CUDA kernels behind
+the C ABI of ``include/lb.h``.
+
+This module is the thin ctypes binding: it marshals arguments and raises
+``LBError`` on a non-zero status.  Every step of the computation runs in the
+CUDA library; there is no CPU path.  Loading fails loudly if the library
+cannot be built or loaded.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import _build
+
+Q = 9
+
+LB_OK, LB_ERR_ARG, LB_ERR_OOM, LB_ERR_CUDA, LB_ERR_STATE, LB_ERR_UNSTABLE, LB_ERR_TIMEOUT = range(7)
+LB_AXIS_UNIFORM, LB_AXIS_TANH, LB_AXIS_SINH = 0, 1, 2
+LB_BC_PERIODIC, LB_BC_WALLS = 0, 1
+LB_STORE_F64, LB_STORE_F32, LB_STORE_F16DEV, LB_STORE_BF16DEV = 0, 1, 2, 3
+LB_INIT_TGV, LB_INIT_SHEAR, LB_INIT_POISEUILLE, LB_INIT_RB, LB_INIT_FIELDS = 0, 1, 2, 3, 4
+
+STORE_NAMES = {"f64": LB_STORE_F64, "f32": LB_STORE_F32, "f16dev": LB_STORE_F16DEV,
+               "bf16dev": LB_STORE_BF16DEV}
+STORE_BYTES = {LB_STORE_F64: 8, LB_STORE_F32: 4, LB_STORE_F16DEV: 2, LB_STORE_BF16DEV: 2}
+
+
+class LBError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"lb status {status}: {msg}")
+        self.status = status
+
+
+class lb_grid_desc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("lx", C.c_double), ("ly", C.c_double),
+                ("sx", C.c_int), ("sy", C.c_int), ("stretch_x", C.c_double),
+                ("stretch_y", C.c_double), ("bcx", C.c_int), ("bcy", C.c_int),
+                ("thermal", C.c_int), ("store", C.c_int), ("cuda_stream", C.c_void_p)]
+
+
+class lb_params(C.Structure):
+    _fields_ = [("tau", C.c_double), ("dt", C.c_double), ("tau_g", C.c_double),
+                ("ax", C.c_double), ("ay", C.c_double), ("beta", C.c_double),
+                ("grav", C.c_double), ("T0", C.c_double), ("T_bot", C.c_double),
+                ("T_top", C.c_double)]
+
+
+_DP = C.POINTER(C.c_double)
+
+
+class lb_init_desc(C.Structure):
+    _fields_ = [("kind", C.c_int), ("mode", C.c_int), ("u0", C.c_double), ("amp", C.c_double),
+                ("seed", C.c_ulonglong), ("rho", _DP), ("ux", _DP), ("uy", _DP), ("T", _DP)]
+
+
+SYMBOLS = ["lb_create_grid", "lb_init", "lb_step_fv", "lb_step_st", "lb_moments",
+           "lb_conservation", "lb_nusselt", "lb_set_populations", "lb_get_populations",
+           "lb_get_window", "lb_sync", "lb_destroy", "lb_last_error", "lb_kernel_launches"]
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build: bool = True) -> C.CDLL:
+    """Load (building first if it is stale) the CUDA library."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"CUDA library missing: {_build.LIB} (run __graft_entry__.build())")
+    L = C.CDLL(_build.LIB)
+    G = C.c_void_p
+    L.lb_create_grid.argtypes = [C.POINTER(lb_grid_desc), C.POINTER(G)]
+    L.lb_init.argtypes = [G, C.POINTER(lb_params), C.POINTER(lb_init_desc)]
+    L.lb_step_fv.argtypes = [G, C.c_int]
+    L.lb_step_st.argtypes = [G, C.c_int]
+    L.lb_moments.argtypes = [G, _DP, _DP, _DP, _DP]
+    L.lb_conservation.argtypes = [G, _DP, _DP, _DP, _DP]
+    L.lb_nusselt.argtypes = [G, _DP, _DP, _DP]
+    L.lb_set_populations.argtypes = [G, _DP, _DP]
+    L.lb_get_populations.argtypes = [G, _DP, _DP]
+    L.lb_get_window.argtypes = [G, C.c_int, C.c_int, C.c_int, C.c_int, _DP, _DP]
+    L.lb_sync.argtypes = [G]
+    L.lb_destroy.argtypes = [G]
+    L.lb_last_error.restype = C.c_char_p
+    L.lb_kernel_launches.restype = C.c_ulonglong
+    for name in SYMBOLS:
+        if name not in ("lb_last_error", "lb_kernel_launches"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def _check(status: int) -> None:
+    if status != LB_OK:
+        raise LBError(status, _lib.lb_last_error().decode())
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(_DP)
+
+
+def _c64(a, shape=None):
+    if a is None:
+        return None
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if shape is not None and a.shape != shape:
+        a = a.reshape(shape)
+    return a
+
+
+# ---------------------------------------------------------------- C names --
+
+def lb_create_grid(desc: lb_grid_desc) -> C.c_void_p:
+    h = C.c_void_p()
+    _check(load().lb_create_grid(C.byref(desc), C.byref(h)))
+    return h
+
+
+def lb_init(grid, params: lb_params, init: lb_init_desc) -> None:
+    _check(load().lb_init(grid, C.byref(params), C.byref(init)))
+
+
+def lb_step_fv(grid, nsteps: int) -> None:
+    _check(load().lb_step_fv(grid, int(nsteps)))
+
+
+def lb_step_st(grid, nsteps: int) -> None:
+    _check(load().lb_step_st(grid, int(nsteps)))
+
+
+def lb_moments(grid, rho, ux, uy, T) -> None:
+    _check(load().lb_moments(grid, _ptr(rho), _ptr(ux), _ptr(uy), _ptr(T)))
+
+
+def lb_conservation(grid):
+    v = [C.c_double() for _ in range(4)]
+    _check(load().lb_conservation(grid, *[C.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+def lb_nusselt(grid):
+    v = [C.c_double() for _ in range(3)]
+    _check(load().lb_nusselt(grid, *[C.byref(x) for x in v]))
+    return tuple(x.value for x in v)
+
+
+def lb_set_populations(grid, f, g) -> None:
+    _check(load().lb_set_populations(grid, _ptr(f), _ptr(g)))
+
+
+def lb_get_populations(grid, f, g) -> None:
+    _check(load().lb_get_populations(grid, _ptr(f), _ptr(g)))
+
+
+def lb_get_window(grid, x0, y0, w, h, f, g) -> None:
+    _check(load().lb_get_window(grid, int(x0), int(y0), int(w), int(h), _ptr(f), _ptr(g)))
+
+
+def lb_sync(grid) -> None:
+    _check(load().lb_sync(grid))
+
+
+def lb_destroy(grid) -> None:
+    _check(load().lb_destroy(grid))
+
+
+def lb_last_error() -> str:
+    return load().lb_last_error().decode()
+
+
+def lb_kernel_launches() -> int:
+    return int(load().lb_kernel_launches())
+
+
+# ------------------------------------------------------- convenience class --
+
+def current_stream_handle():
+    """Handle of torch's current CUDA stream (PyTorch provides the streams)."""
+    import torch
+    return torch.cuda.current_stream().cuda_stream
+
+
+class Grid:
+    """A grid on the GPU.  Arrays returned are host numpy FP64 [ny, nx]."""
+
+    def __init__(self, nx, ny, lx=None, ly=None, sx=LB_AXIS_UNIFORM, sy=LB_AXIS_UNIFORM,
+                 stretch_x=0.0, stretch_y=0.0, bcx=LB_BC_PERIODIC, bcy=LB_BC_PERIODIC,
+                 thermal=False, store=LB_STORE_F32, stream=None):
+        if isinstance(store, str):
+            store = STORE_NAMES[store]
+        if stream is None:
+            stream = current_stream_handle()
+        self.desc = lb_grid_desc(int(nx), int(ny), float(nx if lx is None else lx),
+                                 float(ny if ly is None else ly), int(sx), int(sy),
+                                 float(stretch_x), float(stretch_y), int(bcx), int(bcy),
+                                 int(bool(thermal)), int(store), C.c_void_p(stream or 0))
+        self.nx, self.ny, self.thermal, self.store = int(nx), int(ny), bool(thermal), int(store)
+        self._h = lb_create_grid(self.desc)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            lb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def init(self, tau, dt=1.0, tau_g=None, ax=0.0, ay=0.0, beta=0.0, grav=0.0, T0=1.0, T_bot=1.0,
+             T_top=1.0, kind=LB_INIT_FIELDS, u0=0.0, amp=0.0, mode=1, seed=0, rho=None, ux=None,
+             uy=None, T=None):
+        self.params = lb_params(float(tau), float(dt), float(tau if tau_g is None else tau_g),
+                                float(ax), float(ay), float(beta), float(grav), float(T0),
+                                float(T_bot), float(T_top))
+        shp = (self.ny, self.nx)
+        keep = [_c64(v, shp) for v in (rho, ux, uy, T)]
+        d = lb_init_desc(int(kind), int(mode), float(u0), float(amp), int(seed),
+                         *[_ptr(a) for a in keep])
+        lb_init(self._h, self.params, d)
+        return self
+
+    def step_fv(self, n=1):
+        lb_step_fv(self._h, n)
+        return self
+
+    def step_st(self, n=1):
+        lb_step_st(self._h, n)
+        return self
+
+    def moments(self):
+        out = [np.empty((self.ny, self.nx)) for _ in range(4)]
+        lb_moments(self._h, *out)
+        return tuple(out)
+
+    def conservation(self):
+        return lb_conservation(self._h)
+
+    def nusselt(self):
+        return lb_nusselt(self._h)
+
+    def set_pops(self, f, g=None):
+        shp = (Q, self.ny, self.nx)
+        f, g = _c64(f, shp), _c64(g, shp)
+        lb_set_populations(self._h, f, g)
+        return self
+
+    def get_pops(self):
+        f = np.empty((Q, self.ny, self.nx))
+        g = np.empty((Q, self.ny, self.nx)) if self.thermal else None
+        lb_get_populations(self._h, f, g)
+        return f, g
+
+    def get_window(self, x0, y0, w, h):
+        f = np.empty((Q, h, w))
+        g = np.empty((Q, h, w)) if self.thermal else None
+        lb_get_window(self._h, x0, y0, w, h, f, g)
+        return f, g
+
+    def sync(self):
+        lb_sync(self._h)
+        return self

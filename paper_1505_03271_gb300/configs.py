@@ -1,0 +1,153 @@
+"""Parameter rules and the synthetic workloads (host logic only).
+
+Conventions (readings of the paper listed in the design notes):
+  * ``tau`` handed to the library is the physical relaxation time,
+    nu = tau c_s^2 (Sec. II).  The lattice relaxation time of the streaming
+    scheme at dt = 1 is tau~ = tau + 1/2, so a quoted "tau = 0.8" of an ST
+    run means tau = 0.3 here.
+  * FV time step on a stretched grid: dt = 0.9 min(dx_min, 8 tau); the paper
+    gives the stability limit only at dx = 1 (Sec. III C).
+  * Rayleigh-Benard: free-fall velocity U = sqrt(beta g dT H) = 0.1 (the LB
+    rule of thumb of Sec. IV), Ra = beta g dT H^3 / (nu kappa), Pr = nu/kappa,
+    dT = 1 with plates at T0 +- 1/2 and T0 = 1.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import (LB_AXIS_TANH, LB_AXIS_UNIFORM, LB_BC_PERIODIC, LB_BC_WALLS, LB_INIT_POISEUILLE,
+               LB_INIT_RB, LB_INIT_TGV, LB_STORE_F16DEV, LB_STORE_F32, LB_STORE_F64)
+
+CS2 = 1.0 / 3.0
+
+
+def tau_from_st_tau(tau_tilde_st: float) -> float:
+    """Physical tau from the ST relaxation time at dt = 1 (tau~ = tau + 1/2)."""
+    return tau_tilde_st - 0.5
+
+
+def faces(n: int, L: float, spacing: int, stretch: float) -> np.ndarray:
+    """Face coordinates of Eq. (grids) (uniform or tanh with delta = stretch)."""
+    i = np.arange(n + 1)
+    if spacing == LB_AXIS_TANH:
+        xi = 0.5 * L * (1.0 + np.tanh((2.0 * i / n - 1.0) * stretch) / np.tanh(stretch))
+    else:
+        xi = L * i / n
+    xi[0], xi[-1] = 0.0, L
+    return xi
+
+
+def min_cell(n: int, L: float, spacing: int, stretch: float) -> float:
+    return float(np.diff(faces(n, L, spacing, stretch)).min())
+
+
+def fv_dt(dx_min: float, tau: float, safety: float = 0.9) -> float:
+    return safety * min(dx_min, 8.0 * tau)
+
+
+@dataclass
+class RBParams:
+    tau: float
+    tau_g: float
+    beta: float
+    grav: float
+    T0: float
+    T_bot: float
+    T_top: float
+
+    @property
+    def nu(self):
+        return self.tau * CS2
+
+    @property
+    def kappa(self):
+        return self.tau_g * CS2
+
+
+def rb_params(Ra: float, Pr: float, H: float, U_ff: float = 0.1, T0: float = 1.0,
+              dT: float = 1.0, grav: float = 1.0) -> RBParams:
+    """nu = U H sqrt(Pr/Ra), kappa = nu / Pr, beta g dT = U^2 / H."""
+    nu = U_ff * H * math.sqrt(Pr / Ra)
+    kappa = nu / Pr
+    beta = U_ff**2 / (H * dT * grav)
+    return RBParams(tau=nu / CS2, tau_g=kappa / CS2, beta=beta, grav=grav, T0=T0,
+                    T_bot=T0 + 0.5 * dT, T_top=T0 - 0.5 * dT)
+
+
+def rayleigh(p: RBParams, H: float) -> float:
+    return p.beta * p.grav * (p.T_bot - p.T_top) * H**3 / (p.nu * p.kappa)
+
+
+@dataclass
+class Workload:
+    """A grid description plus parameters and an initial condition."""
+    name: str
+    grid: dict
+    params: dict
+    init: dict
+    steps: int
+    scheme: str
+    notes: dict = field(default_factory=dict)
+
+    @property
+    def cells(self) -> int:
+        return self.grid["nx"] * self.grid["ny"]
+
+
+def tgv64(scheme: str = "st") -> Workload:
+    """64x64 periodic TGV, FP64, quoted tau = 0.8 (tau = 0.3), u0 = 0.01,
+    t = 1000 (ST: dt = 1; FV: dt = 0.5, stable in 2-D at this tau)."""
+    dt = 1.0 if scheme == "st" else 0.5
+    return Workload("tgv64_" + scheme,
+                    dict(nx=64, ny=64, store=LB_STORE_F64),
+                    dict(tau=tau_from_st_tau(0.8), dt=dt),
+                    dict(kind=LB_INIT_TGV, u0=0.01), int(round(1000 / dt)), scheme)
+
+
+def channel(u_max: float | None = None, store: int = LB_STORE_F32, nx: int = 256,
+            ny: int = 512, steps: int = 20000) -> Workload:
+    """Body-force channel, 256 x 512, walls on y with tanh delta = 2, quoted
+    tau = 0.7 (tau = 0.2, nu = 1/15), a_x = 8 nu U / L^2, started on the
+    parabola.  Default U from Re = 10 (Sec. III B)."""
+    tau = tau_from_st_tau(0.7)
+    nu = tau * CS2
+    L = float(ny)
+    U = u_max if u_max is not None else 10.0 * nu / L
+    dt = fv_dt(min_cell(ny, L, LB_AXIS_TANH, 2.0), tau)
+    return Workload("channel_%dx%d" % (nx, ny),
+                    dict(nx=nx, ny=ny, lx=float(nx), ly=L, sy=LB_AXIS_TANH, stretch_y=2.0,
+                         bcy=LB_BC_WALLS, store=store),
+                    dict(tau=tau, dt=dt, ax=8.0 * nu * U / L**2),
+                    dict(kind=LB_INIT_POISEUILLE, u0=U), steps, "fv", dict(U=U, Re=U * L / nu))
+
+
+def rayleigh_benard(n: int = 1024, Ra: float = 1e8, Pr: float = 1.0, store: int = LB_STORE_F16DEV,
+                    steps: int = 2000, seed: int = 1234, amp: float = 1e-3) -> Workload:
+    """Square RB cell, x periodic uniform, plates on y with tanh delta = 2."""
+    H = float(n)
+    p = rb_params(Ra, Pr, H)
+    dt = fv_dt(min_cell(n, H, LB_AXIS_TANH, 2.0), min(p.tau, p.tau_g))
+    return Workload("rb%d_Ra%.0e" % (n, Ra),
+                    dict(nx=n, ny=n, lx=H, ly=H, sy=LB_AXIS_TANH, stretch_y=2.0, bcy=LB_BC_WALLS,
+                         thermal=True, store=store),
+                    dict(tau=p.tau, dt=dt, tau_g=p.tau_g, beta=p.beta, grav=p.grav, T0=p.T0,
+                         T_bot=p.T_bot, T_top=p.T_top),
+                    dict(kind=LB_INIT_RB, amp=amp, seed=seed), steps, "fv")
+
+
+def st_sweep(n: int = 8192, store: int = LB_STORE_F32, steps: int = 500) -> Workload:
+    """Periodic n x n ST: TGV mode 1 (u0 = 0.01) plus shear wave mode 2 (0.01),
+    quoted tau = 0.8."""
+    return Workload("st%d" % n, dict(nx=n, ny=n, store=store),
+                    dict(tau=tau_from_st_tau(0.8), dt=1.0),
+                    dict(kind=LB_INIT_TGV, u0=0.01, amp=0.01, mode=2), steps, "st")
+
+
+def bytes_per_cell(store: int, thermal: bool) -> int:
+    """Compulsory HBM bytes per cell update: every population read and
+    written once (9 or 18 populations)."""
+    from . import STORE_BYTES
+    return 2 * (18 if thermal else 9) * STORE_BYTES[store]

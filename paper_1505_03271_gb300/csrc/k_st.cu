@@ -1,0 +1,88 @@
+// k_st.cu -- fused collide-and-stream (ST) step, Eq. (ST) of Sec. II A with
+// dt = dx = 1, push form: each thread loads the populations of its cell
+// (coalesced along x in the [q][y][x] layout), relaxes them with the BGK
+// collision plus Guo forcing, and writes each post-collision value to the
+// neighbour it streams to.  Walls: half-way bounce-back for f and
+// anti-bounce-back through the plate temperature for g.
+#include "lb_internal.cuh"
+
+namespace lbgb {
+
+template <typename R, typename S, bool TH>
+__global__ void __launch_bounds__(256) k_st(const StepArgs<R> A) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y;
+    if (x >= A.nx) return;
+    const S* fin = static_cast<const S*>(A.fin);
+    S* fout = static_cast<S*>(A.fout);
+    const S* gin = static_cast<const S*>(A.gin);
+    S* gout = static_cast<S*>(A.gout);
+    const long long c = (long long)y * A.pitch + x;
+
+    R d[Q], e[Q];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) d[a] = Store<S>::ld(fin + a * A.plane + c) + wgt<R>(a) * A.roff[y];
+    if (TH) {
+#pragma unroll
+        for (int a = 0; a < Q; ++a) e[a] = Store<S>::ld(gin + a * A.plane + c) + wgt<R>(a) * A.toff[y];
+    }
+    Cell<R, TH> m;
+    m.moments(d, e, A);
+
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        R feqd, F, geqd = 0;
+        m.eq(a, A, feqd, F, geqd);
+        // right-hand side of Eq. (ST), dt = 1: om = 1/tau~, cf = 1 - 1/(2 tau~)
+        const R post = d[a] + A.om * (feqd - d[a]) + A.cf * F;
+        R gpost = 0;
+        if (TH) gpost = e[a] + A.omg * (geqd - e[a]);
+        int tx = x + cx(a), ty = y + cy(a);
+        bool out = false;
+        R dTw = 0;
+        if (tx < 0 || tx >= A.nx) {
+            if (A.bcx == LB_BC_PERIODIC) tx = tx < 0 ? tx + A.nx : tx - A.nx;
+            else out = true;
+        }
+        if (ty < 0 || ty >= A.ny) {
+            if (A.bcy == LB_BC_PERIODIC) {
+                ty = ty < 0 ? ty + A.ny : ty - A.ny;
+            } else {
+                out = true;
+                dTw = ty < 0 ? A.dTb : A.dTt;
+            }
+        }
+        if (out) {
+            const long long o = inv(a) * A.plane + c;
+            Store<S>::st(fout + o, post - wgt<R>(a) * A.roff[y]);
+            if (TH) Store<S>::st(gout + o, -gpost + wgt<R>(a) * (R(2) * dTw - A.toff[y]));
+        } else {
+            const long long o = a * A.plane + (long long)ty * A.pitch + tx;
+            Store<S>::st(fout + o, post - wgt<R>(a) * A.roff[ty]);
+            if (TH) Store<S>::st(gout + o, gpost - wgt<R>(a) * A.toff[ty]);
+        }
+    }
+}
+
+template <typename R, typename S, bool TH>
+static cudaError_t run_st(const void* vargs, cudaStream_t s) {
+    const StepArgs<R>& A = *static_cast<const StepArgs<R>*>(vargs);
+    int bx = A.nx >= 256 ? 256 : ((A.nx + 31) / 32) * 32;
+    dim3 grid((A.nx + bx - 1) / bx, A.ny);
+    k_st<R, S, TH><<<grid, bx, 0, s>>>(A);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_st(Prec p, bool th, const void* args, cudaStream_t s) {
+    switch (p) {
+        case Prec::F64: return th ? run_st<double, double, true>(args, s) : run_st<double, double, false>(args, s);
+        case Prec::F32: return th ? run_st<float, float, true>(args, s) : run_st<float, float, false>(args, s);
+        case Prec::F16: return th ? run_st<float, __half, true>(args, s) : run_st<float, __half, false>(args, s);
+        case Prec::BF16:
+            return th ? run_st<float, __nv_bfloat16, true>(args, s) : run_st<float, __nv_bfloat16, false>(args, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace lbgb

@@ -1,0 +1,627 @@
+// lb_abi.cu -- host side of the C ABI declared in include/lb.h: grid and
+// metric construction, parameter checks, kernel dispatch and observables.
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lb_internal.cuh"
+
+using namespace lbgb;
+
+namespace {
+
+thread_local std::string g_err;
+std::atomic<unsigned long long> g_launches{0};
+
+lb_status fail(lb_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return s;
+}
+
+#define CK(call)                                                                             \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(e_ == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA, "%s: %s", \
+                        #call, cudaGetErrorString(e_));                                      \
+    } while (0)
+
+// Face coordinates of one axis, Eq. (grids) of Sec. III B.
+std::vector<double> axis_faces(int n, double L, int sp, double st) {
+    std::vector<double> xi(n + 1);
+    for (int i = 0; i <= n; ++i) {
+        const double s = (double)i / n;
+        if (sp == LB_AXIS_TANH) {
+            xi[i] = 0.5 * L * (1.0 + std::tanh((2.0 * s - 1.0) * st) / std::tanh(st));
+        } else if (sp == LB_AXIS_SINH) {
+            const double amp = 0.5 * L / std::sinh(0.5 * st);
+            xi[i] = 2 * i <= n ? amp * std::sinh(st * s) : L - amp * std::sinh(st * (double)(n - i) / n);
+        } else {
+            xi[i] = L * s;
+        }
+    }
+    xi[0] = 0.0;
+    xi[n] = L;
+    return xi;
+}
+
+struct Axis {
+    int n = 0;
+    double L = 0;
+    int bc = 0;
+    std::vector<double> xi, c, d;
+    // centre of any integer cell index: periodic repeats shifted by L, walls
+    // mirror the fluid centres about the wall face (ghost centres, Sec. II B 5)
+    double pos(int i) const {
+        if (i >= 0 && i < n) return c[i];
+        if (bc == LB_BC_PERIODIC) {
+            int q = i >= 0 ? i / n : -((-i + n - 1) / n);
+            return c[i - q * n] + q * L;
+        }
+        return i < 0 ? 2.0 * xi[0] - c[-i - 1] : 2.0 * xi[n] - c[2 * n - 1 - i];
+    }
+    // Lagrange weights of the parabola through cells (k0, k0+1, k0+2) at face k:
+    // the QUICK coefficients of Sec. II B 3 (gamma_1 = weight of the
+    // downstream node, gamma_2 = -weight of the far upstream node).
+    void quick(int k0, int k, double w[3]) const {
+        const double p[3] = {pos(k0), pos(k0 + 1), pos(k0 + 2)};
+        const double x = xi[k];
+        w[0] = (x - p[1]) * (x - p[2]) / ((p[0] - p[1]) * (p[0] - p[2]));
+        w[1] = (x - p[0]) * (x - p[2]) / ((p[1] - p[0]) * (p[1] - p[2]));
+        w[2] = (x - p[0]) * (x - p[1]) / ((p[2] - p[0]) * (p[2] - p[1]));
+    }
+    // [6][n+1] weights then [n] inverse widths
+    std::vector<double> metric() const {
+        std::vector<double> m(7 * (n + 1), 0.0);
+        for (int k = 0; k <= n; ++k) {
+            double w[3];
+            quick(k - 2, k, w);
+            for (int r = 0; r < 3; ++r) m[r * (n + 1) + k] = w[r];
+            quick(k - 1, k, w);
+            for (int r = 0; r < 3; ++r) m[(3 + r) * (n + 1) + k] = w[r];
+        }
+        for (int i = 0; i < n; ++i) m[6 * (n + 1) + i] = 1.0 / d[i];
+        return m;
+    }
+};
+
+Axis make_axis(int n, double L, int sp, double st, int bc) {
+    Axis a;
+    a.n = n;
+    a.L = L;
+    a.bc = bc;
+    a.xi = axis_faces(n, L, sp, st);
+    a.c.resize(n);
+    a.d.resize(n);
+    for (int i = 0; i < n; ++i) {
+        a.c[i] = 0.5 * (a.xi[i] + a.xi[i + 1]);
+        a.d[i] = a.xi[i + 1] - a.xi[i];
+    }
+    return a;
+}
+
+Prec prec_of(int store) {
+    switch (store) {
+        case LB_STORE_F64: return Prec::F64;
+        case LB_STORE_F16DEV: return Prec::F16;
+        case LB_STORE_BF16DEV: return Prec::BF16;
+        default: return Prec::F32;
+    }
+}
+
+size_t elem_size(int store) {
+    return store == LB_STORE_F64 ? 8 : (store == LB_STORE_F32 ? 4 : 2);
+}
+
+}  // namespace
+
+namespace lbgb {
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace lbgb
+
+struct lb_grid {
+    lb_grid_desc d{};
+    lb_params p{};
+    bool has_params = false;
+    bool poisoned = false;
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    Prec prec = Prec::F32;
+    int nx = 0, ny = 0, pitch = 0;
+    long long plane = 0;
+    Axis ax, ay;
+    double dmin = 0;
+    void* f[2] = {nullptr, nullptr};
+    void* g[2] = {nullptr, nullptr};
+    int cur = 0;
+    void* mx = nullptr;  // metric in compute precision
+    void* my = nullptr;
+    double *dxv = nullptr, *dyv = nullptr, *xc = nullptr, *yc = nullptr;
+    double* toff = nullptr;     // per-row storage offset of g, FP64 (ny)
+    void* toff_r = nullptr;     // the same in compute precision
+    double* roff = nullptr;     // per-row storage offset of f, FP64 (ny)
+    void* roff_r = nullptr;
+    double* fields = nullptr;   // [4][ny][nx] staging for init/moments
+    double* partial = nullptr;  // reduction partials
+    double* red = nullptr;      // reduction totals
+    int nred = 0;
+};
+
+namespace {
+
+void release(lb_grid* G) {
+    void* ptrs[] = {G->f[0], G->f[1], G->g[0], G->g[1], G->mx, G->my, G->dxv, G->dyv, G->xc,
+                    G->yc, G->toff, G->toff_r, G->roff, G->roff_r, G->fields, G->partial, G->red};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+template <typename R>
+StepArgs<R> step_args(const lb_grid* G, double dt) {
+    StepArgs<R> A{};
+    A.fin = G->f[G->cur];
+    A.fout = G->f[1 - G->cur];
+    A.gin = G->g[G->cur];
+    A.gout = G->g[1 - G->cur];
+    A.nx = G->nx;
+    A.ny = G->ny;
+    A.pitch = G->pitch;
+    A.plane = G->plane;
+    A.bcx = G->d.bcx;
+    A.bcy = G->d.bcy;
+    A.mx = AxisMetric<R>{static_cast<const R*>(G->mx), G->nx + 1};
+    A.my = AxisMetric<R>{static_cast<const R*>(G->my), G->ny + 1};
+    const lb_params& p = G->p;
+    const double taut = p.tau + 0.5 * dt, taugt = p.tau_g + 0.5 * dt;  // tau~ = tau + dt/2
+    A.dt = (R)dt;
+    A.om = (R)(dt / taut);
+    A.omh = (R)(dt / (2.0 * taut));
+    A.cf = (R)(dt * (1.0 - dt / (2.0 * taut)));
+    A.hf = (R)(0.5 * dt);
+    A.omg = (R)(dt / taugt);
+    A.omgh = (R)(dt / (2.0 * taugt));
+    A.ax = (R)p.ax;
+    A.ay = (R)p.ay;
+    A.bg = (R)(p.beta * p.grav);
+    A.dTb = (R)(p.T_bot - p.T0);
+    A.dTt = (R)(p.T_top - p.T0);
+    A.T0 = (R)p.T0;
+    A.toff = static_cast<const R*>(G->toff_r);
+    A.roff = static_cast<const R*>(G->roff_r);
+    return A;
+}
+
+AuxArgs aux_args(const lb_grid* G) {
+    AuxArgs a{};
+    a.f = G->f[G->cur];
+    a.g = G->g[G->cur];
+    a.nx = G->nx;
+    a.ny = G->ny;
+    a.pitch = G->pitch;
+    a.plane = G->plane;
+    a.dt = G->p.dt;
+    a.ax = G->p.ax;
+    a.ay = G->p.ay;
+    a.bg = G->p.beta * G->p.grav;
+    a.T0 = G->p.T0;
+    a.toff = G->toff;
+    a.roff = G->roff;
+    a.dxv = G->dxv;
+    a.dyv = G->dyv;
+    a.xc = G->xc;
+    a.yc = G->yc;
+    return a;
+}
+
+lb_status check_ready(lb_grid* G) {
+    if (!G) return fail(LB_ERR_ARG, "grid is NULL");
+    if (!G->has_params) return fail(LB_ERR_STATE, "grid has no parameters: call lb_init first");
+    if (G->poisoned) return fail(LB_ERR_STATE, "grid diverged (LB_ERR_UNSTABLE); call lb_init again");
+    return LB_OK;
+}
+
+lb_status upload(void** dst, const std::vector<double>& v, bool as_float) {
+    size_t bytes = v.size() * (as_float ? sizeof(float) : sizeof(double));
+    CK(cudaMalloc(dst, bytes ? bytes : 8));
+    if (as_float) {
+        std::vector<float> t(v.begin(), v.end());
+        CK(cudaMemcpy(*dst, t.data(), bytes, cudaMemcpyHostToDevice));
+    } else {
+        CK(cudaMemcpy(*dst, v.data(), bytes, cudaMemcpyHostToDevice));
+    }
+    return LB_OK;
+}
+
+lb_status reduce(lb_grid* G, double out[kRed]) {
+    CK(launch_reduce(G->prec, G->d.thermal != 0, aux_args(G), G->partial, G->nred, G->red, G->stream));
+    CK(cudaMemcpyAsync(out, G->red, sizeof(double) * kRed, cudaMemcpyDeviceToHost, G->stream));
+    CK(cudaStreamSynchronize(G->stream));
+    return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lb_last_error(void) { return g_err.c_str(); }
+
+unsigned long long lb_kernel_launches(void) { return g_launches.load(); }
+
+lb_status lb_create_grid(const lb_grid_desc* d, lb_grid** out) {
+    if (!d || !out) return fail(LB_ERR_ARG, "NULL description or output");
+    if (d->nx < 1 || d->ny < 1) return fail(LB_ERR_ARG, "nx, ny must be >= 1 (got %d, %d)", d->nx, d->ny);
+    if ((long long)d->nx * d->ny > (1LL << 31))
+        return fail(LB_ERR_ARG, "grid of %d x %d cells is larger than supported", d->nx, d->ny);
+    if (d->bcx != LB_BC_PERIODIC && d->bcx != LB_BC_WALLS) return fail(LB_ERR_ARG, "bad bcx");
+    if (d->bcy != LB_BC_PERIODIC && d->bcy != LB_BC_WALLS) return fail(LB_ERR_ARG, "bad bcy");
+    if ((d->bcx == LB_BC_WALLS && d->nx < 2) || (d->bcy == LB_BC_WALLS && d->ny < 2))
+        return fail(LB_ERR_ARG, "a wall axis needs at least 2 cells (two ghost layers)");
+    if (d->thermal && d->bcx == LB_BC_WALLS)
+        return fail(LB_ERR_ARG, "thermal grids have their isothermal plates on y; x must be periodic");
+    if (d->store < LB_STORE_F64 || d->store > LB_STORE_BF16DEV) return fail(LB_ERR_ARG, "bad store");
+    for (int k = 0; k < 2; ++k) {
+        const int sp = k ? d->sy : d->sx, n = k ? d->ny : d->nx;
+        const double L = k ? d->ly : d->lx, st = k ? d->stretch_y : d->stretch_x;
+        if (sp < LB_AXIS_UNIFORM || sp > LB_AXIS_SINH) return fail(LB_ERR_ARG, "bad spacing");
+        if (!(L > 0)) return fail(LB_ERR_ARG, "domain length must be > 0");
+        if (sp != LB_AXIS_UNIFORM && !(st > 0)) return fail(LB_ERR_ARG, "stretch must be > 0");
+        if (sp == LB_AXIS_SINH && (n % 2)) return fail(LB_ERR_ARG, "sinh spacing needs an even cell count");
+    }
+    lb_grid* G = new lb_grid();
+    G->d = *d;
+    G->nx = d->nx;
+    G->ny = d->ny;
+    G->pitch = ((d->nx + 31) / 32) * 32;
+    G->plane = (long long)G->pitch * d->ny;
+    G->prec = prec_of(d->store);
+    G->stream = static_cast<cudaStream_t>(d->cuda_stream);
+    G->ax = make_axis(d->nx, d->lx, d->sx, d->stretch_x, d->bcx);
+    G->ay = make_axis(d->ny, d->ly, d->sy, d->stretch_y, d->bcy);
+    G->dmin = 1e300;
+    for (double v : G->ax.d) G->dmin = std::fmin(G->dmin, v);
+    for (double v : G->ay.d) G->dmin = std::fmin(G->dmin, v);
+    for (int k = 0; k < 2; ++k) {
+        const Axis& a = k ? G->ay : G->ax;
+        for (double v : a.d)
+            if (!(v > 0)) {
+                delete G;
+                return fail(LB_ERR_ARG, "degenerate cell width on axis %c", k ? 'y' : 'x');
+            }
+    }
+    cudaGetDevice(&G->device);
+    const size_t pop_bytes = (size_t)Q * G->plane * elem_size(d->store);
+    const bool as_float = G->prec != Prec::F64;
+    G->nred = reduce_blocks(G->nx, G->ny);
+    lb_status st = LB_OK;
+    auto alloc = [&](void** p, size_t bytes) {
+        if (st != LB_OK) return;
+        cudaError_t e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess) {
+            *p = nullptr;
+            cudaGetLastError();
+            st = fail(e == cudaErrorMemoryAllocation ? LB_ERR_OOM : LB_ERR_CUDA,
+                      "cudaMalloc(%zu bytes): %s", bytes, cudaGetErrorString(e));
+        }
+    };
+    for (int b = 0; b < 2; ++b) {
+        alloc(&G->f[b], pop_bytes);
+        if (d->thermal) alloc(&G->g[b], pop_bytes);
+    }
+    alloc((void**)&G->fields, sizeof(double) * 4 * (size_t)G->nx * G->ny);
+    alloc((void**)&G->toff, sizeof(double) * G->ny);
+    alloc(&G->toff_r, (as_float ? sizeof(float) : sizeof(double)) * G->ny);
+    alloc((void**)&G->roff, sizeof(double) * G->ny);
+    alloc(&G->roff_r, (as_float ? sizeof(float) : sizeof(double)) * G->ny);
+    alloc((void**)&G->partial, sizeof(double) * kRed * G->nred);
+    alloc((void**)&G->red, sizeof(double) * kRed);
+    if (st == LB_OK) st = upload(&G->mx, G->ax.metric(), as_float);
+    if (st == LB_OK) st = upload(&G->my, G->ay.metric(), as_float);
+    if (st == LB_OK) st = upload((void**)&G->dxv, G->ax.d, false);
+    if (st == LB_OK) st = upload((void**)&G->dyv, G->ay.d, false);
+    if (st == LB_OK) st = upload((void**)&G->xc, G->ax.c, false);
+    if (st == LB_OK) st = upload((void**)&G->yc, G->ay.c, false);
+    if (st != LB_OK) {
+        release(G);
+        delete G;
+        return st;
+    }
+    *out = G;
+    return LB_OK;
+}
+
+lb_status lb_destroy(lb_grid* G) {
+    if (!G) return LB_OK;
+    DeviceGuard dg(G->device);
+    cudaStreamSynchronize(G->stream);
+    release(G);
+    delete G;
+    return LB_OK;
+}
+
+lb_status lb_sync(lb_grid* G) {
+    if (!G) return fail(LB_ERR_ARG, "grid is NULL");
+    DeviceGuard dg(G->device);
+    CK(cudaStreamSynchronize(G->stream));
+    return LB_OK;
+}
+
+lb_status lb_init(lb_grid* G, const lb_params* p, const lb_init_desc* in) {
+    if (!G || !p || !in) return fail(LB_ERR_ARG, "NULL argument");
+    if (!(p->tau > 0) || !(p->dt > 0)) return fail(LB_ERR_ARG, "tau and dt must be > 0");
+    if (G->d.thermal && !(p->tau_g > 0)) return fail(LB_ERR_ARG, "tau_g must be > 0 on a thermal grid");
+    if (in->kind < LB_INIT_TGV || in->kind > LB_INIT_FIELDS) return fail(LB_ERR_ARG, "bad init kind");
+    if (in->kind == LB_INIT_RB && !G->d.thermal) return fail(LB_ERR_ARG, "RB preset needs a thermal grid");
+    DeviceGuard dg(G->device);
+    // Reference state of the storage: the barometric density and conductive
+    // temperature of the RB base state on a grid with plates, else 1 and T0.
+    double rho_norm = 1.0;
+    const double dTp = p->T_bot - p->T_top, bgp = p->beta * p->grav, Hy = G->d.ly;
+    auto baro = [&](double y) { return std::exp(3.0 * bgp * dTp * (0.5 * y - 0.5 * y * y / Hy)); };
+    if (in->kind == LB_INIT_RB) {
+        double s = 0.0;
+        for (int j = 0; j < G->ny; ++j) s += G->ay.d[j] * baro(G->ay.c[j]);
+        rho_norm = Hy / s;  // sum V rho = sum V
+    }
+    {
+        std::vector<double> to(G->ny, 0.0), ro(G->ny, 0.0);
+        const bool plates = G->d.thermal && G->d.bcy == LB_BC_WALLS;
+        for (int j = 0; j < G->ny; ++j) {
+            if (plates) to[j] = dTp * (0.5 - G->ay.c[j] / Hy) + 0.5 * (p->T_bot + p->T_top) - p->T0;
+            if (in->kind == LB_INIT_RB) ro[j] = rho_norm * baro(G->ay.c[j]) - 1.0;
+        }
+        CK(cudaMemcpy(G->toff, to.data(), sizeof(double) * G->ny, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(G->roff, ro.data(), sizeof(double) * G->ny, cudaMemcpyHostToDevice));
+        if (G->prec == Prec::F64) {
+            CK(cudaMemcpy(G->toff_r, to.data(), sizeof(double) * G->ny, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(G->roff_r, ro.data(), sizeof(double) * G->ny, cudaMemcpyHostToDevice));
+        } else {
+            std::vector<float> tf(to.begin(), to.end()), rf(ro.begin(), ro.end());
+            CK(cudaMemcpy(G->toff_r, tf.data(), sizeof(float) * G->ny, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(G->roff_r, rf.data(), sizeof(float) * G->ny, cudaMemcpyHostToDevice));
+        }
+    }
+    InitArgs a{};
+    a.f = G->f[0];
+    a.g = G->g[0];
+    a.nx = G->nx;
+    a.ny = G->ny;
+    a.pitch = G->pitch;
+    a.plane = G->plane;
+    a.kind = in->kind;
+    a.mode = in->mode;
+    a.u0 = in->u0;
+    a.amp = in->amp;
+    a.seed = in->seed;
+    a.lx = G->d.lx;
+    a.ly = G->d.ly;
+    a.dt = p->dt;
+    a.ax = p->ax;
+    a.ay = p->ay;
+    a.bg = p->beta * p->grav;
+    a.T0 = p->T0;
+    a.Tb = p->T_bot;
+    a.Tt = p->T_top;
+    a.xc = G->xc;
+    a.yc = G->yc;
+    a.toff = G->toff;
+    a.roff = G->roff;
+    a.fields = G->fields;
+    a.rho_norm = rho_norm;
+    if (in->kind == LB_INIT_FIELDS) {
+        const size_t n = (size_t)G->nx * G->ny;
+        std::vector<double> h(4 * n);
+        for (size_t c = 0; c < n; ++c) {
+            h[c] = in->rho ? in->rho[c] : 1.0;
+            h[n + c] = in->ux ? in->ux[c] : 0.0;
+            h[2 * n + c] = in->uy ? in->uy[c] : 0.0;
+            h[3 * n + c] = in->T ? in->T[c] : p->T0;
+            if (!(h[c] > 0)) return fail(LB_ERR_ARG, "density must be > 0 (cell %zu)", c);
+        }
+        CK(cudaMemcpyAsync(G->fields, h.data(), sizeof(double) * 4 * n, cudaMemcpyHostToDevice, G->stream));
+        CK(launch_init(G->prec, G->d.thermal != 0, a, G->stream));
+        CK(cudaStreamSynchronize(G->stream));  // h is released on return
+    } else {
+        CK(launch_init(G->prec, G->d.thermal != 0, a, G->stream));
+    }
+    G->p = *p;
+    G->has_params = true;
+    G->poisoned = false;
+    G->cur = 0;
+    return LB_OK;
+}
+
+lb_status lb_step_fv(lb_grid* G, int nsteps) {
+    lb_status s = check_ready(G);
+    if (s != LB_OK) return s;
+    if (nsteps < 0) return fail(LB_ERR_ARG, "nsteps must be >= 0");
+    DeviceGuard dg(G->device);
+    const bool th = G->d.thermal != 0;
+    for (int k = 0; k < nsteps; ++k) {
+        cudaError_t e;
+        if (G->prec == Prec::F64) {
+            StepArgs<double> A = step_args<double>(G, G->p.dt);
+            e = launch_fv(G->prec, th, &A, G->stream);
+        } else {
+            StepArgs<float> A = step_args<float>(G, G->p.dt);
+            e = launch_fv(G->prec, th, &A, G->stream);
+        }
+        CK(e);
+        G->cur ^= 1;
+    }
+    return LB_OK;
+}
+
+lb_status lb_step_st(lb_grid* G, int nsteps) {
+    lb_status s = check_ready(G);
+    if (s != LB_OK) return s;
+    if (nsteps < 0) return fail(LB_ERR_ARG, "nsteps must be >= 0");
+    for (int k = 0; k < 2; ++k) {
+        const int sp = k ? G->d.sy : G->d.sx, n = k ? G->ny : G->nx;
+        const double L = k ? G->d.ly : G->d.lx;
+        if (sp != LB_AXIS_UNIFORM || std::fabs(L / n - 1.0) > 1e-12)
+            return fail(LB_ERR_ARG, "ST needs uniform axes with unit spacing (axis %c: L/n = %g)",
+                        k ? 'y' : 'x', L / n);
+    }
+    if (std::fabs(G->p.dt - 1.0) > 1e-12) return fail(LB_ERR_ARG, "ST needs dt = 1 (got %g)", G->p.dt);
+    DeviceGuard dg(G->device);
+    const bool th = G->d.thermal != 0;
+    for (int k = 0; k < nsteps; ++k) {
+        cudaError_t e;
+        if (G->prec == Prec::F64) {
+            StepArgs<double> A = step_args<double>(G, 1.0);
+            e = launch_st(G->prec, th, &A, G->stream);
+        } else {
+            StepArgs<float> A = step_args<float>(G, 1.0);
+            e = launch_st(G->prec, th, &A, G->stream);
+        }
+        CK(e);
+        G->cur ^= 1;
+    }
+    return LB_OK;
+}
+
+lb_status lb_moments(lb_grid* G, double* rho, double* ux, double* uy, double* T) {
+    if (!G) return fail(LB_ERR_ARG, "grid is NULL");
+    if (!G->has_params) return fail(LB_ERR_STATE, "grid has no parameters: call lb_init first");
+    DeviceGuard dg(G->device);
+    CK(launch_moments(G->prec, G->d.thermal != 0, aux_args(G), G->fields, G->stream));
+    const size_t n = (size_t)G->nx * G->ny;
+    double* outs[4] = {rho, ux, uy, T};
+    for (int k = 0; k < 4; ++k)
+        if (outs[k])
+            CK(cudaMemcpyAsync(outs[k], G->fields + k * n, sizeof(double) * n, cudaMemcpyDeviceToHost,
+                               G->stream));
+    CK(cudaStreamSynchronize(G->stream));
+    return LB_OK;
+}
+
+lb_status lb_conservation(lb_grid* G, double* mass, double* momx, double* momy, double* heat) {
+    if (!G) return fail(LB_ERR_ARG, "grid is NULL");
+    if (!G->has_params) return fail(LB_ERR_STATE, "grid has no parameters: call lb_init first");
+    DeviceGuard dg(G->device);
+    double v[kRed];
+    lb_status s = reduce(G, v);
+    if (s != LB_OK) return s;
+    if (mass) *mass = v[0];
+    if (momx) *momx = v[1];
+    if (momy) *momy = v[2];
+    if (heat) *heat = v[3];
+    for (int q = 0; q < 4; ++q)
+        if (!std::isfinite(v[q])) {
+            G->poisoned = true;
+            return fail(LB_ERR_UNSTABLE, "non-finite conservation sum: the run diverged (dt too large "
+                                         "for tau or the grid)");
+        }
+    return LB_OK;
+}
+
+lb_status lb_nusselt(lb_grid* G, double* nu_vol, double* nu_bot, double* nu_top) {
+    if (!G) return fail(LB_ERR_ARG, "grid is NULL");
+    if (!G->d.thermal) return fail(LB_ERR_STATE, "Nusselt numbers need a thermal grid");
+    if (!G->has_params) return fail(LB_ERR_STATE, "grid has no parameters: call lb_init first");
+    DeviceGuard dg(G->device);
+    double v[kRed];
+    lb_status s = reduce(G, v);
+    if (s != LB_OK) return s;
+    const lb_params& p = G->p;
+    const double H = G->d.ly, dT = p.T_bot - p.T_top, kappa = p.tau_g / 3.0, Lx = G->d.lx;
+    if (nu_vol) *nu_vol = 1.0 + H * (v[4] / v[5]) / (kappa * dT);
+    // plate gradients: quadratic through the wall value and the first two
+    // x-averaged nodes, differentiated at the wall
+    const double t0 = v[6] / Lx, t1 = v[7] / Lx, tn2 = v[8] / Lx, tn1 = v[9] / Lx;
+    const double y0 = G->ay.c[0], y1 = G->ay.c[1];
+    const double gb = -(y0 + y1) / (y0 * y1) * p.T_bot + y1 / (y0 * (y1 - y0)) * t0 - y0 / (y1 * (y1 - y0)) * t1;
+    const double s0 = H - G->ay.c[G->ny - 1], s1 = H - G->ay.c[G->ny - 2];
+    const double gt = -(s0 + s1) / (s0 * s1) * p.T_top + s1 / (s0 * (s1 - s0)) * tn1 - s0 / (s1 * (s1 - s0)) * tn2;
+    if (nu_bot) *nu_bot = -H * gb / dT;
+    if (nu_top) *nu_top = H * gt / dT;
+    for (double x : v)
+        if (!std::isfinite(x)) {
+            G->poisoned = true;
+            return fail(LB_ERR_UNSTABLE, "non-finite reduction: the run diverged");
+        }
+    return LB_OK;
+}
+
+lb_status lb_set_populations(lb_grid* G, const double* f, const double* g) {
+    if (!G) return fail(LB_ERR_ARG, "grid is NULL");
+    if (!G->has_params) return fail(LB_ERR_STATE, "set parameters with lb_init before setting populations");
+    if (g && !G->d.thermal) return fail(LB_ERR_STATE, "thermal populations on a flow-only grid");
+    DeviceGuard dg(G->device);
+    const size_t n = (size_t)Q * G->nx * G->ny;
+    double* tmp = nullptr;
+    CK(cudaMalloc(&tmp, sizeof(double) * n));
+    lb_status st = LB_OK;
+    const double* srcs[2] = {f, g};
+    void* dsts[2] = {G->f[G->cur], G->g[G->cur]};
+    const double offs[2] = {1.0, G->p.T0};
+    const double* rowoffs[2] = {G->roff, G->toff};
+    for (int k = 0; k < 2 && st == LB_OK; ++k) {
+        if (!srcs[k]) continue;
+        cudaError_t e = cudaMemcpy(tmp, srcs[k], sizeof(double) * n, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = launch_pack(G->prec, tmp, dsts[k], G->nx, G->ny, G->pitch, G->plane, offs[k], rowoffs[k],
+                            G->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(G->stream);
+        if (e != cudaSuccess) st = fail(LB_ERR_CUDA, "set_populations: %s", cudaGetErrorString(e));
+    }
+    cudaFree(tmp);
+    return st;
+}
+
+lb_status lb_get_window(lb_grid* G, int x0, int y0, int w, int h, double* f, double* g) {
+    if (!G) return fail(LB_ERR_ARG, "grid is NULL");
+    if (!G->has_params) return fail(LB_ERR_STATE, "grid has no parameters: call lb_init first");
+    if (g && !G->d.thermal) return fail(LB_ERR_STATE, "thermal populations on a flow-only grid");
+    if (w < 1 || h < 1 || w > G->nx || h > G->ny)
+        return fail(LB_ERR_ARG, "window %d x %d does not fit a %d x %d grid", w, h, G->nx, G->ny);
+    DeviceGuard dg(G->device);
+    x0 = ((x0 % G->nx) + G->nx) % G->nx;
+    y0 = ((y0 % G->ny) + G->ny) % G->ny;
+    const size_t n = (size_t)Q * w * h;
+    double* tmp = nullptr;
+    CK(cudaMalloc(&tmp, sizeof(double) * n));
+    lb_status st = LB_OK;
+    double* dsts[2] = {f, g};
+    const void* srcs[2] = {G->f[G->cur], G->g[G->cur]};
+    const double offs[2] = {1.0, G->p.T0};
+    const double* rowoffs[2] = {G->roff, G->toff};
+    for (int k = 0; k < 2 && st == LB_OK; ++k) {
+        if (!dsts[k]) continue;
+        cudaError_t e = launch_unpack(G->prec, srcs[k], tmp, G->nx, G->ny, G->pitch, G->plane, offs[k],
+                                      rowoffs[k], x0, y0, w, h, G->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dsts[k], tmp, sizeof(double) * n, cudaMemcpyDeviceToHost, G->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(G->stream);
+        if (e != cudaSuccess) st = fail(LB_ERR_CUDA, "get_window: %s", cudaGetErrorString(e));
+    }
+    cudaFree(tmp);
+    return st;
+}
+
+lb_status lb_get_populations(lb_grid* G, double* f, double* g) {
+    if (!G) return fail(LB_ERR_ARG, "grid is NULL");
+    return lb_get_window(G, 0, 0, G->nx, G->ny, f, g);
+}
+
+}  // extern "C"

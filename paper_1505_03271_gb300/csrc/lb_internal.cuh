@@ -1,0 +1,212 @@
+// lb_internal.cuh -- types and device helpers shared by the library's CUDA
+// translation units (not part of the public ABI; see include/lb.h).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/lb.h"
+
+namespace lbgb {
+
+constexpr int Q = 9;
+
+// D2Q9 lattice in the order of include/lb.h (Sec. II, D3Q19 reduced to 2-D).
+__host__ __device__ constexpr int cx(int a) {
+    return a == 1 || a == 5 || a == 8 ? 1 : (a == 3 || a == 6 || a == 7 ? -1 : 0);
+}
+__host__ __device__ constexpr int cy(int a) {
+    return a == 2 || a == 5 || a == 6 ? 1 : (a == 4 || a == 7 || a == 8 ? -1 : 0);
+}
+__host__ __device__ constexpr int inv(int a) {
+    return a == 0 ? 0 : (a <= 4 ? ((a + 1) & 3) + 1 : ((a - 3) & 3) + 5);
+}
+template <typename R>
+__host__ __device__ constexpr R wgt(int a) {
+    return a == 0 ? R(4) / R(9) : (a <= 4 ? R(1) / R(9) : R(1) / R(36));
+}
+static_assert(inv(1) == 3 && inv(3) == 1 && inv(2) == 4 && inv(4) == 2, "inv");
+static_assert(inv(5) == 7 && inv(7) == 5 && inv(6) == 8 && inv(8) == 6 && inv(0) == 0, "inv");
+
+// ---- storage types ----
+// The state holds f - w rho_ref(y) and g - w T_ref(y), deviations from a
+// per-row reference state: the hydrostatic, conductive base state of a grid
+// with plates (barometric rho_ref, linear T_ref), else rho_ref = 1, T_ref =
+// T0.  Kernels add w roff[y] (roff = rho_ref - 1) and w toff[y]
+// (toff = T_ref - T0) on load and work with f - w and g - w T0 in
+// registers.  With 16-bit storage the stored values are then small, so the
+// slow departures from the base state (buoyancy, wall gradients) keep their
+// precision instead of vanishing below half an ulp.
+template <typename S> struct Store;
+template <> struct Store<double> {
+    __device__ static double ld(const double* p) { return __ldg(p); }
+    __device__ static void st(double* p, double v) { *p = v; }
+};
+template <> struct Store<float> {
+    __device__ static float ld(const float* p) { return __ldg(p); }
+    __device__ static void st(float* p, float v) { *p = v; }
+};
+template <> struct Store<__half> {
+    __device__ static float ld(const __half* p) { return __half2float(__ldg(p)); }
+    __device__ static void st(__half* p, float v) { *p = __float2half_rn(v); }
+};
+template <> struct Store<__nv_bfloat16> {
+    __device__ static float ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
+    __device__ static void st(__nv_bfloat16* p, float v) { *p = __float2bfloat16_rn(v); }
+};
+
+// Per-axis metric in compute precision: for faces k = 0..n the QUICK
+// weights wp[0..2][k] (nodes k-2, k-1, k; used when c > 0) and wm[0..2][k]
+// (nodes k-1, k, k+1; c < 0); then 1/dx for cells 0..n-1.
+// Layout: [6][n + 1] followed by [n].
+template <typename R>
+struct AxisMetric {
+    const R* m;
+    int n1;  // n + 1
+    __device__ R wp(int r, int k) const { return __ldg(m + r * n1 + k); }
+    __device__ R wm(int r, int k) const { return __ldg(m + (3 + r) * n1 + k); }
+    __device__ R invd(int i) const { return __ldg(m + 6 * n1 + i); }
+};
+
+// Parameters of one step, in compute precision R.
+template <typename R>
+struct StepArgs {
+    const void* fin;
+    void* fout;
+    const void* gin;
+    void* gout;
+    int nx, ny, pitch;
+    long long plane;  // pitch * ny
+    int bcx, bcy;
+    AxisMetric<R> mx, my;
+    R dt, om, omh, cf, hf;  // dt/tau~, dt/(2 tau~), dt (1 - dt/(2 tau~)), dt/2
+    R omg, omgh;            // dt/tau~_g, dt/(2 tau~_g)
+    R ax, ay, bg;           // external acceleration, beta * grav
+    R dTb, dTt;             // T_bot - T0, T_top - T0
+    R T0;                   // reference temperature
+    const R* toff;          // per-row storage offset of g (thermal grids)
+    const R* roff;          // per-row storage offset of f
+};
+
+// Wrap or reject a global index on one axis: periodic axes wrap, wall axes
+// reject indices outside the domain.
+__device__ __forceinline__ bool map_axis(int g, int n, int bc, int& out) {
+    if (g >= 0 && g < n) {
+        out = g;
+        return true;
+    }
+    if (bc == LB_BC_PERIODIC) {
+        int r = g % n;
+        out = r < 0 ? r + n : r;
+        return true;
+    }
+    return false;
+}
+
+// Macroscopic moments of one cell from deviation populations d (and e):
+// rho = 1 + sum d, u = sum c d / rho + dt/2 a, T - T0 = sum e,
+// a = (ax, ay + beta grav (T - T0)).
+template <typename R, bool TH>
+struct Cell {
+    R rp, rho, ux, uy, Td, ay;  // rp = rho - 1, kept unrounded
+    __device__ __forceinline__ void moments(const R* d, const R* e, const StepArgs<R>& A) {
+        R r = 0, jx = 0, jy = 0;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            r += d[a];
+            jx += R(cx(a)) * d[a];
+            jy += R(cy(a)) * d[a];
+        }
+        Td = 0;
+        if (TH) {
+#pragma unroll
+            for (int a = 0; a < Q; ++a) Td += e[a];
+        }
+        rp = r;
+        rho = R(1) + r;
+        ay = A.ay + (TH ? A.bg * Td : R(0));
+        R ir = R(1) / rho;
+        ux = jx * ir + A.hf * A.ax;
+        uy = jy * ir + A.hf * ay;
+    }
+    // f_eq - w, Guo force F (Eq. (F2)) and, if thermal, g_eq - w T0.
+    __device__ __forceinline__ void eq(int a, const StepArgs<R>& A, R& feqd, R& F,
+                                       R& geqd) const {
+        const R w = wgt<R>(a);
+        const R cu = R(cx(a)) * ux + R(cy(a)) * uy;
+        const R uu = ux * ux + uy * uy;
+        const R poly = R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu;
+        feqd = w * (rp + rho * poly);
+        const R ca = R(cx(a)) * A.ax + R(cy(a)) * ay;
+        const R ua = ux * A.ax + uy * ay;
+        F = w * rho * (R(3) * (ca - ua) + R(9) * cu * ca);
+        if (TH) geqd = w * (Td + (Td + A.T0) * poly);
+    }
+};
+
+}  // namespace lbgb
+
+// ---- launchers (implemented in the kernel translation units) ----
+namespace lbgb {
+enum class Prec { F64, F32, F16, BF16 };
+
+cudaError_t launch_st(Prec p, bool thermal, const void* args, cudaStream_t s);
+cudaError_t launch_fv(Prec p, bool thermal, const void* args, cudaStream_t s);
+
+struct AuxArgs {
+    const void* f;  // state buffers (deviation storage)
+    const void* g;
+    int nx, ny, pitch;
+    long long plane;
+    double dt, ax, ay, bg, T0;
+    const double* toff; // per-row storage offset of g (thermal grids)
+    const double* roff; // per-row storage offset of f
+    const double* dxv;  // cell widths x (nx), FP64
+    const double* dyv;  // cell widths y (ny)
+    const double* xc;   // centres x
+    const double* yc;   // centres y
+};
+
+// Moments of every cell into out[4][ny][nx] (rho, ux, uy, T), FP64.
+cudaError_t launch_moments(Prec p, bool thermal, const AuxArgs& a, double* out, cudaStream_t s);
+// Block partial sums of the reduction quantities (kRed values) then a final
+// fixed-order sum into out[kRed].
+constexpr int kRed = 10;
+cudaError_t launch_reduce(Prec p, bool thermal, const AuxArgs& a, double* partial, int nblocks,
+                          double* out, cudaStream_t s);
+int reduce_blocks(int nx, int ny);
+
+// Populations FP64 host layout [9][ny][nx] (device copy) -> storage, and back.
+// Stored value = value - w (off + rowoff[y]); rowoff may be NULL.
+cudaError_t launch_pack(Prec p, const double* src, void* dst, int nx, int ny, int pitch,
+                        long long plane, double off, const double* rowoff, cudaStream_t s);
+// Window [9][h][w] starting at (x0, y0), indices wrapping modulo nx, ny.
+cudaError_t launch_unpack(Prec p, const void* src, double* dst, int nx, int ny, int pitch,
+                          long long plane, double off, const double* rowoff, int x0, int y0, int w,
+                          int h, cudaStream_t s);
+
+struct InitArgs {
+    void* f;
+    void* g;
+    int nx, ny, pitch;
+    long long plane;
+    int kind, mode;
+    double u0, amp;
+    unsigned long long seed;
+    double lx, ly;
+    double dt, ax, ay, bg, T0, Tb, Tt;
+    double rho_norm;
+    const double* toff;
+    const double* roff;
+    const double* xc;
+    const double* yc;
+    const double* fields;  // LB_INIT_FIELDS: [4][ny][nx] rho, ux, uy, T on device
+};
+cudaError_t launch_init(Prec p, bool thermal, const InitArgs& a, cudaStream_t s);
+
+void count_launch();
+}  // namespace lbgb

@@ -1,0 +1,77 @@
+"""Host-side checks that need no GPU: the C-ABI library builds for sm_103a,
+loads, and exports every entry point that include/lb.h declares; the
+parameter rules of the workloads reproduce the paper's numbers."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared_symbols():
+    text = open(os.path.join(ROOT, "include", "lb.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lb_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared_symbols()
+    for required in ("lb_create_grid", "lb_init", "lb_step_fv", "lb_step_st", "lb_moments",
+                     "lb_nusselt", "lb_conservation", "lb_destroy", "lb_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    import paper_1505_03271_gb300 as lb
+    L = lb.load()
+    for name in _declared_symbols():
+        assert hasattr(L, name), name
+    assert set(lb.SYMBOLS) == set(_declared_symbols())
+    from paper_1505_03271_gb300 import _build
+    assert "arch=compute_103a,code=sm_103a" in _build.ARCH
+
+
+def test_last_error_without_gpu_work():
+    import paper_1505_03271_gb300 as lb
+    lb.load()
+    assert isinstance(lb.lb_last_error(), str)
+    assert lb.lb_kernel_launches() >= 0
+
+
+def test_struct_layouts_match_header():
+    """ctypes mirrors of the C structs have the C sizes (int/double/pointer)."""
+    import paper_1505_03271_gb300 as lb
+    assert ctypes.sizeof(lb.lb_grid_desc) == 2 * 4 + 2 * 8 + 2 * 4 + 2 * 8 + 4 * 4 + 8
+    assert ctypes.sizeof(lb.lb_params) == 10 * 8
+    assert ctypes.sizeof(lb.lb_init_desc) == 2 * 4 + 2 * 8 + 8 + 4 * 8
+
+
+def test_rb_parameter_rule_and_table():
+    from paper_1505_03271_gb300 import configs as cfg
+    for Ra, H in ((1e4, 64.0), (1e8, 1024.0)):
+        p = cfg.rb_params(Ra, 1.0, H)
+        assert abs(cfg.rayleigh(p, H) / Ra - 1) < 1e-12
+        assert abs(np.sqrt(p.beta * p.grav * (p.T_bot - p.T_top) * H) - 0.1) < 1e-12
+    # Table rb (Sec. IV): both rows give Ra = 2.5e6 with nu = tau c_s^2
+    fv = cfg.RBParams(0.5, 0.5, 1.325e-4, 1.0, 1.0, 2.0, 0.0)
+    st = cfg.RBParams(0.05, 0.05, 1.325e-3, 1.0, 1.0, 2.0, 0.0)
+    assert abs(cfg.rayleigh(fv, 640.0) / 2.5e6 - 1) < 1e-3
+    assert abs(cfg.rayleigh(st, 64.0) / 2.5e6 - 1) < 1e-3
+
+
+def test_workload_rules():
+    from paper_1505_03271_gb300 import configs as cfg
+    w = cfg.channel()
+    assert w.grid["nx"] == 256 and w.grid["ny"] == 512
+    assert abs(w.params["tau"] - 0.2) < 1e-15
+    assert abs(w.notes["Re"] - 10.0) < 1e-12
+    dmin = cfg.min_cell(512, 512.0, 1, 2.0)
+    assert 0.14 < dmin < 0.16
+    assert abs(w.params["dt"] - 0.9 * dmin) < 1e-15
+    t = cfg.tgv64("st")
+    assert t.steps == 1000 and abs(t.params["tau"] - 0.3) < 1e-15
+    assert cfg.bytes_per_cell(1, False) == 72 and cfg.bytes_per_cell(2, True) == 72
+    assert cfg.bytes_per_cell(0, True) == 288

@@ -1,0 +1,352 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs, element by element, at small sizes spanning several tiles
+with ragged tails, and on sampled windows at the full workload sizes."""
+import os
+
+import numpy as np
+import pytest
+
+from tests import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _threads(oracle):
+    oracle.set_threads(os.cpu_count() or 1)
+
+
+def pair(lb, O, nx, ny, store, lx=None, ly=None, sx=0, sy=0, stretch_x=0.0, stretch_y=0.0,
+         bcx=0, bcy=0, thermal=False, **params):
+    g = lb.Grid(nx, ny, lx, ly, sx, sy, stretch_x, stretch_y, bcx, bcy, thermal, store)
+    r = O.RefGrid(nx, ny, lx, ly, sx, sy, stretch_x, stretch_y, bcx, bcy, thermal)
+    init = {k: params.pop(k) for k in ("kind", "u0", "amp", "mode", "seed") if k in params}
+    r.set_params(**params)
+    g.init(**params, **init)
+    if init:
+        r.init_preset({0: O.INIT_TGV, 1: O.INIT_SHEAR, 2: O.INIT_POISEUILLE, 3: O.INIT_RB}[init["kind"]],
+                      init.get("u0", 0.0), init.get("amp", 0.0), init.get("mode", 1),
+                      init.get("seed", 0))
+    return g, r
+
+
+def rel_l2_u(g, r):
+    _, ux, uy, _ = g.moments()
+    _, vx, vy, _ = r.moments()
+    return np.sqrt(((ux - vx) ** 2 + (uy - vy) ** 2).sum() / (vx**2 + vy**2).sum())
+
+
+# ------------------------------------------------------------------- init --
+
+@pytest.mark.parametrize("case", ["tgv", "shear", "poiseuille", "rb"])
+def test_init_presets(lbgpu, oracle, case):
+    lb = lbgpu
+    if case == "tgv":
+        g, r = pair(lb, oracle, 40, 24, lb.LB_STORE_F64, tau=0.3, dt=0.5, ax=1e-4, kind=0, u0=0.02,
+                    amp=0.01, mode=2)
+    elif case == "shear":
+        g, r = pair(lb, oracle, 1, 64, lb.LB_STORE_F64, lx=1.0, tau=0.3, kind=1, amp=0.01, mode=1)
+    elif case == "poiseuille":
+        g, r = pair(lb, oracle, 8, 30, lb.LB_STORE_F64, sy=1, stretch_y=2.0, bcy=1, tau=0.2, dt=0.1,
+                    ax=1e-6, kind=2, u0=0.05)
+    else:
+        g, r = pair(lb, oracle, 33, 20, lb.LB_STORE_F64, sy=1, stretch_y=2.0, bcy=1, thermal=True,
+                    tau=0.05, tau_g=0.05, dt=0.1, beta=1e-4, grav=1.0, T0=1.0, T_bot=1.5, T_top=0.5,
+                    kind=3, amp=1e-3, seed=1234)
+    fg, gg = g.get_pops()
+    fr, gr = r.get_pops()
+    assert np.abs(fg - fr).max() < 1e-15
+    if gg is not None:
+        assert np.abs(gg - gr).max() < 1e-15
+
+
+@pytest.mark.parametrize("store,tol", [("f64", 0.0), ("f32", 1e-8), ("bf16dev", 2e-3), ("f16dev", 2e-4)])
+def test_population_roundtrip(lbgpu, store, tol):
+    g = lbgpu.Grid(19, 11, thermal=True, store=store)
+    g.init(tau=0.3, T0=1.0)
+    f = inputs.random_populations(11, 19, seed=1, amp=0.1).reshape(9, 11, 19)
+    gg = inputs.random_populations(11, 19, seed=2, amp=0.1).reshape(9, 11, 19)
+    g.set_pops(f, gg)
+    f2, g2 = g.get_pops()
+    assert np.abs(f2 - f).max() <= tol * 0.5 + 1e-300
+    assert np.abs(g2 - gg).max() <= tol * 0.5 + 1e-300
+    w = g.get_window(17, 9, 5, 4)[0]  # wraps across both periodic edges
+    cols = [(17 + i) % 19 for i in range(5)]
+    rows = [(9 + j) % 11 for j in range(4)]
+    assert np.array_equal(w, f2[:, rows][:, :, cols])
+
+
+# ------------------------------------------------------- step parity F64 --
+
+ST_CASES = [
+    dict(nx=13, ny=7),
+    dict(nx=37, ny=19, bcy=1),
+    dict(nx=16, ny=9, bcx=1, bcy=1),
+    dict(nx=300, ny=5),
+    dict(nx=20, ny=12, bcy=1, thermal=True),
+    dict(nx=1, ny=10),
+]
+
+
+@pytest.mark.parametrize("case", ST_CASES, ids=lambda c: "x".join(map(str, c.values())))
+def test_st_step_f64(lbgpu, oracle, case):
+    nx, ny = case["nx"], case["ny"]
+    th = case.get("thermal", False)
+    kw = dict(tau=0.3, dt=1.0, ax=2e-4, ay=-1e-4)
+    if th:
+        kw.update(tau_g=0.25, beta=1e-2, grav=1.0, T0=1.0, T_bot=1.3, T_top=0.8)
+    g, r = pair(lbgpu, oracle, store=lbgpu.LB_STORE_F64, **case, **kw)
+    f = inputs.random_populations(nx, ny, seed=nx + ny, amp=0.2)
+    gg = inputs.random_populations(nx, ny, seed=7, amp=0.2) if th else None
+    g.set_pops(f, gg)
+    r.set_pops(f, gg)
+    g.step_st(5)
+    r.step_st(5)
+    fg, ggg = g.get_pops()
+    fr, ggr = r.get_pops()
+    assert np.abs(fg - fr).max() < 1e-14
+    if th:
+        assert np.abs(ggg - ggr).max() < 1e-14
+
+
+FV_CASES = [
+    dict(nx=70, ny=37),
+    dict(nx=45, ny=33, sy=1, stretch_y=1.5),
+    dict(nx=50, ny=40, sy=1, stretch_y=2.0, bcy=1),
+    dict(nx=35, ny=34, sx=1, stretch_x=1.0, sy=2, stretch_y=4.0, bcx=1, bcy=1),
+    dict(nx=40, ny=36, sy=1, stretch_y=2.0, bcy=1, thermal=True),
+    dict(nx=5, ny=3),
+    dict(nx=1, ny=64, lx=1.0),
+    dict(nx=4, ny=2, bcy=1),
+    dict(nx=33, ny=17, bcx=1),
+]
+
+
+@pytest.mark.parametrize("case", FV_CASES, ids=lambda c: "-".join(f"{k}{v}" for k, v in c.items()))
+def test_fv_step_f64(lbgpu, oracle, case):
+    nx, ny = case["nx"], case["ny"]
+    th = case.get("thermal", False)
+    kw = dict(tau=0.3, dt=0.05, ax=2e-4, ay=-1e-4)
+    if th:
+        kw.update(tau_g=0.25, beta=1e-2, grav=1.0, T0=1.0, T_bot=1.3, T_top=0.8)
+    g, r = pair(lbgpu, oracle, store=lbgpu.LB_STORE_F64, **case, **kw)
+    f = inputs.random_populations(nx, ny, seed=3 * nx + ny, amp=0.2)
+    gg = inputs.random_populations(nx, ny, seed=11, amp=0.2) if th else None
+    g.set_pops(f, gg)
+    r.set_pops(f, gg)
+    g.step_fv(3)
+    r.step_fv(3)
+    fg, ggg = g.get_pops()
+    fr, ggr = r.get_pops()
+    assert np.abs(fg - fr).max() < 1e-13
+    if th:
+        assert np.abs(ggg - ggr).max() < 1e-13
+
+
+@pytest.mark.parametrize("store", ["f32"])
+@pytest.mark.parametrize("scheme", ["st", "fv"])
+def test_f32_paths(lbgpu, oracle, scheme, store):
+    """FP32 arithmetic on deviations: relative L2 velocity error <= 1e-5."""
+    dt = 1.0 if scheme == "st" else 0.5
+    g, r = pair(lbgpu, oracle, 64, 48, store, ly=48.0, tau=0.3, dt=dt, ax=1e-6, kind=0, u0=0.02)
+    for x in (g, r):
+        (x.step_st if scheme == "st" else x.step_fv)(200)
+    assert rel_l2_u(g, r) < 1e-5
+
+
+# ---------------------------------------------------- full-size workloads --
+
+@pytest.mark.parametrize("scheme", ["st", "fv"])
+def test_config_tgv64_f64(lbgpu, oracle, scheme):
+    """64x64 periodic TGV in FP64 for t = 1000: GPU = oracle to 1e-12 (relative
+    L2 of u) and the decay follows exp(-2 nu k^2 t)."""
+    from paper_1505_03271_gb300 import configs as cfg
+    w = cfg.tgv64(scheme)
+    g, r = pair(lbgpu, oracle, 64, 64, w.grid["store"], **w.params, **w.init)
+    _, ux0, _, _ = g.moments()
+    for x in (g, r):
+        (x.step_st if scheme == "st" else x.step_fv)(w.steps)
+    assert rel_l2_u(g, r) < 1e-12
+    _, ux, _, _ = g.moments()
+    xc = yc = np.arange(64) + 0.5
+    k = 2 * np.pi / 64
+    mode = -np.cos(k * xc)[None, :] * np.sin(k * yc)[:, None]
+    ratio = (ux * mode).sum() / (ux0 * mode).sum()
+    assert abs(ratio / np.exp(-2 * 0.1 * k * k * 1000) - 1) < (0.01 if scheme == "st" else 0.02)
+
+
+def test_config_channel_f32(lbgpu, oracle):
+    """256 x 512 tanh channel, FP32, U = 0.05 variant: 1000 FV steps match the
+    oracle (relative L2 of u <= 1e-5)."""
+    from paper_1505_03271_gb300 import configs as cfg
+    w = cfg.channel(u_max=0.05)
+    g, r = pair(lbgpu, oracle, store=w.grid.pop("store"), **w.grid, **w.params, **w.init)
+    g.step_fv(1000)
+    r.step_fv(1000)
+    assert rel_l2_u(g, r) < 1e-5
+
+
+def test_config_channel_re10_holds_parabola(lbgpu):
+    """The Re = 10 channel for the full 20000 steps stays on the parabola
+    (relative weighted L2 error below 1e-3; Sec. III B)."""
+    from paper_1505_03271_gb300 import configs as cfg
+    w = cfg.channel()
+    grid = dict(w.grid)
+    g = lbgpu.Grid(store=grid.pop("store"), **grid)
+    g.init(**w.params, **w.init)
+    g.step_fv(w.steps)
+    _, ux, _, _ = g.moments()
+    xi = cfg.faces(512, 512.0, 1, 2.0)
+    yc, dy = 0.5 * (xi[1:] + xi[:-1]), np.diff(xi)
+    U = 4 * w.notes["U"] * yc * (512 - yc) / 512**2
+    err = np.sqrt((((ux - U[:, None]) ** 2) * dy[:, None]).sum() / ((U[:, None] ** 2) * dy[:, None]).sum() / 256)
+    assert err < 1e-3
+
+
+def _strip_compare(lb, O, w, steps, strip, x0, tol_rel):
+    """Sample a full-height strip of a large x-periodic grid: the oracle runs
+    the strip (periodic in x) from the GPU's own state; cells 4*steps away from
+    the strip's x-edges are unaffected by the cut and must match."""
+    grid = dict(w.grid)
+    store = grid.pop("store")
+    g = lb.Grid(store=store, **grid)
+    g.init(**w.params, **w.init)
+    ny = grid["ny"]
+    f0, g0 = g.get_window(x0, 0, strip, ny)
+    r = O.RefGrid(strip, ny, float(strip), grid.get("ly", ny), 0, grid.get("sy", 0), 0.0,
+                  grid.get("stretch_y", 0.0), 0, grid.get("bcy", 0), grid.get("thermal", False))
+    r.set_params(**w.params)
+    r.set_pops(f0, g0)
+    (g.step_st if w.scheme == "st" else g.step_fv)(steps)
+    (r.step_st if w.scheme == "st" else r.step_fv)(steps)
+    f1, g1 = g.get_window(x0, 0, strip, ny)
+    fr, gr = r.get_pops()
+    halo = (1 if w.scheme == "st" else 4) * steps
+    sl = slice(halo, strip - halo)
+    scale = np.abs(f0 - O.lattice()[2][:, None, None]).max()
+    assert np.abs(f1[:, :, sl] - fr[:, :, sl]).max() <= tol_rel * scale
+    if g1 is not None:
+        gscale = np.abs(g0 - O.lattice()[2][:, None, None] * w.params["T0"]).max()
+        assert np.abs(g1[:, :, sl] - gr[:, :, sl]).max() <= tol_rel * gscale
+
+
+@pytest.mark.parametrize("store,tol", [("f32", 1e-5), ("bf16dev", 2e-2), ("f16dev", 3e-3)])
+def test_config_st8192_sampled(lbgpu, oracle, store, tol):
+    """8192^2 periodic ST (TGV + shear wave): 40x40 windows (three spots, two
+    crossing the periodic edges) are advanced 3 steps by the oracle from the
+    GPU's stored state; cells 3 away from the window edge must match."""
+    from paper_1505_03271_gb300 import configs as cfg
+    w = cfg.st_sweep(8192, lbgpu.STORE_NAMES[store])
+    grid = dict(w.grid)
+    g = lbgpu.Grid(store=grid.pop("store"), **grid)
+    g.init(**w.params, **w.init)
+    n, k = 40, 3
+    spots = [(0, 0), (4000, 8170), (8180, 123)]
+    refs = []
+    for x0, y0 in spots:
+        f0, _ = g.get_window(x0 - k, y0 - k, n, n)
+        r = oracle.RefGrid(n, n).set_params(**w.params).set_pops(f0)
+        r.step_st(k)
+        refs.append((f0, r.get_pops()[0]))
+    g.step_st(k)
+    inner = slice(k, n - k)
+    wts = oracle.lattice()[2][:, None, None]
+    for (x0, y0), (f0, fr) in zip(spots, refs):
+        f1, _ = g.get_window(x0 - k, y0 - k, n, n)
+        scale = np.abs(f0 - wts).max()
+        assert np.abs(f1[:, inner, inner] - fr[:, inner, inner]).max() <= tol * scale
+
+
+def test_config_rb1024_strip(lbgpu, oracle):
+    """1024^2 RB at Ra = 1e8 with FP16 deviation storage: a full-height strip
+    advanced 2 FV steps by the oracle from the GPU's state matches the GPU."""
+    from paper_1505_03271_gb300 import configs as cfg
+    w = cfg.rayleigh_benard(1024, 1e8, store=lbgpu.LB_STORE_F16DEV)
+    _strip_compare(lbgpu, oracle, w, 2, 24, 500, 4e-3)
+
+
+def test_config_channel_strip_f32(lbgpu, oracle):
+    from paper_1505_03271_gb300 import configs as cfg
+    w = cfg.channel(u_max=0.05)
+    _strip_compare(lbgpu, oracle, w, 3, 30, 100, 1e-5)
+
+
+# ------------------------------------------------------------ observables --
+
+def test_conservation_and_nusselt(lbgpu, oracle):
+    nx, ny = 48, 40
+    g, r = pair(lbgpu, oracle, nx, ny, lbgpu.LB_STORE_F64, sy=1, stretch_y=2.0, bcy=1, thermal=True,
+                tau=0.2, tau_g=0.2, dt=0.1, beta=1e-3, grav=1.0, T0=1.0, T_bot=1.5, T_top=0.5)
+    f = inputs.random_populations(nx, ny, seed=5, amp=0.1)
+    gg = inputs.random_populations(nx, ny, seed=6, amp=0.1)
+    g.set_pops(f, gg)
+    r.set_pops(f, gg)
+    for a, b in zip(g.conservation(), r.conservation()):
+        assert abs(a - b) <= 1e-12 * abs(b) + 1e-15
+    for a, b in zip(g.nusselt(), r.nusselt()):
+        assert abs(a - b) <= 1e-10 * max(1.0, abs(b))
+    rho, ux, uy, T = g.moments()
+    for a, b in zip((rho, ux, uy, T), r.moments()):
+        assert np.abs(a - b).max() < 1e-14
+
+
+def test_rb_nusselt_f16_vs_oracle(lbgpu, oracle):
+    """Reduced-precision storage: FP16 deviation storage keeps the Nusselt
+    numbers within 1e-3 of the FP64 oracle over 500 FV steps of an RB cell."""
+    from paper_1505_03271_gb300 import configs as cfg
+    w = cfg.rayleigh_benard(128, 1e6, store=lbgpu.LB_STORE_F16DEV, steps=500)
+    grid = dict(w.grid)
+    grid.pop("store")
+    g, r = pair(lbgpu, oracle, store=lbgpu.LB_STORE_F16DEV, **grid, **w.params, **w.init)
+    g.step_fv(w.steps)
+    r.step_fv(w.steps)
+    for a, b in zip(g.nusselt(), r.nusselt()):
+        assert abs(a / b - 1) < 1e-3
+
+
+# ------------------------------------------------------- errors and edges --
+
+def test_error_statuses(lbgpu):
+    lb = lbgpu
+    with pytest.raises(lb.LBError) as e:
+        lb.Grid(0, 4)
+    assert e.value.status == lb.LB_ERR_ARG
+    with pytest.raises(lb.LBError) as e:
+        lb.Grid(8, 1, bcy=1)
+    assert e.value.status == lb.LB_ERR_ARG
+    g = lb.Grid(16, 16, sy=1, stretch_y=2.0)
+    with pytest.raises(lb.LBError) as e:
+        g.step_fv(1)
+    assert e.value.status == lb.LB_ERR_STATE
+    g.init(tau=0.3, dt=1.0)
+    with pytest.raises(lb.LBError) as e:
+        g.step_st(1)  # streaming needs a uniform unit lattice
+    assert e.value.status == lb.LB_ERR_ARG
+    with pytest.raises(lb.LBError) as e:
+        g.nusselt()
+    assert e.value.status == lb.LB_ERR_STATE
+    g.step_fv(0)
+    f = np.full((9, 16, 16), np.nan)
+    g.set_pops(f)
+    with pytest.raises(lb.LBError) as e:
+        g.conservation()
+    assert e.value.status == lb.LB_ERR_UNSTABLE
+    with pytest.raises(lb.LBError) as e:
+        g.step_fv(1)
+    assert e.value.status == lb.LB_ERR_STATE
+    g.init(tau=0.3, dt=1.0, kind=lb.LB_INIT_TGV, u0=0.01)
+    g.step_fv(1)
+    assert np.isfinite(g.conservation()[0])
+
+
+def test_deterministic(lbgpu):
+    outs = []
+    for _ in range(2):
+        g = lbgpu.Grid(100, 60, sy=1, stretch_y=2.0, bcy=1, thermal=True, store="f32")
+        g.init(tau=0.1, tau_g=0.1, dt=0.1, beta=1e-3, grav=1.0, T0=1.0, T_bot=1.5, T_top=0.5,
+               kind=lbgpu.LB_INIT_RB, amp=1e-2, seed=9)
+        g.step_fv(20)
+        outs.append((g.get_pops(), g.nusselt()))
+    assert np.array_equal(outs[0][0][0], outs[1][0][0])
+    assert np.array_equal(outs[0][0][1], outs[1][0][1])
+    assert outs[0][1] == outs[1][1]
