@@ -161,6 +161,33 @@ lb_status lb_get_populations(lb_grid* grid, double* f, double* g);
  * copy whole.  LB_ERR_ARG if w or h is < 1 or larger than the grid. */
 lb_status lb_get_window(lb_grid* grid, int x0, int y0, int w, int h, double* f, double* g);
 
+/* Mass, momentum and heat sums of lb_conservation (sum V rho, sum V rho u_x,
+ * sum V rho u_y, sum V T) for a state held in caller-owned device buffers,
+ * computed without allocating any memory.  The paper has no counterpart: this
+ * entry point exists for callers that cannot call cudaMalloc, such as a
+ * process whose device memory is owned by its own pool or arena (a serving
+ * engine that reserves HBM at start-up, a framework's caching allocator) or
+ * code on a latency-critical path where an allocation would synchronise the
+ * device.  Such a caller cannot create an lb_grid, which allocates.
+ *   f, g   device, FP32, [9][ny][pitch]: f - w_a and g - w_a T0 (g may be NULL
+ *          for a flow-only state); pitch >= nx elements.
+ *   dx, dy device, FP64 cell widths (nx and ny values).
+ *   dt, ax, ay, beta_grav, T0: as in lb_params (beta_grav = beta * grav), used
+ *          for the force-corrected velocity u = sum c f / rho + dt/2 a.
+ *   out    device, 4 doubles, written asynchronously on cuda_stream (NULL =
+ *          default stream); read it after the stream has synchronised.
+ * Its scratch is a fixed array inside the library (one per GPU that loads it,
+ * held until the process exits), so a call handles at most 8,388,608 cells;
+ * larger grids return LB_ERR_ARG.  All calls share that array: calls that
+ * overlap on the GPU race and must be serialised.  The first call on a device
+ * looks up the array's address with that device current; make it before any
+ * stream capture begins.  LB_ERR_ARG on NULL or inconsistent sizes,
+ * LB_ERR_CUDA if the launch fails. */
+lb_status lb_conservation_noalloc(const float* f, const float* g, int nx, int ny, int pitch,
+                                  const double* dx, const double* dy, double dt, double ax,
+                                  double ay, double beta_grav, double T0, double* out,
+                                  void* cuda_stream);
+
 /* Wait for all work queued on the grid's stream. */
 lb_status lb_sync(lb_grid* grid);
 

@@ -59,7 +59,8 @@ class lb_init_desc(C.Structure):
 
 SYMBOLS = ["lb_create_grid", "lb_init", "lb_step_fv", "lb_step_st", "lb_moments",
            "lb_conservation", "lb_nusselt", "lb_set_populations", "lb_get_populations",
-           "lb_get_window", "lb_sync", "lb_destroy", "lb_last_error", "lb_kernel_launches"]
+           "lb_get_window", "lb_sync", "lb_destroy", "lb_last_error", "lb_kernel_launches",
+           "lb_conservation_noalloc"]
 
 _lib = None
 
@@ -89,6 +90,9 @@ def load(build: bool = True) -> C.CDLL:
     L.lb_set_populations.argtypes = [G, _DP, _DP]
     L.lb_get_populations.argtypes = [G, _DP, _DP]
     L.lb_get_window.argtypes = [G, C.c_int, C.c_int, C.c_int, C.c_int, _DP, _DP]
+    L.lb_conservation_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
+                                          C.c_void_p, C.c_void_p] + [C.c_double] * 5 + [
+                                          C.c_void_p, C.c_void_p]
     L.lb_sync.argtypes = [G]
     L.lb_destroy.argtypes = [G]
     L.lb_last_error.restype = C.c_char_p
@@ -164,6 +168,16 @@ def lb_get_populations(grid, f, g) -> None:
 
 def lb_get_window(grid, x0, y0, w, h, f, g) -> None:
     _check(load().lb_get_window(grid, int(x0), int(y0), int(w), int(h), _ptr(f), _ptr(g)))
+
+
+def lb_conservation_noalloc(f_ptr, g_ptr, nx, ny, pitch, dx_ptr, dy_ptr, dt, ax, ay, beta_grav,
+                            T0, out_ptr, stream=None) -> None:
+    """Conservation sums of caller-owned device buffers (raw device addresses
+    as ints), without any allocation; `out_ptr` receives 4 doubles on
+    `stream`.  See include/lb.h for the limits."""
+    _check(load().lb_conservation_noalloc(f_ptr, g_ptr, int(nx), int(ny), int(pitch), dx_ptr,
+                                          dy_ptr, float(dt), float(ax), float(ay),
+                                          float(beta_grav), float(T0), out_ptr, stream))
 
 
 def lb_sync(grid) -> None:

@@ -127,6 +127,8 @@ size_t elem_size(int store) {
 
 namespace lbgb {
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+// Record a failure message for lb_last_error() from another translation unit.
+lb_status set_last_error(lb_status s, const char* msg) { return fail(s, "%s", msg); }
 }  // namespace lbgb
 
 struct lb_grid {
