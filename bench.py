@@ -101,12 +101,23 @@ class ClockSampler:
 
 # --------------------------------------------------------------------- GPU --
 
-def make_grid(lb, w, stream):
+def make_grid(lb, w, stream, tune=True):
+    """Grid of a workload; FV grids run the library's autotuner (it restores
+    the state it times on), so the timed steps use the schedule it picked."""
     grid = dict(w.grid)
     store = grid.pop("store")
     g = lb.Grid(store=store, stream=stream, **grid)
     g.init(**w.params, **w.init)
+    if tune and w.scheme == "fv":
+        g.autotune_fv(5)
     return g
+
+
+def schedule_name(lb, g, scheme):
+    if scheme != "fv":
+        return "st push, one thread per cell"
+    k, c = g.fv_schedule()
+    return "fv tile 32x16 (halo 4)" if k == lb.LB_FV_TILE else "fv march, %d rows per CTA" % c
 
 
 def time_steps(lb, torch, g, scheme, steps, warmup, flush=None):
@@ -149,7 +160,7 @@ def extra_lines(lb, torch, cfg, stream, peak, peak_kind, flush):
         mean = sum(ms) / len(ms)
         bpc = cfg.bytes_per_cell(w.grid["store"], w.grid.get("thermal", False))
         out[name] = {"mlups": round(w.cells / (mean * 1e-3) / 1e6, 1), "ms_per_step": round(mean, 5),
-                     "bytes_per_cell": bpc,
+                     "bytes_per_cell": bpc, "schedule": schedule_name(lb, g, w.scheme),
                      "roofline": roofline(bpc * w.cells, mean, peak, peak_kind),
                      "cells": w.cells, "l2": "flushed" if fl is not None else "state > L2"}
         g.close()
@@ -347,6 +358,7 @@ def main():
             "roofline": roofline(bpc * w.cells, mean_ms, peak, peak_kind),
             "clocks": clk.summary()}
     line["config"]["parallelism"] = "replicas" if world > 1 else "single"
+    line["config"]["schedule"] = schedule_name(lb, g, w.scheme)
     if not args.no_extra and args.case == "channel":
         line["e2e"] = e2e_measure(lb, torch, w, stream)
         line["extra"] = extra_lines(lb, torch, cfg, stream, peak, peak_kind, flush)
@@ -355,7 +367,8 @@ def main():
         O.build()
         r, done, el, thr = oracle_sample(w, budget_s=15.0)
         # error of the GPU against the oracle after the same number of steps
-        g2 = make_grid(lb, w, stream)
+        g2 = make_grid(lb, w, stream, tune=False)
+        g2.set_fv_schedule(*g.fv_schedule())
         lb.lb_step_fv(g2.handle, done)
         _, ux, uy, _ = g2.moments()
         _, vx, vy, _ = r.moments()

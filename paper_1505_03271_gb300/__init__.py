@@ -60,7 +60,9 @@ class lb_init_desc(C.Structure):
 SYMBOLS = ["lb_create_grid", "lb_init", "lb_step_fv", "lb_step_st", "lb_moments",
            "lb_conservation", "lb_nusselt", "lb_set_populations", "lb_get_populations",
            "lb_get_window", "lb_sync", "lb_destroy", "lb_last_error", "lb_kernel_launches",
-           "lb_conservation_noalloc"]
+           "lb_conservation_noalloc", "lb_set_fv_schedule", "lb_get_fv_schedule",
+           "lb_autotune_fv"]
+LB_FV_AUTO, LB_FV_TILE, LB_FV_MARCH = 0, 1, 2
 
 _lib = None
 
@@ -93,6 +95,9 @@ def load(build: bool = True) -> C.CDLL:
     L.lb_conservation_noalloc.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
                                           C.c_void_p, C.c_void_p] + [C.c_double] * 5 + [
                                           C.c_void_p, C.c_void_p]
+    L.lb_set_fv_schedule.argtypes = [G, C.c_int, C.c_int]
+    L.lb_get_fv_schedule.argtypes = [G, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.lb_autotune_fv.argtypes = [G, C.c_int]
     L.lb_sync.argtypes = [G]
     L.lb_destroy.argtypes = [G]
     L.lb_last_error.restype = C.c_char_p
@@ -178,6 +183,20 @@ def lb_conservation_noalloc(f_ptr, g_ptr, nx, ny, pitch, dx_ptr, dy_ptr, dt, ax,
     _check(load().lb_conservation_noalloc(f_ptr, g_ptr, int(nx), int(ny), int(pitch), dx_ptr,
                                           dy_ptr, float(dt), float(ax), float(ay),
                                           float(beta_grav), float(T0), out_ptr, stream))
+
+
+def lb_set_fv_schedule(grid, kernel: int, chunk: int = 0) -> None:
+    _check(load().lb_set_fv_schedule(grid, int(kernel), int(chunk)))
+
+
+def lb_get_fv_schedule(grid):
+    k, c = C.c_int(), C.c_int()
+    _check(load().lb_get_fv_schedule(grid, C.byref(k), C.byref(c)))
+    return k.value, c.value
+
+
+def lb_autotune_fv(grid, steps: int = 5) -> None:
+    _check(load().lb_autotune_fv(grid, int(steps)))
 
 
 def lb_sync(grid) -> None:
@@ -285,6 +304,17 @@ class Grid:
         g = np.empty((Q, h, w)) if self.thermal else None
         lb_get_window(self._h, x0, y0, w, h, f, g)
         return f, g
+
+    def set_fv_schedule(self, kernel, chunk=0):
+        lb_set_fv_schedule(self._h, kernel, chunk)
+        return self
+
+    def fv_schedule(self):
+        return lb_get_fv_schedule(self._h)
+
+    def autotune_fv(self, steps=5):
+        lb_autotune_fv(self._h, steps)
+        return self.fv_schedule()
 
     def sync(self):
         lb_sync(self._h)

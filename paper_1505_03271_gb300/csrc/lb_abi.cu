@@ -157,6 +157,9 @@ struct lb_grid {
     double* partial = nullptr;  // reduction partials
     double* red = nullptr;      // reduction totals
     int nred = 0;
+    int fv_kernel = LB_FV_AUTO;  // requested schedule
+    int fv_chunk = 0;
+    int sms = 0;                 // streaming multiprocessors of the device
 };
 
 namespace {
@@ -243,6 +246,37 @@ lb_status check_ready(lb_grid* G) {
     return LB_OK;
 }
 
+// Schedule actually used: AUTO takes the marching kernel once the grid is
+// wide and tall enough to fill the GPU with strips, else the tile kernel.
+int resolved_kernel(const lb_grid* G) {
+    if (G->fv_kernel != LB_FV_AUTO) return G->fv_kernel;
+    return (G->nx >= 480 && G->ny >= 256) ? LB_FV_MARCH : LB_FV_TILE;
+}
+
+// Rows per CTA of the marching kernel: one wave of resident CTAs.
+int resolved_chunk(const lb_grid* G) {
+    if (G->fv_chunk > 0) return G->fv_chunk;
+    const bool th = G->d.thermal != 0;
+    const int strips = (G->nx + march_width(G->prec, th) - 1) / march_width(G->prec, th);
+    const size_t smem = march_smem(G->prec, th);
+    int per_sm = (int)(227 * 1024 / smem);
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 4) per_sm = 4;
+    const long long slots = (long long)G->sms * per_sm;
+    long long chunks = (slots + strips - 1) / strips;
+    if (chunks < 1) chunks = 1;
+    int ch = (int)((G->ny + chunks - 1) / chunks);
+    return ch < 16 ? 16 : ch;
+}
+
+template <typename R>
+cudaError_t launch_fv_step(lb_grid* G) {
+    StepArgs<R> A = step_args<R>(G, G->p.dt);
+    const bool th = G->d.thermal != 0;
+    if (resolved_kernel(G) == LB_FV_MARCH) return launch_fv_march(G->prec, th, &A, resolved_chunk(G), G->stream);
+    return launch_fv(G->prec, th, &A, G->stream);
+}
+
 lb_status upload(void** dst, const std::vector<double>& v, bool as_float) {
     size_t bytes = v.size() * (as_float ? sizeof(float) : sizeof(double));
     CK(cudaMalloc(dst, bytes ? bytes : 8));
@@ -312,6 +346,8 @@ lb_status lb_create_grid(const lb_grid_desc* d, lb_grid** out) {
             }
     }
     cudaGetDevice(&G->device);
+    cudaDeviceGetAttribute(&G->sms, cudaDevAttrMultiProcessorCount, G->device);
+    if (G->sms <= 0) G->sms = 152;
     const size_t pop_bytes = (size_t)Q * G->plane * elem_size(d->store);
     const bool as_float = G->prec != Prec::F64;
     G->nred = reduce_blocks(G->nx, G->ny);
@@ -458,19 +494,98 @@ lb_status lb_step_fv(lb_grid* G, int nsteps) {
     if (s != LB_OK) return s;
     if (nsteps < 0) return fail(LB_ERR_ARG, "nsteps must be >= 0");
     DeviceGuard dg(G->device);
-    const bool th = G->d.thermal != 0;
     for (int k = 0; k < nsteps; ++k) {
-        cudaError_t e;
-        if (G->prec == Prec::F64) {
-            StepArgs<double> A = step_args<double>(G, G->p.dt);
-            e = launch_fv(G->prec, th, &A, G->stream);
-        } else {
-            StepArgs<float> A = step_args<float>(G, G->p.dt);
-            e = launch_fv(G->prec, th, &A, G->stream);
-        }
-        CK(e);
+        CK(G->prec == Prec::F64 ? launch_fv_step<double>(G) : launch_fv_step<float>(G));
         G->cur ^= 1;
     }
+    return LB_OK;
+}
+
+lb_status lb_set_fv_schedule(lb_grid* G, int kernel, int chunk) {
+    if (!G) return fail(LB_ERR_ARG, "grid is NULL");
+    if (kernel < LB_FV_AUTO || kernel > LB_FV_MARCH) return fail(LB_ERR_ARG, "unknown FV kernel %d", kernel);
+    if (chunk < 0) return fail(LB_ERR_ARG, "chunk must be >= 0");
+    G->fv_kernel = kernel;
+    G->fv_chunk = chunk;
+    return LB_OK;
+}
+
+lb_status lb_get_fv_schedule(lb_grid* G, int* kernel, int* chunk) {
+    if (!G) return fail(LB_ERR_ARG, "grid is NULL");
+    if (kernel) *kernel = resolved_kernel(G);
+    if (chunk) *chunk = resolved_kernel(G) == LB_FV_MARCH ? resolved_chunk(G) : 0;
+    return LB_OK;
+}
+
+lb_status lb_autotune_fv(lb_grid* G, int steps) {
+    lb_status s = check_ready(G);
+    if (s != LB_OK) return s;
+    if (steps < 1) return fail(LB_ERR_ARG, "steps must be >= 1");
+    DeviceGuard dg(G->device);
+    const size_t bytes = (size_t)Q * G->plane * elem_size(G->d.store);
+    void *sf = nullptr, *sg = nullptr;
+    CK(cudaMalloc(&sf, bytes));
+    if (G->d.thermal && cudaMalloc(&sg, bytes) != cudaSuccess) {
+        cudaFree(sf);
+        return fail(LB_ERR_OOM, "autotune: no memory for the state copy");
+    }
+    const int cur0 = G->cur;
+    cudaMemcpyAsync(sf, G->f[cur0], bytes, cudaMemcpyDeviceToDevice, G->stream);
+    if (sg) cudaMemcpyAsync(sg, G->g[cur0], bytes, cudaMemcpyDeviceToDevice, G->stream);
+    const int k0 = G->fv_kernel, c0 = G->fv_chunk;
+    G->fv_kernel = LB_FV_MARCH;
+    G->fv_chunk = 0;
+    const int base = resolved_chunk(G);
+    std::vector<std::pair<int, int>> cands = {{LB_FV_TILE, 0}};
+    for (int ch : {base / 2, base, base * 2, 32, 64, 128})
+        if (ch >= 16 && ch <= 4 * G->ny) cands.push_back({LB_FV_MARCH, ch});
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    std::pair<int, int> pick = {LB_FV_TILE, 0};
+    lb_status st = LB_OK;
+    for (auto& c : cands) {
+        G->fv_kernel = c.first;
+        G->fv_chunk = c.second;
+        G->cur = cur0;
+        // warm-up step, then the timed ones
+        cudaError_t e = G->prec == Prec::F64 ? launch_fv_step<double>(G) : launch_fv_step<float>(G);
+        G->cur ^= 1;
+        cudaEventRecord(e0, G->stream);
+        for (int k = 0; k < steps && e == cudaSuccess; ++k) {
+            e = G->prec == Prec::F64 ? launch_fv_step<double>(G) : launch_fv_step<float>(G);
+            G->cur ^= 1;
+        }
+        cudaEventRecord(e1, G->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            st = fail(LB_ERR_CUDA, "autotune: %s", cudaGetErrorString(e));
+            break;
+        }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            pick = c;
+        }
+    }
+    // restore the state into the buffer it started in
+    G->cur = cur0;
+    cudaMemcpyAsync(G->f[cur0], sf, bytes, cudaMemcpyDeviceToDevice, G->stream);
+    if (sg) cudaMemcpyAsync(G->g[cur0], sg, bytes, cudaMemcpyDeviceToDevice, G->stream);
+    cudaStreamSynchronize(G->stream);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sf);
+    if (sg) cudaFree(sg);
+    if (st != LB_OK) {
+        G->fv_kernel = k0;
+        G->fv_chunk = c0;
+        return st;
+    }
+    G->fv_kernel = pick.first;
+    G->fv_chunk = pick.second;
     return LB_OK;
 }
 

@@ -50,9 +50,14 @@ template <> struct Store<float> {
     __device__ static float ld(const float* p) { return __ldg(p); }
     __device__ static void st(float* p, float v) { *p = v; }
 };
+// FP16 holds the deviation times 2^12: the deviations are O(1e-1) at most,
+// so the scale keeps the small ones (buoyancy and wall increments of 1e-8)
+// out of FP16's subnormal range, where the spacing is 6e-8.  The largest
+// storable deviation is 65504 / 4096 = 16.  Powers of two scale exactly.
+constexpr float kF16Scale = 4096.0f;
 template <> struct Store<__half> {
-    __device__ static float ld(const __half* p) { return __half2float(__ldg(p)); }
-    __device__ static void st(__half* p, float v) { *p = __float2half_rn(v); }
+    __device__ static float ld(const __half* p) { return __half2float(__ldg(p)) * (1.0f / kF16Scale); }
+    __device__ static void st(__half* p, float v) { *p = __float2half_rn(v * kF16Scale); }
 };
 template <> struct Store<__nv_bfloat16> {
     __device__ static float ld(const __nv_bfloat16* p) { return __bfloat162float(__ldg(p)); }
@@ -156,6 +161,10 @@ enum class Prec { F64, F32, F16, BF16 };
 
 cudaError_t launch_st(Prec p, bool thermal, const void* args, cudaStream_t s);
 cudaError_t launch_fv(Prec p, bool thermal, const void* args, cudaStream_t s);
+// y-marching FV kernel: strips of march_width() output columns, `chunk` rows per CTA
+cudaError_t launch_fv_march(Prec p, bool thermal, const void* args, int chunk, cudaStream_t s);
+int march_width(Prec p, bool thermal);
+size_t march_smem(Prec p, bool thermal);
 
 struct AuxArgs {
     const void* f;  // state buffers (deviation storage)

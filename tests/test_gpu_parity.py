@@ -122,14 +122,19 @@ FV_CASES = [
 ]
 
 
+SCHEDULES = [(1, 0), (2, 8), (2, 16), (2, 0)]  # tile; march with 8, 16 and auto rows per CTA
+
+
+@pytest.mark.parametrize("sched", SCHEDULES, ids=lambda s: f"k{s[0]}c{s[1]}")
 @pytest.mark.parametrize("case", FV_CASES, ids=lambda c: "-".join(f"{k}{v}" for k, v in c.items()))
-def test_fv_step_f64(lbgpu, oracle, case):
+def test_fv_step_f64(lbgpu, oracle, case, sched):
     nx, ny = case["nx"], case["ny"]
     th = case.get("thermal", False)
     kw = dict(tau=0.3, dt=0.05, ax=2e-4, ay=-1e-4)
     if th:
         kw.update(tau_g=0.25, beta=1e-2, grav=1.0, T0=1.0, T_bot=1.3, T_top=0.8)
     g, r = pair(lbgpu, oracle, store=lbgpu.LB_STORE_F64, **case, **kw)
+    g.set_fv_schedule(*sched)
     f = inputs.random_populations(nx, ny, seed=3 * nx + ny, amp=0.2)
     gg = inputs.random_populations(nx, ny, seed=11, amp=0.2) if th else None
     g.set_pops(f, gg)
@@ -144,11 +149,14 @@ def test_fv_step_f64(lbgpu, oracle, case):
 
 
 @pytest.mark.parametrize("store", ["f32"])
-@pytest.mark.parametrize("scheme", ["st", "fv"])
+@pytest.mark.parametrize("scheme", ["st", "fv", "fv-march"])
 def test_f32_paths(lbgpu, oracle, scheme, store):
     """FP32 arithmetic on deviations: relative L2 velocity error <= 1e-5."""
     dt = 1.0 if scheme == "st" else 0.5
     g, r = pair(lbgpu, oracle, 64, 48, store, ly=48.0, tau=0.3, dt=dt, ax=1e-6, kind=0, u0=0.02)
+    if scheme == "fv-march":
+        g.set_fv_schedule(lbgpu.LB_FV_MARCH, 16)
+        scheme = "fv"
     for x in (g, r):
         (x.step_st if scheme == "st" else x.step_fv)(200)
     assert rel_l2_u(g, r) < 1e-5
@@ -257,6 +265,27 @@ def test_config_st8192_sampled(lbgpu, oracle, store, tol):
         assert np.abs(f1[:, inner, inner] - fr[:, inner, inner]).max() <= tol * scale
 
 
+def test_autotune_keeps_state_and_results(lbgpu, oracle):
+    """The autotuner times every schedule on the live state and restores it:
+    the populations are unchanged and the next steps still match the oracle."""
+    nx, ny = 300, 130
+    g, r = pair(lbgpu, oracle, nx, ny, lbgpu.LB_STORE_F64, sy=1, stretch_y=2.0, bcy=1, thermal=True,
+                tau=0.1, tau_g=0.1, dt=0.05, beta=1e-3, grav=1.0, T0=1.0, T_bot=1.5, T_top=0.5,
+                kind=3, amp=1e-2, seed=5)
+    g.step_fv(2)
+    r.step_fv(2)
+    before = g.get_pops()
+    kernel, chunk = g.autotune_fv(3)
+    assert kernel in (lbgpu.LB_FV_TILE, lbgpu.LB_FV_MARCH)
+    after = g.get_pops()
+    assert np.array_equal(before[0], after[0]) and np.array_equal(before[1], after[1])
+    g.step_fv(3)
+    r.step_fv(3)
+    fg, gg = g.get_pops()
+    fr, gr = r.get_pops()
+    assert np.abs(fg - fr).max() < 1e-13 and np.abs(gg - gr).max() < 1e-13
+
+
 def test_config_rb1024_strip(lbgpu, oracle):
     """1024^2 RB at Ra = 1e8 with FP16 deviation storage: a full-height strip
     advanced 2 FV steps by the oracle from the GPU's state matches the GPU."""
@@ -302,6 +331,21 @@ def test_rb_nusselt_f16_vs_oracle(lbgpu, oracle):
     r.step_fv(w.steps)
     for a, b in zip(g.nusselt(), r.nusselt()):
         assert abs(a / b - 1) < 1e-3
+
+
+@pytest.mark.parametrize("store,tol", [("f32", 1e-6), ("bf16dev", 1e-2)])
+def test_rb_nusselt_storage_errors(lbgpu, oracle, store, tol):
+    """The same RB cell with FP32 and BF16 deviation storage (BF16's 8-bit
+    mantissa gives a looser bound)."""
+    from paper_1505_03271_gb300 import configs as cfg
+    w = cfg.rayleigh_benard(128, 1e6, store=lbgpu.STORE_NAMES[store], steps=500)
+    grid = dict(w.grid)
+    st = grid.pop("store")
+    g, r = pair(lbgpu, oracle, store=st, **grid, **w.params, **w.init)
+    g.step_fv(w.steps)
+    r.step_fv(w.steps)
+    for a, b in zip(g.nusselt(), r.nusselt()):
+        assert abs(a / b - 1) < tol
 
 
 # ------------------------------------------------------- errors and edges --
