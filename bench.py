@@ -101,15 +101,24 @@ class ClockSampler:
 
 # --------------------------------------------------------------------- GPU --
 
+FV_SCHEDULE = "tune"
+
+
 def make_grid(lb, w, stream, tune=True):
     """Grid of a workload; FV grids run the library's autotuner (it restores
-    the state it times on), so the timed steps use the schedule it picked."""
+    the state it times on), so the timed steps use the schedule it picked,
+    unless --fv-schedule fixes one."""
     grid = dict(w.grid)
     store = grid.pop("store")
     g = lb.Grid(store=store, stream=stream, **grid)
     g.init(**w.params, **w.init)
-    if tune and w.scheme == "fv":
-        g.autotune_fv(5)
+    if w.scheme == "fv":
+        if FV_SCHEDULE == "tile":
+            g.set_fv_schedule(lb.LB_FV_TILE)
+        elif FV_SCHEDULE.startswith("march"):
+            g.set_fv_schedule(lb.LB_FV_MARCH, int(FV_SCHEDULE.split(":")[1]) if ":" in FV_SCHEDULE else 0)
+        elif tune:
+            g.autotune_fv(5)
     return g
 
 
@@ -306,8 +315,12 @@ def main():
     ap.add_argument("--case", default="channel",
                     help="workload to time: channel (headline), st8192, st4096, st4096_f16dev, "
                          "fv4096, fv2048, rb1024")
+    ap.add_argument("--fv-schedule", default="tune",
+                    help="tune (autotuner), tile, march or march:<rows per CTA>")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    global FV_SCHEDULE
+    FV_SCHEDULE = args.fv_schedule
     if args.impl == "reference":
         return run_reference(args)
 

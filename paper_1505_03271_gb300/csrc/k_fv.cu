@@ -57,18 +57,22 @@ __device__ __forceinline__ R advect(const R* P, int stride, int ix, int iy, int 
     return v;
 }
 
+// Flux divergences of all populations: the deviations' part plus the base
+// state's own y flux (a per-row constant).
 template <typename R, bool TH, int a>
 __device__ __forceinline__ void unroll_advect(const R* P, int plane, int stride, int ix, int iy,
                                               int gx, int gy, const StepArgs<R>& A, R* out) {
-    out[a] = advect<R, a>(P + a * plane, stride, ix, iy, gx, gy, A);
-    if constexpr (TH) out[Q + a] = advect<R, a>(P + (Q + a) * plane, stride, ix, iy, gx, gy, A);
+    out[a] = advect<R, a>(P + a * plane, stride, ix, iy, gx, gy, A) + ref_flux<R, a>(A, gy, false);
+    if constexpr (TH)
+        out[Q + a] = advect<R, a>(P + (Q + a) * plane, stride, ix, iy, gx, gy, A) + ref_flux<R, a>(A, gy, true);
     if constexpr (a + 1 < Q) unroll_advect<R, TH, a + 1>(P, plane, stride, ix, iy, gx, gy, A, out);
 }
 
 // Ghost cells of one shared-memory region W x H whose corner is the grid
-// position (gx0, gy0): double reflection h_a(x_-k) = h_inv(a)(x_k) for f and
-// anti-reflection hg_a(x_-k) = 2 w_a (T_wall - T0) - hg_inv(a)(x_k) for the
-// thermal deviations (walls on y only for thermal grids).
+// position (gx0, gy0).  Double reflection h_a(x_-k) = h_inv(a)(x_k) for f;
+// for g the anti-reflection hg_a(x_-k) = 2 w_a T_wall - hg_inv(a)(x_k), which
+// on base-state deviations (T_r odd about T_wall) reads h'_a = -h'_inv(a).
+// Thermal grids have their plates on y only.
 template <typename R, bool TH>
 __device__ void ghost_fill(R* P, int plane, int W, int H, int gx0, int gy0, const StepArgs<R>& A) {
     if (A.bcy == LB_BC_WALLS) {
@@ -86,9 +90,7 @@ __device__ void ghost_fill(R* P, int plane, int W, int H, int gx0, int gy0, cons
 #pragma unroll
             for (int a = 0; a < Q; ++a) {
                 P[a * plane + dst] = P[inv(a) * plane + src];
-                if (TH)
-                    P[(Q + a) * plane + dst] =
-                        R(2) * wgt<R>(a) * (bot ? A.dTb : A.dTt) - P[(Q + inv(a)) * plane + src];
+                if (TH) P[(Q + a) * plane + dst] = -P[(Q + inv(a)) * plane + src];
             }
         }
     }
@@ -132,13 +134,13 @@ __global__ void __launch_bounds__(kFvThreads) k_fv(const StepArgs<R> A) {
         const long long c = (long long)gy * A.pitch + gx;
         R d[Q], e[Q];
 #pragma unroll
-        for (int a = 0; a < Q; ++a) d[a] = Store<S>::ld(fin + a * A.plane + c) + wgt<R>(a) * A.roff[gy];
+        for (int a = 0; a < Q; ++a) d[a] = Store<S>::ld(fin + a * A.plane + c);
         if constexpr (TH) {
 #pragma unroll
-            for (int a = 0; a < Q; ++a) e[a] = Store<S>::ld(gin + a * A.plane + c) + wgt<R>(a) * A.toff[gy];
+            for (int a = 0; a < Q; ++a) e[a] = Store<S>::ld(gin + a * A.plane + c);
         }
         Cell<R, TH> m;
-        m.moments(d, e, A);
+        m.moments(d, e, A, A.roff[gy], A.toff[gy]);
         const bool inB = ex >= 2 && ex < EX - 2 && ey >= 2 && ey < EY - 2;
         const int kb = (ey - 2) * BX + (ex - 2);
 #pragma unroll
@@ -181,7 +183,7 @@ __global__ void __launch_bounds__(kFvThreads) k_fv(const StepArgs<R> A) {
             }
         }
         Cell<R, TH> m;
-        m.moments(fs, es, A);
+        m.moments(fs, es, A, A.roff[gy], A.toff[gy]);
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
             R feqd, F, geqd = 0;
@@ -207,10 +209,8 @@ __global__ void __launch_bounds__(kFvThreads) k_fv(const StepArgs<R> A) {
         const long long c = (long long)gy * A.pitch + gx;
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
-            Store<S>::st(fout + a * A.plane + c, sFC[a * NB + kb] - A.hf * adv[a] - wgt<R>(a) * A.roff[gy]);
-            if constexpr (TH)
-                Store<S>::st(gout + a * A.plane + c,
-                             sFC[(Q + a) * NB + kb] - A.hf * adv[Q + a] - wgt<R>(a) * A.toff[gy]);
+            Store<S>::st(fout + a * A.plane + c, sFC[a * NB + kb] - A.hf * adv[a]);
+            if constexpr (TH) Store<S>::st(gout + a * A.plane + c, sFC[(Q + a) * NB + kb] - A.hf * adv[Q + a]);
         }
     }
 }

@@ -92,24 +92,24 @@ __device__ __forceinline__ R advect_col(const R* ring, const int* sl, int p, int
     return v;
 }
 
+// All populations: the deviations' flux divergence plus the base state's
+// own y flux (a per-row constant).
 template <typename R, bool TH, int NQ, int NT, int a>
 __device__ __forceinline__ void advect_all(const R* ring, const int* sl, int k, const XMetric<R>& X,
-                                           const YMetric<R>& Y, R* out) {
-    out[a] = advect_col<R, NQ, NT, a>(ring, sl, a, k, X, Y);
-    if constexpr (TH) out[Q + a] = advect_col<R, NQ, NT, a>(ring, sl, Q + a, k, X, Y);
-    if constexpr (a + 1 < Q) advect_all<R, TH, NQ, NT, a + 1>(ring, sl, k, X, Y, out);
+                                           const YMetric<R>& Y, const StepArgs<R>& A, int gy, R* out) {
+    out[a] = advect_col<R, NQ, NT, a>(ring, sl, a, k, X, Y) + ref_flux<R, a>(A, gy, false);
+    if constexpr (TH) out[Q + a] = advect_col<R, NQ, NT, a>(ring, sl, Q + a, k, X, Y) + ref_flux<R, a>(A, gy, true);
+    if constexpr (a + 1 < Q) advect_all<R, TH, NQ, NT, a + 1>(ring, sl, k, X, Y, A, gy, out);
 }
 
-// Ghost row of a wall on y, own column: double reflection for f,
-// anti-reflection through T_wall for g.
+// Ghost row of a wall on y, own column, on base-state deviations: double
+// reflection h'_a = h'_inv(a) for f, anti-reflection h'_a = -h'_inv(a) for g.
 template <typename R, bool TH, int NQ, int NT>
-__device__ __forceinline__ void ghost_row(R* ring, int dst_slot, int src_slot, int k, R dTw) {
+__device__ __forceinline__ void ghost_row(R* ring, int dst_slot, int src_slot, int k) {
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
         ring[(dst_slot * NQ + a) * NT + k] = ring[(src_slot * NQ + inv(a)) * NT + k];
-        if constexpr (TH)
-            ring[(dst_slot * NQ + Q + a) * NT + k] =
-                R(2) * wgt<R>(a) * dTw - ring[(src_slot * NQ + Q + inv(a)) * NT + k];
+        if constexpr (TH) ring[(dst_slot * NQ + Q + a) * NT + k] = -ring[(src_slot * NQ + Q + inv(a)) * NT + k];
     }
 }
 
@@ -154,13 +154,11 @@ __global__ void __launch_bounds__(NT) k_fv_march(const StepArgs<R> A, const int 
         int gy;
         if (colA && r < ye + 4 && fluid_row(r, gy)) {
             const long long c = (long long)gy * A.pitch + gx;
-            const R ro = A.roff[gy];
 #pragma unroll
-            for (int a = 0; a < Q; ++a) nd[a] = Store<S>::ld(fin + a * A.plane + c) + wgt<R>(a) * ro;
+            for (int a = 0; a < Q; ++a) nd[a] = Store<S>::ld(fin + a * A.plane + c);
             if constexpr (TH) {
-                const R to = A.toff[gy];
 #pragma unroll
-                for (int a = 0; a < Q; ++a) ne[a] = Store<S>::ld(gin + a * A.plane + c) + wgt<R>(a) * to;
+                for (int a = 0; a < Q; ++a) ne[a] = Store<S>::ld(gin + a * A.plane + c);
             }
         }
     };
@@ -196,7 +194,7 @@ __global__ void __launch_bounds__(NT) k_fv_march(const StepArgs<R> A, const int 
                     }
                     prefetch(t + 1);
                     Cell<R, TH> m;
-                    m.moments(d, e, A);
+                    m.moments(d, e, A, A.roff[gy], A.toff[gy]);
 #pragma unroll
                     for (int a = 0; a < Q; ++a) {
                         R feqd, F, geqd = 0;
@@ -215,11 +213,11 @@ __global__ void __launch_bounds__(NT) k_fv_march(const StepArgs<R> A, const int 
                 prefetch(t + 1);
                 // top wall ghosts at their own iteration; bottom ones below
                 if (wally && colA && (t == A.ny || t == A.ny + 1))
-                    ghost_row<R, TH, NQ, NT>(sH, s, slot5(2 * A.ny - 1 - t), k, A.dTt);
+                    ghost_row<R, TH, NQ, NT>(sH, s, slot5(2 * A.ny - 1 - t), k);
             }
             if (wally && colA && t == 1 && ys == 0) {
-                ghost_row<R, TH, NQ, NT>(sH, slot5(-1), slot5(0), k, A.dTb);
-                ghost_row<R, TH, NQ, NT>(sH, slot5(-2), slot5(1), k, A.dTb);
+                ghost_row<R, TH, NQ, NT>(sH, slot5(-1), slot5(0), k);
+                ghost_row<R, TH, NQ, NT>(sH, slot5(-2), slot5(1), k);
             }
         }
         // ---- stage B on row t - 2 ----
@@ -234,7 +232,7 @@ __global__ void __launch_bounds__(NT) k_fv_march(const StepArgs<R> A, const int 
                         load_y(A.my, gy, Y);
                         const int sl[5] = {slot5(r - 2), slot5(r - 1), s, slot5(r + 1), slot5(r + 2)};
                         R adv[NQ];
-                        advect_all<R, TH, NQ, NT, 0>(sH, sl, k, X, Y, adv);
+                        advect_all<R, TH, NQ, NT, 0>(sH, sl, k, X, Y, A, gy, adv);
                         R fs[Q], es[Q];
 #pragma unroll
                         for (int a = 0; a < Q; ++a) {
@@ -248,7 +246,7 @@ __global__ void __launch_bounds__(NT) k_fv_march(const StepArgs<R> A, const int 
                             }
                         }
                         Cell<R, TH> m;
-                        m.moments(fs, es, A);
+                        m.moments(fs, es, A, A.roff[gy], A.toff[gy]);
 #pragma unroll
                         for (int a = 0; a < Q; ++a) {
                             R feqd, F, geqd = 0;
@@ -258,11 +256,11 @@ __global__ void __launch_bounds__(NT) k_fv_march(const StepArgs<R> A, const int 
                         }
                     }
                 } else if (wally && colA && (r == A.ny || r == A.ny + 1)) {
-                    ghost_row<R, TH, NQ, NT>(sS, s, slot5(2 * A.ny - 1 - r), k, A.dTt);
+                    ghost_row<R, TH, NQ, NT>(sS, s, slot5(2 * A.ny - 1 - r), k);
                 }
                 if (wally && colA && r == 1 && ys == 0) {
-                    ghost_row<R, TH, NQ, NT>(sS, slot5(-1), slot5(0), k, A.dTb);
-                    ghost_row<R, TH, NQ, NT>(sS, slot5(-2), slot5(1), k, A.dTb);
+                    ghost_row<R, TH, NQ, NT>(sS, slot5(-1), slot5(0), k);
+                    ghost_row<R, TH, NQ, NT>(sS, slot5(-2), slot5(1), k);
                 }
             }
         }
@@ -275,18 +273,15 @@ __global__ void __launch_bounds__(NT) k_fv_march(const StepArgs<R> A, const int 
                 load_y(A.my, r, Y);
                 const int sl[5] = {slot5(r - 2), slot5(r - 1), s, slot5(r + 1), slot5(r + 2)};
                 R adv[NQ];
-                advect_all<R, TH, NQ, NT, 0>(sS, sl, k, X, Y, adv);
+                advect_all<R, TH, NQ, NT, 0>(sS, sl, k, X, Y, A, r, adv);
                 const long long c = (long long)r * A.pitch + gx;
-                const R ro = A.roff[r];
 #pragma unroll
                 for (int a = 0; a < Q; ++a)
-                    Store<S>::st(fout + a * A.plane + c, sP[(s * NQ + a) * NT + k] - A.hf * adv[a] - wgt<R>(a) * ro);
+                    Store<S>::st(fout + a * A.plane + c, sP[(s * NQ + a) * NT + k] - A.hf * adv[a]);
                 if constexpr (TH) {
-                    const R to = A.toff[r];
 #pragma unroll
                     for (int a = 0; a < Q; ++a)
-                        Store<S>::st(gout + a * A.plane + c,
-                                     sP[(s * NQ + Q + a) * NT + k] - A.hf * adv[Q + a] - wgt<R>(a) * to);
+                        Store<S>::st(gout + a * A.plane + c, sP[(s * NQ + Q + a) * NT + k] - A.hf * adv[Q + a]);
                 }
             }
         }

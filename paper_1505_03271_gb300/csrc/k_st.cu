@@ -3,7 +3,8 @@
 // (coalesced along x in the [q][y][x] layout), relaxes them with the BGK
 // collision plus Guo forcing, and writes each post-collision value to the
 // neighbour it streams to.  Walls: half-way bounce-back for f and
-// anti-bounce-back through the plate temperature for g.
+// anti-bounce-back through the plate temperature for g,
+// g_inv(a)(x) = -g*_a(x) + 2 w_a T_wall.
 #include "lb_internal.cuh"
 
 namespace lbgb {
@@ -21,13 +22,14 @@ __global__ void __launch_bounds__(256) k_st(const StepArgs<R> A) {
 
     R d[Q], e[Q];
 #pragma unroll
-    for (int a = 0; a < Q; ++a) d[a] = Store<S>::ld(fin + a * A.plane + c) + wgt<R>(a) * A.roff[y];
+    for (int a = 0; a < Q; ++a) d[a] = Store<S>::ld(fin + a * A.plane + c);
     if (TH) {
 #pragma unroll
-        for (int a = 0; a < Q; ++a) e[a] = Store<S>::ld(gin + a * A.plane + c) + wgt<R>(a) * A.toff[y];
+        for (int a = 0; a < Q; ++a) e[a] = Store<S>::ld(gin + a * A.plane + c);
     }
+    const R ro = A.roff[y], to = TH ? A.toff[y] : R(0);
     Cell<R, TH> m;
-    m.moments(d, e, A);
+    m.moments(d, e, A, ro, to);
 
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
@@ -52,14 +54,16 @@ __global__ void __launch_bounds__(256) k_st(const StepArgs<R> A) {
                 dTw = ty < 0 ? A.dTb : A.dTt;
             }
         }
+        // post and gpost are deviations from the base state of row y; a
+        // population streamed to row ty is stored against ty's base state
         if (out) {
             const long long o = inv(a) * A.plane + c;
-            Store<S>::st(fout + o, post - wgt<R>(a) * A.roff[y]);
-            if (TH) Store<S>::st(gout + o, -gpost + wgt<R>(a) * (R(2) * dTw - A.toff[y]));
+            Store<S>::st(fout + o, post);
+            if (TH) Store<S>::st(gout + o, -gpost + R(2) * wgt<R>(a) * (dTw - to));
         } else {
             const long long o = a * A.plane + (long long)ty * A.pitch + tx;
-            Store<S>::st(fout + o, post - wgt<R>(a) * A.roff[ty]);
-            if (TH) Store<S>::st(gout + o, gpost - wgt<R>(a) * A.toff[ty]);
+            Store<S>::st(fout + o, post + wgt<R>(a) * (ro - A.roff[ty]));
+            if (TH) Store<S>::st(gout + o, gpost + wgt<R>(a) * (to - A.toff[ty]));
         }
     }
 }

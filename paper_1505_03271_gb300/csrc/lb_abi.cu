@@ -153,6 +153,7 @@ struct lb_grid {
     void* toff_r = nullptr;     // the same in compute precision
     double* roff = nullptr;     // per-row storage offset of f, FP64 (ny)
     void* roff_r = nullptr;
+    void* dref_r = nullptr;     // [4][ny] y flux divergence of the base state, compute precision
     double* fields = nullptr;   // [4][ny][nx] staging for init/moments
     double* partial = nullptr;  // reduction partials
     double* red = nullptr;      // reduction totals
@@ -166,7 +167,7 @@ namespace {
 
 void release(lb_grid* G) {
     void* ptrs[] = {G->f[0], G->f[1], G->g[0], G->g[1], G->mx, G->my, G->dxv, G->dyv, G->xc,
-                    G->yc, G->toff, G->toff_r, G->roff, G->roff_r, G->fields, G->partial, G->red};
+                    G->yc, G->toff, G->toff_r, G->roff, G->roff_r, G->dref_r, G->fields, G->partial, G->red};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -214,6 +215,7 @@ StepArgs<R> step_args(const lb_grid* G, double dt) {
     A.T0 = (R)p.T0;
     A.toff = static_cast<const R*>(G->toff_r);
     A.roff = static_cast<const R*>(G->roff_r);
+    A.dref = static_cast<const R*>(G->dref_r);
     return A;
 }
 
@@ -371,6 +373,7 @@ lb_status lb_create_grid(const lb_grid_desc* d, lb_grid** out) {
     alloc(&G->toff_r, (as_float ? sizeof(float) : sizeof(double)) * G->ny);
     alloc((void**)&G->roff, sizeof(double) * G->ny);
     alloc(&G->roff_r, (as_float ? sizeof(float) : sizeof(double)) * G->ny);
+    alloc(&G->dref_r, (as_float ? sizeof(float) : sizeof(double)) * 4 * G->ny);
     alloc((void**)&G->partial, sizeof(double) * kRed * G->nred);
     alloc((void**)&G->red, sizeof(double) * kRed);
     if (st == LB_OK) st = upload(&G->mx, G->ax.metric(), as_float);
@@ -428,15 +431,47 @@ lb_status lb_init(lb_grid* G, const lb_params* p, const lb_init_desc* in) {
             if (plates) to[j] = dTp * (0.5 - G->ay.c[j] / Hy) + 0.5 * (p->T_bot + p->T_top) - p->T0;
             if (in->kind == LB_INIT_RB) ro[j] = rho_norm * baro(G->ay.c[j]) - 1.0;
         }
+        // y flux divergence of the base state per row and upwind sign, with
+        // the same QUICK weights as the kernels; ghost rows extend rho_r
+        // evenly and T_r oddly about the plate temperature.
+        const int ny = G->ny;
+        const bool wall = G->d.bcy == LB_BC_WALLS;
+        auto ext = [&](const std::vector<double>& v, int i, double wall_lo, double wall_hi, bool odd) {
+            if (i >= 0 && i < ny) return v[i];
+            if (!wall) return v[((i % ny) + ny) % ny];
+            if (i < 0) return odd ? 2.0 * wall_lo - v[-i - 1] : v[-i - 1];
+            return odd ? 2.0 * wall_hi - v[2 * ny - 1 - i] : v[2 * ny - 1 - i];
+        };
+        std::vector<double> dref(4 * (size_t)ny, 0.0);
+        for (int q = 0; q < 2; ++q) {
+            const std::vector<double>& v = q ? to : ro;
+            const double lo = q ? p->T_bot - p->T0 : 0.0, hi = q ? p->T_top - p->T0 : 0.0;
+            bool any = false;
+            for (double x : v) any = any || x != 0.0;
+            if (!any) continue;
+            for (int sgn = 0; sgn < 2; ++sgn) {
+                auto face = [&](int kf) {
+                    const int k0 = sgn == 0 ? kf - 2 : kf - 1;
+                    double w[3];
+                    G->ay.quick(k0, kf, w);
+                    double phi = 0.0;
+                    for (int m = 0; m < 3; ++m) phi += w[m] * ext(v, k0 + m, lo, hi, q == 1);
+                    return phi;
+                };
+                for (int j = 0; j < ny; ++j) dref[(2 * q + sgn) * ny + j] = (face(j + 1) - face(j)) / G->ay.d[j];
+            }
+        }
         CK(cudaMemcpy(G->toff, to.data(), sizeof(double) * G->ny, cudaMemcpyHostToDevice));
         CK(cudaMemcpy(G->roff, ro.data(), sizeof(double) * G->ny, cudaMemcpyHostToDevice));
         if (G->prec == Prec::F64) {
             CK(cudaMemcpy(G->toff_r, to.data(), sizeof(double) * G->ny, cudaMemcpyHostToDevice));
             CK(cudaMemcpy(G->roff_r, ro.data(), sizeof(double) * G->ny, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(G->dref_r, dref.data(), sizeof(double) * dref.size(), cudaMemcpyHostToDevice));
         } else {
-            std::vector<float> tf(to.begin(), to.end()), rf(ro.begin(), ro.end());
+            std::vector<float> tf(to.begin(), to.end()), rf(ro.begin(), ro.end()), df(dref.begin(), dref.end());
             CK(cudaMemcpy(G->toff_r, tf.data(), sizeof(float) * G->ny, cudaMemcpyHostToDevice));
             CK(cudaMemcpy(G->roff_r, rf.data(), sizeof(float) * G->ny, cudaMemcpyHostToDevice));
+            CK(cudaMemcpy(G->dref_r, df.data(), sizeof(float) * df.size(), cudaMemcpyHostToDevice));
         }
     }
     InitArgs a{};

@@ -32,15 +32,18 @@ __host__ __device__ constexpr R wgt(int a) {
 static_assert(inv(1) == 3 && inv(3) == 1 && inv(2) == 4 && inv(4) == 2, "inv");
 static_assert(inv(5) == 7 && inv(7) == 5 && inv(6) == 8 && inv(8) == 6 && inv(0) == 0, "inv");
 
-// ---- storage types ----
-// The state holds f - w rho_ref(y) and g - w T_ref(y), deviations from a
-// per-row reference state: the hydrostatic, conductive base state of a grid
-// with plates (barometric rho_ref, linear T_ref), else rho_ref = 1, T_ref =
-// T0.  Kernels add w roff[y] (roff = rho_ref - 1) and w toff[y]
-// (toff = T_ref - T0) on load and work with f - w and g - w T0 in
-// registers.  With 16-bit storage the stored values are then small, so the
-// slow departures from the base state (buoyancy, wall gradients) keep their
-// precision instead of vanishing below half an ulp.
+// ---- storage and arithmetic frame ----
+// The state holds f - w rho_r(y) and g - w T_r(y): deviations from a per-row
+// base state, which on a grid with plates is the hydrostatic, conductive RB
+// state (barometric rho_r, linear T_r) and elsewhere rho_r = 1, T_r = T0.
+// Kernels compute in the same frame: moments add the row's rho_r and T_r,
+// and the y flux divergence of the base state itself enters as a per-row
+// constant (QUICK is linear, so A[h' + w ref] = A[h'] + w A[ref]).  Near the
+// plates every quantity the kernels round is then small, so the wall
+// temperature gradient (the Nusselt number) keeps its digits in FP32
+// arithmetic and in 16-bit storage.  Ghost rows extend the base state by the
+// wall's own symmetry (rho_r even, T_r odd about T_wall), which turns the
+// wall rules into h'_a(x_-k) = h'_inv(a)(x_k) for f and -h'_inv(a)(x_k) for g.
 template <typename S> struct Store;
 template <> struct Store<double> {
     __device__ static double ld(const double* p) { return __ldg(p); }
@@ -93,8 +96,9 @@ struct StepArgs {
     R ax, ay, bg;           // external acceleration, beta * grav
     R dTb, dTt;             // T_bot - T0, T_top - T0
     R T0;                   // reference temperature
-    const R* toff;          // per-row storage offset of g (thermal grids)
-    const R* roff;          // per-row storage offset of f
+    const R* toff;          // per row: T_r - T0 (thermal grids)
+    const R* roff;          // per row: rho_r - 1
+    const R* dref;          // [4][ny]: y flux divergence of rho_r (c_y > 0, < 0), of T_r (> 0, < 0)
 };
 
 // Wrap or reject a global index on one axis: periodic axes wrap, wall axes
@@ -112,13 +116,14 @@ __device__ __forceinline__ bool map_axis(int g, int n, int bc, int& out) {
     return false;
 }
 
-// Macroscopic moments of one cell from deviation populations d (and e):
-// rho = 1 + sum d, u = sum c d / rho + dt/2 a, T - T0 = sum e,
-// a = (ax, ay + beta grav (T - T0)).
+// Macroscopic moments of one cell from base-state deviations d (and e) of a
+// row with references rho_r = 1 + ro, T_r = T0 + to:
+// rho = rho_r + sum d, T = T_r + sum e, a = (ax, ay + beta grav (T - T0)),
+// u = sum c d / rho + dt/2 a (Sec. II B 4).
 template <typename R, bool TH>
 struct Cell {
-    R rp, rho, ux, uy, Td, ay;  // rp = rho - 1, kept unrounded
-    __device__ __forceinline__ void moments(const R* d, const R* e, const StepArgs<R>& A) {
+    R rp, rho, ux, uy, Td, T, ay;  // rp = rho - rho_r, Td = T - T_r: kept unrounded
+    __device__ __forceinline__ void moments(const R* d, const R* e, const StepArgs<R>& A, R ro, R to) {
         R r = 0, jx = 0, jy = 0;
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
@@ -132,15 +137,16 @@ struct Cell {
             for (int a = 0; a < Q; ++a) Td += e[a];
         }
         rp = r;
-        rho = R(1) + r;
-        ay = A.ay + (TH ? A.bg * Td : R(0));
+        rho = (R(1) + ro) + r;
+        const R dT0 = to + Td;  // T - T0
+        T = A.T0 + dT0;
+        ay = A.ay + (TH ? A.bg * dT0 : R(0));
         R ir = R(1) / rho;
         ux = jx * ir + A.hf * A.ax;
         uy = jy * ir + A.hf * ay;
     }
-    // f_eq - w, Guo force F (Eq. (F2)) and, if thermal, g_eq - w T0.
-    __device__ __forceinline__ void eq(int a, const StepArgs<R>& A, R& feqd, R& F,
-                                       R& geqd) const {
+    // f_eq - w rho_r, Guo force F (Eq. (F2)) and, if thermal, g_eq - w T_r.
+    __device__ __forceinline__ void eq(int a, const StepArgs<R>& A, R& feqd, R& F, R& geqd) const {
         const R w = wgt<R>(a);
         const R cu = R(cx(a)) * ux + R(cy(a)) * uy;
         const R uu = ux * ux + uy * uy;
@@ -149,9 +155,21 @@ struct Cell {
         const R ca = R(cx(a)) * A.ax + R(cy(a)) * ay;
         const R ua = ux * A.ax + uy * ay;
         F = w * rho * (R(3) * (ca - ua) + R(9) * cu * ca);
-        if (TH) geqd = w * (Td + (Td + A.T0) * poly);
+        if (TH) geqd = w * (Td + T * poly);
     }
 };
+
+// y flux divergence of the base state for population a at row gy (zero for
+// c_y = 0): c_y w_a (Phi_n - Phi_s)[ref] / dy.
+template <typename R, int a>
+__device__ __forceinline__ R ref_flux(const StepArgs<R>& A, int gy, bool thermal) {
+    if constexpr (cy(a) == 0) {
+        return R(0);
+    } else {
+        const int k = (thermal ? 2 : 0) + (cy(a) > 0 ? 0 : 1);
+        return R(cy(a)) * wgt<R>(a) * __ldg(A.dref + k * A.ny + gy);
+    }
+}
 
 }  // namespace lbgb
 
