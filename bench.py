@@ -115,8 +115,9 @@ def make_grid(lb, w, stream, tune=True):
     if w.scheme == "fv":
         if FV_SCHEDULE == "tile":
             g.set_fv_schedule(lb.LB_FV_TILE)
-        elif FV_SCHEDULE.startswith("march"):
-            g.set_fv_schedule(lb.LB_FV_MARCH, int(FV_SCHEDULE.split(":")[1]) if ":" in FV_SCHEDULE else 0)
+        elif FV_SCHEDULE.startswith("march") or FV_SCHEDULE.startswith("pair"):
+            kern = lb.LB_FV_MARCH if FV_SCHEDULE.startswith("march") else lb.LB_FV_PAIR
+            g.set_fv_schedule(kern, int(FV_SCHEDULE.split(":")[1]) if ":" in FV_SCHEDULE else 0)
         elif tune:
             g.autotune_fv(5)
     return g
@@ -126,7 +127,9 @@ def schedule_name(lb, g, scheme):
     if scheme != "fv":
         return "st push, one thread per cell"
     k, c = g.fv_schedule()
-    return "fv tile 32x16 (halo 4)" if k == lb.LB_FV_TILE else "fv march, %d rows per CTA" % c
+    if k == lb.LB_FV_TILE:
+        return "fv tile 32x16 (halo 4)"
+    return ("fv pair-march (f32x2)" if k == lb.LB_FV_PAIR else "fv march") + ", %d rows per CTA" % c
 
 
 def time_steps(lb, torch, g, scheme, steps, warmup, flush=None):
@@ -316,7 +319,7 @@ def main():
                     help="workload to time: channel (headline), st8192, st4096, st4096_f16dev, "
                          "fv4096, fv2048, rb1024")
     ap.add_argument("--fv-schedule", default="tune",
-                    help="tune (autotuner), tile, march or march:<rows per CTA>")
+                    help="tune (autotuner), tile, march[:rows per CTA] or pair[:rows per CTA]")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     global FV_SCHEDULE

@@ -131,21 +131,24 @@ lb_status lb_step_fv(lb_grid* grid, int nsteps);
  * the mesh to the lattice (Sec. II A).  One kernel launch per step. */
 lb_status lb_step_st(lb_grid* grid, int nsteps);
 
-/* Kernel schedule of lb_step_fv.  Both kernels compute the same step
+/* Kernel schedule of lb_step_fv.  All kernels compute the same step
  * (Eq. (semi-heun)); they differ only in how the grid is cut into CTAs:
  *   LB_FV_TILE:  32 x 16 tiles with a 4-cell halo in both axes, three
  *                shared-memory regions per tile;
  *   LB_FV_MARCH: strips of 120 columns (56 for FP64 thermal) that march up
- *                `chunk` rows each, halo only in x.
+ *                `chunk` rows each, halo only in x;
+ *   LB_FV_PAIR:  the marching strips with two columns per thread and packed
+ *                FP32 pair arithmetic; FP32/FP16/BF16 storage and x-periodic
+ *                grids only (LB_ERR_ARG otherwise).
  * LB_FV_AUTO picks by grid size.  chunk = 0 lets the library size the
  * chunks to fill the GPU.  LB_ERR_ARG on an unknown kernel or chunk < 0. */
-typedef enum { LB_FV_AUTO = 0, LB_FV_TILE = 1, LB_FV_MARCH = 2 } lb_fv_kernel;
+typedef enum { LB_FV_AUTO = 0, LB_FV_TILE = 1, LB_FV_MARCH = 2, LB_FV_PAIR = 3 } lb_fv_kernel;
 lb_status lb_set_fv_schedule(lb_grid* grid, int kernel, int chunk);
 /* The schedule lb_step_fv will use now (after AUTO has been resolved). */
 lb_status lb_get_fv_schedule(lb_grid* grid, int* kernel, int* chunk);
 
 /* Autotuner: times `steps` FV steps for each candidate schedule (tile; march
- * with several chunk lengths) on the grid's current state, restores the
+ * and pair with several chunk lengths) on the grid's current state, restores the
  * state after each candidate, and keeps the fastest.  Synchronous; uses a
  * temporary copy of the populations.  LB_ERR_STATE before lb_init. */
 lb_status lb_autotune_fv(lb_grid* grid, int steps);

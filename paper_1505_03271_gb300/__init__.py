@@ -62,7 +62,7 @@ SYMBOLS = ["lb_create_grid", "lb_init", "lb_step_fv", "lb_step_st", "lb_moments"
            "lb_get_window", "lb_sync", "lb_destroy", "lb_last_error", "lb_kernel_launches",
            "lb_conservation_noalloc", "lb_set_fv_schedule", "lb_get_fv_schedule",
            "lb_autotune_fv"]
-LB_FV_AUTO, LB_FV_TILE, LB_FV_MARCH = 0, 1, 2
+LB_FV_AUTO, LB_FV_TILE, LB_FV_MARCH, LB_FV_PAIR = 0, 1, 2, 3
 
 _lib = None
 

@@ -1,0 +1,428 @@
+// k_fv_pair.cu -- the FV time step (Sec. II B: Eqs. (semi), (semi-heun),
+// QUICK faces of Sec. II B 3, double-reflection walls of Sec. II B 5) as a
+// y-marching strip kernel in which every thread owns two adjacent columns
+// and all arithmetic runs on packed FP32 pairs (Blackwell's f32x2 FMA, ADD
+// and MUL: one instruction for both columns).
+//
+// March structure as in k_fv_march.cu: stage A forms h^n and f~ + Coll^n of
+// row t, stage B forms f~* and h* of row t - 2, stage C writes f~^(n+1) of
+// row t - 4; rows live in 5-slot shared-memory rings, one barrier per row.
+// Pairing adds:
+//   - populations are loaded and stored two columns at a time (8-byte FP32,
+//     4-byte half2 / bfloat162), so 16-bit storage also halves instructions;
+//   - equilibrium and Guo force are formed for each pair of opposite
+//     velocities together (they share c.u squared and the force terms);
+//   - the two columns share their middle x face, so an x flux needs three
+//     face values for two cells instead of four.
+// The kernel serves x-periodic grids (every workload here); grids with walls
+// on x use the scalar kernels.
+#include "lb_internal.cuh"
+
+namespace lbgb {
+
+namespace {
+
+struct V2 {
+    float2 v;
+};
+__device__ __forceinline__ V2 mk(float a, float b) { return {make_float2(a, b)}; }
+__device__ __forceinline__ V2 bc(float s) { return {make_float2(s, s)}; }
+__device__ __forceinline__ V2 operator+(V2 a, V2 b) { return {__fadd2_rn(a.v, b.v)}; }
+__device__ __forceinline__ V2 operator*(V2 a, V2 b) { return {__fmul2_rn(a.v, b.v)}; }
+__device__ __forceinline__ V2 fma2(V2 a, V2 b, V2 c) { return {__ffma2_rn(a.v, b.v, c.v)}; }
+__device__ __forceinline__ V2 operator-(V2 a, V2 b) { return fma2(b, bc(-1.0f), a); }
+
+// Pair loads/stores of the deviation storage (see Store<> for the scales).
+template <typename S> struct PairIO;
+template <> struct PairIO<float> {
+    __device__ static V2 ld(const float* p) { return {__ldg(reinterpret_cast<const float2*>(p))}; }
+    __device__ static void st(float* p, V2 v) { *reinterpret_cast<float2*>(p) = v.v; }
+};
+template <> struct PairIO<__half> {
+    __device__ static V2 ld(const __half* p) {
+        float2 f = __half22float2(__ldg(reinterpret_cast<const __half2*>(p)));
+        return {make_float2(f.x * (1.0f / kF16Scale), f.y * (1.0f / kF16Scale))};
+    }
+    __device__ static void st(__half* p, V2 v) {
+        *reinterpret_cast<__half2*>(p) = __floats2half2_rn(v.v.x * kF16Scale, v.v.y * kF16Scale);
+    }
+};
+template <> struct PairIO<__nv_bfloat16> {
+    __device__ static V2 ld(const __nv_bfloat16* p) {
+        return {__bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(p)))};
+    }
+    __device__ static void st(__nv_bfloat16* p, V2 v) {
+        *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(v.v.x, v.v.y);
+    }
+};
+
+// Collision data of a pair of cells on one row (base-state frame, see
+// lb_internal.cuh): moments, then per population the deviation of f_eq, the
+// Guo force and (thermal) the deviation of g_eq.
+template <bool TH>
+struct PairCell {
+    V2 rp, rho, ux, uy, Td, T, ay, uuneg, ua3neg;
+    V2 feqd[Q], F[Q], geqd[Q];
+
+    __device__ __forceinline__ void build(const V2* d, const V2* e, const StepArgs<float>& A, float ro, float to) {
+        V2 r = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+        V2 jx = (d[1] + d[5] + d[8]) - (d[3] + d[6] + d[7]);
+        V2 jy = (d[2] + d[5] + d[6]) - (d[4] + d[7] + d[8]);
+        rp = r;
+        rho = r + bc(1.0f + ro);
+        V2 ir = mk(__fdividef(1.0f, rho.v.x), __fdividef(1.0f, rho.v.y));
+        if (TH) {
+            Td = ((e[0] + e[1]) + (e[2] + e[3])) + ((e[4] + e[5]) + (e[6] + e[7])) + e[8];
+            const V2 dT0 = Td + bc(to);
+            T = dT0 + bc(A.T0);
+            ay = fma2(bc(A.bg), dT0, bc(A.ay));
+        } else {
+            ay = bc(A.ay);
+        }
+        ux = fma2(jx, ir, bc(A.hf * A.ax));
+        uy = fma2(ay, bc(A.hf), jy * ir);
+        uuneg = (ux * ux + uy * uy) * bc(-1.5f);
+        ua3neg = fma2(uy, ay, ux * bc(A.ax)) * bc(-3.0f);
+        // rest population: c = 0
+        const float w0 = wgt<float>(0);
+        const V2 wr0 = rho * bc(w0);
+        feqd[0] = fma2(wr0, uuneg, rp * bc(w0));
+        F[0] = wr0 * ua3neg;
+        if (TH) geqd[0] = fma2(T * bc(w0), uuneg, Td * bc(w0));
+        pair<1>(A);
+        pair<2>(A);
+        pair<5>(A);
+        pair<6>(A);
+    }
+
+    // populations a and inv(a): c.u and c.a flip sign, squares do not.
+    template <int a>
+    __device__ __forceinline__ void pair(const StepArgs<float>& A) {
+        constexpr int b = inv(a);
+        const float w = wgt<float>(a);
+        V2 cu, ca;
+        if constexpr (a == 1) { cu = ux; ca = bc(A.ax); }
+        else if constexpr (a == 2) { cu = uy; ca = ay; }
+        else if constexpr (a == 5) { cu = ux + uy; ca = ay + bc(A.ax); }
+        else { cu = uy - ux; ca = ay - bc(A.ax); }  // a == 6: c = (-1, 1)
+        const V2 q = fma2(cu * bc(4.5f), cu, uuneg);  // 4.5 (c.u)^2 - 1.5 u.u
+        const V2 pa = fma2(bc(3.0f), cu, q), pb = fma2(bc(-3.0f), cu, q);
+        const V2 wr = rho * bc(w), wrp = rp * bc(w);
+        feqd[a] = fma2(wr, pa, wrp);
+        feqd[b] = fma2(wr, pb, wrp);
+        const V2 t = ca * bc(3.0f);
+        const V2 m = fma2(cu * bc(3.0f), t, ua3neg);  // 9 (c.u)(c.a) - 3 u.a
+        F[a] = wr * (m + t);
+        F[b] = wr * (m - t);
+        if (TH) {
+            const V2 wT = T * bc(w), wTd = Td * bc(w);
+            geqd[a] = fma2(wT, pa, wTd);
+            geqd[b] = fma2(wT, pb, wTd);
+        }
+    }
+};
+
+__device__ __forceinline__ int slot5(int r) {
+    const int s = r % 5;
+    return s < 0 ? s + 5 : s;
+}
+
+// x metric of the thread's two columns: faces W (west of the left column),
+// M (between them) and E (east of the right one), both upwind directions.
+struct XPair {
+    float wp[3], mp[3], ep[3];  // c > 0: nodes (k-2, k-1, k) of face k
+    float wm[3], mm[3], em[3];  // c < 0: nodes (k-1, k, k+1)
+    V2 inv;
+};
+
+// y metric of one row, duplicated into pairs.
+struct YPair {
+    V2 ps[3], pn[3], ms[3], mn[3], inv;
+};
+
+__device__ __forceinline__ void load_ypair(const AxisMetric<float>& m, int g, YPair& Y) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        Y.ps[r] = bc(m.wp(r, g));
+        Y.pn[r] = bc(m.wp(r, g + 1));
+        Y.ms[r] = bc(m.wm(r, g));
+        Y.mn[r] = bc(m.wm(r, g + 1));
+    }
+    Y.inv = bc(m.invd(g));
+}
+
+// Flux divergence of ring plane p (population a) for the thread's two
+// columns; rows r-2..r+2 sit in slots sl[0..4], x neighbours are the pairs
+// of threads k-1 and k+1.
+template <int NQ, int NT, int a>
+__device__ __forceinline__ V2 advect_pair(const V2* ring, const int* sl, int p, int k, const XPair& X,
+                                          const YPair& Y) {
+    V2 v = bc(0.0f);
+    if constexpr (cx(a) != 0) {
+        const V2* row = ring + (sl[2] * NQ + p) * NT;
+        const float2 P0 = row[k - 1].v, P1 = row[k].v, P2 = row[k + 1].v;  // columns 2k-2 .. 2k+3
+        float fw, fm, fe;
+        if constexpr (cx(a) > 0) {
+            fw = X.wp[0] * P0.x + X.wp[1] * P0.y + X.wp[2] * P1.x;
+            fm = X.mp[0] * P0.y + X.mp[1] * P1.x + X.mp[2] * P1.y;
+            fe = X.ep[0] * P1.x + X.ep[1] * P1.y + X.ep[2] * P2.x;
+        } else {
+            fw = X.wm[0] * P0.y + X.wm[1] * P1.x + X.wm[2] * P1.y;
+            fm = X.mm[0] * P1.x + X.mm[1] * P1.y + X.mm[2] * P2.x;
+            fe = X.em[0] * P1.y + X.em[1] * P2.x + X.em[2] * P2.y;
+        }
+        const V2 dx = (mk(fm, fe) - mk(fw, fm)) * X.inv;
+        v = cx(a) > 0 ? dx : v - dx;
+    }
+    if constexpr (cy(a) != 0) {
+        V2 c[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) c[i] = ring[(sl[i] * NQ + p) * NT + k];
+        V2 fn, fs;
+        if constexpr (cy(a) > 0) {
+            fn = fma2(Y.pn[0], c[1], fma2(Y.pn[1], c[2], Y.pn[2] * c[3]));
+            fs = fma2(Y.ps[0], c[0], fma2(Y.ps[1], c[1], Y.ps[2] * c[2]));
+            v = fma2(fn - fs, Y.inv, v);
+        } else {
+            fn = fma2(Y.mn[0], c[2], fma2(Y.mn[1], c[3], Y.mn[2] * c[4]));
+            fs = fma2(Y.ms[0], c[1], fma2(Y.ms[1], c[2], Y.ms[2] * c[3]));
+            v = v - (fn - fs) * Y.inv;
+        }
+    }
+    return v;
+}
+
+template <bool TH, int NQ, int NT, int a>
+__device__ __forceinline__ void advect_all(const V2* ring, const int* sl, int k, const XPair& X, const YPair& Y,
+                                           const StepArgs<float>& A, int gy, V2* out) {
+    out[a] = advect_pair<NQ, NT, a>(ring, sl, a, k, X, Y) + bc(ref_flux<float, a>(A, gy, false));
+    if constexpr (TH) out[Q + a] = advect_pair<NQ, NT, a>(ring, sl, Q + a, k, X, Y) + bc(ref_flux<float, a>(A, gy, true));
+    if constexpr (a + 1 < Q) advect_all<TH, NQ, NT, a + 1>(ring, sl, k, X, Y, A, gy, out);
+}
+
+// Ghost row of a wall on y (own columns), base-state deviations: h'_a =
+// h'_inv(a) for f and -h'_inv(a) for g.
+template <bool TH, int NQ, int NT>
+__device__ __forceinline__ void ghost_row(V2* ring, int dst, int src, int k) {
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        ring[(dst * NQ + a) * NT + k] = ring[(src * NQ + inv(a)) * NT + k];
+        if constexpr (TH) ring[(dst * NQ + Q + a) * NT + k] = bc(0.0f) - ring[(src * NQ + Q + inv(a)) * NT + k];
+    }
+}
+
+}  // namespace
+
+template <typename S, bool TH, int NT>
+__global__ void __launch_bounds__(NT) k_fv_pair(const StepArgs<float> A, const int CH) {
+    constexpr int NQ = TH ? 2 * Q : Q;
+    constexpr int W = 2 * NT - 8;  // output columns per strip
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V2* sH = reinterpret_cast<V2*>(smem_raw);  // [5][NQ][NT] h^n
+    V2* sP = sH + 5 * NQ * NT;                 // [5][NQ][NT] f~ + Coll, then - dt/2 A[h^n] (own)
+    V2* sS = sP + 5 * NQ * NT;                 // [5][NQ][NT] h*
+    const int k = threadIdx.x;
+    const int xu = blockIdx.x * W - 4 + 2 * k;  // unwrapped left column of the pair
+    const int ys = blockIdx.y * CH;
+    const int ye = min(ys + CH, A.ny);
+    const int nx = A.nx;
+    const int gxl = ((xu % nx) + nx) % nx;
+    const int gxr = ((xu + 1) % nx + nx) % nx;
+    const bool contiguous = xu >= 0 && xu + 1 < nx;  // pair stored side by side
+    const bool colB = k >= 1 && k < NT - 1;
+    const bool colC = k >= 2 && k < NT - 2 && xu < nx;
+    const bool wally = A.bcy == LB_BC_WALLS;
+
+    XPair X;
+    if (colB) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            X.wp[r] = A.mx.wp(r, gxl);
+            X.mp[r] = A.mx.wp(r, gxl + 1);
+            X.ep[r] = A.mx.wp(r, gxr + 1);
+            X.wm[r] = A.mx.wm(r, gxl);
+            X.mm[r] = A.mx.wm(r, gxl + 1);
+            X.em[r] = A.mx.wm(r, gxr + 1);
+        }
+        X.inv = mk(A.mx.invd(gxl), A.mx.invd(gxr));
+    }
+
+    const S* fin = static_cast<const S*>(A.fin);
+    const S* gin = static_cast<const S*>(A.gin);
+    S* fout = static_cast<S*>(A.fout);
+    S* gout = static_cast<S*>(A.gout);
+
+    auto fluid_row = [&](int r, int& gy) { return map_axis(r, A.ny, A.bcy, gy); };
+    auto load_pair = [&](const S* base, int gy, V2& out) {
+        const long long row = (long long)gy * A.pitch;
+        if (contiguous) {
+            out = PairIO<S>::ld(base + row + xu);
+        } else {
+            out = mk(Store<S>::ld(base + row + gxl), Store<S>::ld(base + row + gxr));
+        }
+    };
+    // populations of row r into (bd, be); rows are loaded two iterations
+    // before stage A needs them, so the DRAM latency overlaps two rows of work
+    auto prefetch = [&](int r, V2* bd, V2* be) {
+        int gy;
+        if (r < ye + 4 && fluid_row(r, gy)) {
+#pragma unroll
+            for (int a = 0; a < Q; ++a) load_pair(fin + a * A.plane, gy, bd[a]);
+            if constexpr (TH) {
+#pragma unroll
+                for (int a = 0; a < Q; ++a) load_pair(gin + a * A.plane, gy, be[a]);
+            }
+        }
+    };
+
+    // one row iteration; (bd, be) holds row t on entry and row t + 2 on exit
+    auto iteration = [&](const int t, V2* bd, V2* be) {
+        // ---- stage A on row t ----
+        {
+            int gy;
+            const int s = slot5(t);
+            if (fluid_row(t, gy)) {
+                V2 d[Q], e[Q];
+#pragma unroll
+                for (int a = 0; a < Q; ++a) {
+                    d[a] = bd[a];
+                    if constexpr (TH) e[a] = be[a];
+                }
+                prefetch(t + 2, bd, be);
+                PairCell<TH> m;
+                m.build(d, e, A, A.roff[gy], TH ? A.toff[gy] : 0.0f);
+#pragma unroll
+                for (int a = 0; a < Q; ++a) {
+                    const V2 neq = m.feqd[a] - d[a];
+                    sH[(s * NQ + a) * NT + k] = fma2(bc(A.omh), neq, fma2(bc(A.hf), m.F[a], d[a]));
+                    sP[(s * NQ + a) * NT + k] = fma2(bc(A.om), neq, fma2(bc(A.cf), m.F[a], d[a]));
+                    if constexpr (TH) {
+                        const V2 neqg = m.geqd[a] - e[a];
+                        sH[(s * NQ + Q + a) * NT + k] = fma2(bc(A.omgh), neqg, e[a]);
+                        sP[(s * NQ + Q + a) * NT + k] = fma2(bc(A.omg), neqg, e[a]);
+                    }
+                }
+            } else {
+                prefetch(t + 2, bd, be);
+                if (wally && (t == A.ny || t == A.ny + 1)) ghost_row<TH, NQ, NT>(sH, s, slot5(2 * A.ny - 1 - t), k);
+            }
+            if (wally && t == 1 && ys == 0) {
+                ghost_row<TH, NQ, NT>(sH, slot5(-1), slot5(0), k);
+                ghost_row<TH, NQ, NT>(sH, slot5(-2), slot5(1), k);
+            }
+        }
+        // ---- stage B on row t - 2 ----
+        {
+            const int r = t - 2;
+            int gy;
+            if (r >= ys - 2 && r < ye + 2) {
+                const int s = slot5(r);
+                if (fluid_row(r, gy)) {
+                    if (colB) {
+                        YPair Y;
+                        load_ypair(A.my, gy, Y);
+                        const int sl[5] = {slot5(r - 2), slot5(r - 1), s, slot5(r + 1), slot5(r + 2)};
+                        V2 adv[NQ];
+                        advect_all<TH, NQ, NT, 0>(sH, sl, k, X, Y, A, gy, adv);
+                        V2 fs[Q], es[Q];
+#pragma unroll
+                        for (int a = 0; a < Q; ++a) {
+                            const V2 fc = sP[(s * NQ + a) * NT + k];
+                            fs[a] = fma2(bc(-A.dt), adv[a], fc);
+                            sP[(s * NQ + a) * NT + k] = fma2(bc(-A.hf), adv[a], fc);
+                            if constexpr (TH) {
+                                const V2 gc = sP[(s * NQ + Q + a) * NT + k];
+                                es[a] = fma2(bc(-A.dt), adv[Q + a], gc);
+                                sP[(s * NQ + Q + a) * NT + k] = fma2(bc(-A.hf), adv[Q + a], gc);
+                            }
+                        }
+                        PairCell<TH> m;
+                        m.build(fs, es, A, A.roff[gy], TH ? A.toff[gy] : 0.0f);
+#pragma unroll
+                        for (int a = 0; a < Q; ++a) {
+                            sS[(s * NQ + a) * NT + k] =
+                                fma2(bc(A.omh), m.feqd[a] - fs[a], fma2(bc(A.hf), m.F[a], fs[a]));
+                            if constexpr (TH)
+                                sS[(s * NQ + Q + a) * NT + k] = fma2(bc(A.omgh), m.geqd[a] - es[a], es[a]);
+                        }
+                    }
+                } else if (wally && (r == A.ny || r == A.ny + 1)) {
+                    ghost_row<TH, NQ, NT>(sS, s, slot5(2 * A.ny - 1 - r), k);
+                }
+                if (wally && r == 1 && ys == 0) {
+                    ghost_row<TH, NQ, NT>(sS, slot5(-1), slot5(0), k);
+                    ghost_row<TH, NQ, NT>(sS, slot5(-2), slot5(1), k);
+                }
+            }
+        }
+        // ---- stage C on row t - 4 ----
+        {
+            const int r = t - 4;
+            if (r >= ys && r < ye && colC) {
+                const int s = slot5(r);
+                YPair Y;
+                load_ypair(A.my, r, Y);
+                const int sl[5] = {slot5(r - 2), slot5(r - 1), s, slot5(r + 1), slot5(r + 2)};
+                V2 adv[NQ];
+                advect_all<TH, NQ, NT, 0>(sS, sl, k, X, Y, A, r, adv);
+                const long long row = (long long)r * A.pitch;
+                const bool both = xu + 1 < nx;
+#pragma unroll
+                for (int a = 0; a < NQ; ++a) {
+                    const V2 o = fma2(bc(-A.hf), adv[a], sP[(s * NQ + a) * NT + k]);
+                    S* base = (a < Q ? fout + a * A.plane : gout + (a - Q) * A.plane) + row;
+                    if (both) PairIO<S>::st(base + xu, o);
+                    else Store<S>::st(base + xu, o.v.x);
+                }
+            }
+        }
+        __syncthreads();
+    };
+
+    // two register buffers in turn: even rows in (d0, e0), odd rows in (d1, e1)
+    V2 d0[Q], e0[Q], d1[Q], e1[Q];
+    prefetch(ys - 4, d0, e0);
+    prefetch(ys - 3, d1, e1);
+    for (int t = ys - 4; t < ye + 4; t += 2) {
+        iteration(t, d0, e0);
+        if (t + 1 < ye + 4) iteration(t + 1, d1, e1);
+    }
+}
+
+template <typename S, bool TH, int NT>
+static cudaError_t run_pair(const void* vargs, int chunk, cudaStream_t s) {
+    const StepArgs<float>& A = *static_cast<const StepArgs<float>*>(vargs);
+    constexpr int NQ = TH ? 2 * Q : Q;
+    constexpr size_t smem = sizeof(V2) * 15 * NQ * NT;
+    static_assert(smem <= 232448, "shared memory per CTA");
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_fv_pair<S, TH, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    const int ch = chunk < 8 ? 8 : chunk;
+    constexpr int W = 2 * NT - 8;
+    dim3 grid((A.nx + W - 1) / W, (A.ny + ch - 1) / ch);
+    k_fv_pair<S, TH, NT><<<grid, NT, smem, s>>>(A, ch);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fv_pair(Prec p, bool th, const void* args, int chunk, cudaStream_t s) {
+    switch (p) {
+        case Prec::F32: return th ? run_pair<float, true, 64>(args, chunk, s) : run_pair<float, false, 64>(args, chunk, s);
+        case Prec::F16: return th ? run_pair<__half, true, 64>(args, chunk, s) : run_pair<__half, false, 64>(args, chunk, s);
+        case Prec::BF16:
+            return th ? run_pair<__nv_bfloat16, true, 64>(args, chunk, s)
+                      : run_pair<__nv_bfloat16, false, 64>(args, chunk, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+int pair_width() { return 2 * 64 - 8; }
+
+size_t pair_smem(bool th) { return sizeof(float2) * 15 * (th ? 18 : 9) * 64; }
+
+}  // namespace lbgb

@@ -248,34 +248,44 @@ lb_status check_ready(lb_grid* G) {
     return LB_OK;
 }
 
-// Schedule actually used: AUTO takes the marching kernel once the grid is
-// wide and tall enough to fill the GPU with strips, else the tile kernel.
+bool pair_ok(const lb_grid* G) { return G->prec != Prec::F64 && G->d.bcx == LB_BC_PERIODIC; }
+
+// Schedule actually used: AUTO takes a marching kernel (the paired one when
+// it applies) once the grid is wide and tall enough to fill the GPU with
+// strips, else the tile kernel.
 int resolved_kernel(const lb_grid* G) {
     if (G->fv_kernel != LB_FV_AUTO) return G->fv_kernel;
-    return (G->nx >= 480 && G->ny >= 256) ? LB_FV_MARCH : LB_FV_TILE;
+    if (G->nx >= 480 && G->ny >= 256) return pair_ok(G) ? LB_FV_PAIR : LB_FV_MARCH;
+    return LB_FV_TILE;
 }
 
-// Rows per CTA of the marching kernel: one wave of resident CTAs.
+// Rows per CTA of the marching kernels: one wave of resident CTAs.
 int resolved_chunk(const lb_grid* G) {
     if (G->fv_chunk > 0) return G->fv_chunk;
     const bool th = G->d.thermal != 0;
-    const int strips = (G->nx + march_width(G->prec, th) - 1) / march_width(G->prec, th);
-    const size_t smem = march_smem(G->prec, th);
+    const bool pr = resolved_kernel(G) == LB_FV_PAIR;
+    const int width = pr ? pair_width() : march_width(G->prec, th);
+    const int strips = (G->nx + width - 1) / width;
+    const size_t smem = pr ? pair_smem(th) : march_smem(G->prec, th);
     int per_sm = (int)(227 * 1024 / smem);
     if (per_sm < 1) per_sm = 1;
     if (per_sm > 4) per_sm = 4;
+    // about four waves of resident CTAs: short marches balance better than
+    // one wave with a ragged tail, at 12 halo rows per chunk
     const long long slots = (long long)G->sms * per_sm;
-    long long chunks = (slots + strips - 1) / strips;
+    long long chunks = (4 * slots + strips - 1) / strips;
     if (chunks < 1) chunks = 1;
     int ch = (int)((G->ny + chunks - 1) / chunks);
-    return ch < 16 ? 16 : ch;
+    return ch < 32 ? 32 : ch;
 }
 
 template <typename R>
 cudaError_t launch_fv_step(lb_grid* G) {
     StepArgs<R> A = step_args<R>(G, G->p.dt);
     const bool th = G->d.thermal != 0;
-    if (resolved_kernel(G) == LB_FV_MARCH) return launch_fv_march(G->prec, th, &A, resolved_chunk(G), G->stream);
+    const int k = resolved_kernel(G);
+    if (k == LB_FV_PAIR) return launch_fv_pair(G->prec, th, &A, resolved_chunk(G), G->stream);
+    if (k == LB_FV_MARCH) return launch_fv_march(G->prec, th, &A, resolved_chunk(G), G->stream);
     return launch_fv(G->prec, th, &A, G->stream);
 }
 
@@ -538,8 +548,10 @@ lb_status lb_step_fv(lb_grid* G, int nsteps) {
 
 lb_status lb_set_fv_schedule(lb_grid* G, int kernel, int chunk) {
     if (!G) return fail(LB_ERR_ARG, "grid is NULL");
-    if (kernel < LB_FV_AUTO || kernel > LB_FV_MARCH) return fail(LB_ERR_ARG, "unknown FV kernel %d", kernel);
+    if (kernel < LB_FV_AUTO || kernel > LB_FV_PAIR) return fail(LB_ERR_ARG, "unknown FV kernel %d", kernel);
     if (chunk < 0) return fail(LB_ERR_ARG, "chunk must be >= 0");
+    if (kernel == LB_FV_PAIR && !pair_ok(G))
+        return fail(LB_ERR_ARG, "the paired FV kernel needs FP32/FP16/BF16 storage and a periodic x axis");
     G->fv_kernel = kernel;
     G->fv_chunk = chunk;
     return LB_OK;
@@ -548,7 +560,7 @@ lb_status lb_set_fv_schedule(lb_grid* G, int kernel, int chunk) {
 lb_status lb_get_fv_schedule(lb_grid* G, int* kernel, int* chunk) {
     if (!G) return fail(LB_ERR_ARG, "grid is NULL");
     if (kernel) *kernel = resolved_kernel(G);
-    if (chunk) *chunk = resolved_kernel(G) == LB_FV_MARCH ? resolved_chunk(G) : 0;
+    if (chunk) *chunk = resolved_kernel(G) == LB_FV_TILE ? 0 : resolved_chunk(G);
     return LB_OK;
 }
 
@@ -568,12 +580,15 @@ lb_status lb_autotune_fv(lb_grid* G, int steps) {
     cudaMemcpyAsync(sf, G->f[cur0], bytes, cudaMemcpyDeviceToDevice, G->stream);
     if (sg) cudaMemcpyAsync(sg, G->g[cur0], bytes, cudaMemcpyDeviceToDevice, G->stream);
     const int k0 = G->fv_kernel, c0 = G->fv_chunk;
-    G->fv_kernel = LB_FV_MARCH;
-    G->fv_chunk = 0;
-    const int base = resolved_chunk(G);
     std::vector<std::pair<int, int>> cands = {{LB_FV_TILE, 0}};
-    for (int ch : {base / 2, base, base * 2, 32, 64, 128})
-        if (ch >= 16 && ch <= 4 * G->ny) cands.push_back({LB_FV_MARCH, ch});
+    for (int kern : {(int)LB_FV_MARCH, (int)LB_FV_PAIR}) {
+        if (kern == LB_FV_PAIR && !pair_ok(G)) continue;
+        G->fv_kernel = kern;
+        G->fv_chunk = 0;
+        const int base = resolved_chunk(G);
+        for (int ch : {base / 2, base, base * 2, 32, 64, 128})
+            if (ch >= 16 && ch <= 4 * G->ny) cands.push_back({kern, ch});
+    }
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);

@@ -183,6 +183,10 @@ cudaError_t launch_fv(Prec p, bool thermal, const void* args, cudaStream_t s);
 cudaError_t launch_fv_march(Prec p, bool thermal, const void* args, int chunk, cudaStream_t s);
 int march_width(Prec p, bool thermal);
 size_t march_smem(Prec p, bool thermal);
+// paired-column marching FV kernel (FP32 arithmetic, x-periodic grids only)
+cudaError_t launch_fv_pair(Prec p, bool thermal, const void* args, int chunk, cudaStream_t s);
+int pair_width();
+size_t pair_smem(bool thermal);
 
 struct AuxArgs {
     const void* f;  // state buffers (deviation storage)

@@ -148,14 +148,45 @@ def test_fv_step_f64(lbgpu, oracle, case, sched):
         assert np.abs(ggg - ggr).max() < 1e-13
 
 
+@pytest.mark.parametrize("sched", [(1, 0), (2, 16), (3, 8), (3, 16), (3, 0)], ids=lambda s: f"k{s[0]}c{s[1]}")
+@pytest.mark.parametrize("case", [c for c in FV_CASES if c.get("bcx", 0) == 0],
+                         ids=lambda c: "-".join(f"{k}{v}" for k, v in c.items()))
+def test_fv_step_f32_schedules(lbgpu, oracle, case, sched):
+    """FP32 kernels (tile, march and the paired f32x2 march) element by
+    element against the FP64 oracle: after 3 steps every population agrees
+    to 2e-6 of the deviation scale."""
+    nx, ny = case["nx"], case["ny"]
+    th = case.get("thermal", False)
+    kw = dict(tau=0.3, dt=0.05, ax=2e-4, ay=-1e-4)
+    if th:
+        kw.update(tau_g=0.25, beta=1e-2, grav=1.0, T0=1.0, T_bot=1.3, T_top=0.8)
+    g, r = pair(lbgpu, oracle, store=lbgpu.LB_STORE_F32, **case, **kw)
+    g.set_fv_schedule(*sched)
+    f = inputs.random_populations(nx, ny, seed=3 * nx + ny, amp=0.2)
+    gg = inputs.random_populations(nx, ny, seed=11, amp=0.2) if th else None
+    g.set_pops(f, gg)
+    # start both sides from the FP32-rounded state
+    f, gg = g.get_pops()
+    r.set_pops(f, gg)
+    g.step_fv(3)
+    r.step_fv(3)
+    fg, ggg = g.get_pops()
+    fr, ggr = r.get_pops()
+    wts = oracle.lattice()[2][:, None, None]
+    scale = np.abs(f - wts).max()
+    assert np.abs(fg - fr).max() <= 2e-6 * scale
+    if th:
+        assert np.abs(ggg - ggr).max() <= 2e-6 * np.abs(gg - wts).max()
+
+
 @pytest.mark.parametrize("store", ["f32"])
-@pytest.mark.parametrize("scheme", ["st", "fv", "fv-march"])
+@pytest.mark.parametrize("scheme", ["st", "fv", "fv-march", "fv-pair"])
 def test_f32_paths(lbgpu, oracle, scheme, store):
     """FP32 arithmetic on deviations: relative L2 velocity error <= 1e-5."""
     dt = 1.0 if scheme == "st" else 0.5
     g, r = pair(lbgpu, oracle, 64, 48, store, ly=48.0, tau=0.3, dt=dt, ax=1e-6, kind=0, u0=0.02)
-    if scheme == "fv-march":
-        g.set_fv_schedule(lbgpu.LB_FV_MARCH, 16)
+    if scheme in ("fv-march", "fv-pair"):
+        g.set_fv_schedule(lbgpu.LB_FV_MARCH if scheme == "fv-march" else lbgpu.LB_FV_PAIR, 16)
         scheme = "fv"
     for x in (g, r):
         (x.step_st if scheme == "st" else x.step_fv)(200)
