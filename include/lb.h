@@ -210,6 +210,57 @@ lb_status lb_conservation_noalloc(const float* f, const float* g, int nx, int ny
                                   double ay, double beta_grav, double T0, double* out,
                                   void* cuda_stream);
 
+/* ---- Serving: continuous batching of independent FV simulations ----
+ * The paper's parameter studies (Sec. III, IV: many runs over grid sizes,
+ * Rayleigh numbers and step counts) as a stream of requests.  A server
+ * owns the requests' grids; every lb_server_pump() admits queued requests
+ * in arrival order while their memory fits (the budget and the device's free
+ * memory), advances all active requests together by up to
+ * steps_per_launch FV steps (Eq. (semi-heun)) in one batched kernel per
+ * step over a device table of (request, tile) entries, replayed from a
+ * captured CUDA graph, and retires the requests that are done.  Every tile
+ * is stepped by the same code whatever else is in the table, so a request's
+ * result is bit-for-bit the same alone and in any batch; it is the
+ * LB_FV_TILE step of lb_step_fv (equal up to FP32 rounding, since the two are
+ * compiled separately). */
+typedef struct lb_server lb_server;
+
+typedef struct {
+    long long id;          /* caller's tag, returned in the result            */
+    lb_grid_desc grid;     /* its cuda_stream is ignored (the server's is used) */
+    lb_params params;
+    lb_init_desc init;     /* LB_INIT_FIELDS arrays must live until the request is admitted */
+    int nsteps;            /* FV steps to take                                */
+} lb_request;
+
+typedef struct {
+    long long id;
+    int status;            /* LB_OK, or the failure that ended the request    */
+    int steps;             /* steps taken                                     */
+    long long cells;       /* nx * ny                                         */
+    double nu_vol, nu_bot, nu_top; /* Nusselt numbers (thermal servers)       */
+    double mass;           /* sum V rho at the end                             */
+    double t_submit, t_admit, t_done; /* seconds on the server clock          */
+} lb_result;
+
+/* store/thermal: the one storage type and model all requests use.
+ * hbm_budget: bytes of device memory the requests may hold at once.
+ * steps_per_launch: >= 1 (steps per pump).  cuda_stream: NULL lets the server create
+ * its own non-blocking stream (graph capture needs a non-default stream). */
+lb_status lb_server_create(int store, int thermal, unsigned long long hbm_budget, int steps_per_launch,
+                           void* cuda_stream, lb_server** out);
+/* Queue a request (host side only).  LB_ERR_ARG if its storage or thermal
+ * flag differs from the server's or it alone exceeds the budget. */
+lb_status lb_server_submit(lb_server* server, const lb_request* request);
+/* Admit, advance and retire as described above.  Synchronous.  Reports how
+ * many requests are active and still queued afterwards. */
+lb_status lb_server_pump(lb_server* server, int* n_active, int* n_pending);
+/* Move up to max finished results into out; *n receives the count. */
+lb_status lb_server_results(lb_server* server, lb_result* out, int max, int* n);
+/* Seconds since the server was created (the clock of lb_result). */
+double lb_server_clock(lb_server* server);
+lb_status lb_server_destroy(lb_server* server);
+
 /* Wait for all work queued on the grid's stream. */
 lb_status lb_sync(lb_grid* grid);
 

@@ -57,11 +57,24 @@ class lb_init_desc(C.Structure):
                 ("seed", C.c_ulonglong), ("rho", _DP), ("ux", _DP), ("uy", _DP), ("T", _DP)]
 
 
+class lb_request(C.Structure):
+    _fields_ = [("id", C.c_longlong), ("grid", lb_grid_desc), ("params", lb_params),
+                ("init", lb_init_desc), ("nsteps", C.c_int)]
+
+
+class lb_result(C.Structure):
+    _fields_ = [("id", C.c_longlong), ("status", C.c_int), ("steps", C.c_int), ("cells", C.c_longlong),
+                ("nu_vol", C.c_double), ("nu_bot", C.c_double), ("nu_top", C.c_double),
+                ("mass", C.c_double), ("t_submit", C.c_double), ("t_admit", C.c_double),
+                ("t_done", C.c_double)]
+
+
 SYMBOLS = ["lb_create_grid", "lb_init", "lb_step_fv", "lb_step_st", "lb_moments",
            "lb_conservation", "lb_nusselt", "lb_set_populations", "lb_get_populations",
            "lb_get_window", "lb_sync", "lb_destroy", "lb_last_error", "lb_kernel_launches",
            "lb_conservation_noalloc", "lb_set_fv_schedule", "lb_get_fv_schedule",
-           "lb_autotune_fv"]
+           "lb_autotune_fv", "lb_server_create", "lb_server_submit", "lb_server_pump",
+           "lb_server_results", "lb_server_clock", "lb_server_destroy"]
 LB_FV_AUTO, LB_FV_TILE, LB_FV_MARCH, LB_FV_PAIR = 0, 1, 2, 3
 
 _lib = None
@@ -98,12 +111,20 @@ def load(build: bool = True) -> C.CDLL:
     L.lb_set_fv_schedule.argtypes = [G, C.c_int, C.c_int]
     L.lb_get_fv_schedule.argtypes = [G, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.lb_autotune_fv.argtypes = [G, C.c_int]
+    L.lb_server_create.argtypes = [C.c_int, C.c_int, C.c_ulonglong, C.c_int, C.c_void_p,
+                                   C.POINTER(C.c_void_p)]
+    L.lb_server_submit.argtypes = [C.c_void_p, C.POINTER(lb_request)]
+    L.lb_server_pump.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+    L.lb_server_results.argtypes = [C.c_void_p, C.POINTER(lb_result), C.c_int, C.POINTER(C.c_int)]
+    L.lb_server_clock.argtypes = [C.c_void_p]
+    L.lb_server_clock.restype = C.c_double
+    L.lb_server_destroy.argtypes = [C.c_void_p]
     L.lb_sync.argtypes = [G]
     L.lb_destroy.argtypes = [G]
     L.lb_last_error.restype = C.c_char_p
     L.lb_kernel_launches.restype = C.c_ulonglong
     for name in SYMBOLS:
-        if name not in ("lb_last_error", "lb_kernel_launches"):
+        if name not in ("lb_last_error", "lb_kernel_launches", "lb_server_clock"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -319,3 +340,59 @@ class Grid:
     def sync(self):
         lb_sync(self._h)
         return self
+
+
+class Server:
+    """Continuous-batching server of FV requests (see include/lb.h)."""
+
+    def __init__(self, store=LB_STORE_F32, thermal=True, hbm_budget=64 << 30, steps_per_launch=50,
+                 stream=None):
+        if isinstance(store, str):
+            store = STORE_NAMES[store]
+        self.store, self.thermal = int(store), bool(thermal)
+        h = C.c_void_p()
+        _check(load().lb_server_create(self.store, int(self.thermal), int(hbm_budget),
+                                       int(steps_per_launch), stream, C.byref(h)))
+        self._h = h
+        self._keep = {}
+
+    def submit(self, rid, nsteps, nx, ny, lx=None, ly=None, sx=LB_AXIS_UNIFORM, sy=LB_AXIS_UNIFORM,
+               stretch_x=0.0, stretch_y=0.0, bcx=LB_BC_PERIODIC, bcy=LB_BC_PERIODIC, tau=0.3, dt=1.0,
+               tau_g=None, ax=0.0, ay=0.0, beta=0.0, grav=0.0, T0=1.0, T_bot=1.0, T_top=1.0,
+               kind=LB_INIT_RB, u0=0.0, amp=0.0, mode=1, seed=0):
+        req = lb_request()
+        req.id = int(rid)
+        req.grid = lb_grid_desc(int(nx), int(ny), float(nx if lx is None else lx),
+                                float(ny if ly is None else ly), int(sx), int(sy), float(stretch_x),
+                                float(stretch_y), int(bcx), int(bcy), int(self.thermal), self.store, None)
+        req.params = lb_params(float(tau), float(dt), float(tau if tau_g is None else tau_g), float(ax),
+                               float(ay), float(beta), float(grav), float(T0), float(T_bot), float(T_top))
+        req.init = lb_init_desc(int(kind), int(mode), float(u0), float(amp), int(seed), None, None, None, None)
+        req.nsteps = int(nsteps)
+        _check(load().lb_server_submit(self._h, C.byref(req)))
+
+    def pump(self):
+        a, p = C.c_int(), C.c_int()
+        _check(load().lb_server_pump(self._h, C.byref(a), C.byref(p)))
+        return a.value, p.value
+
+    def results(self, max_n=4096):
+        buf = (lb_result * max_n)()
+        n = C.c_int()
+        _check(load().lb_server_results(self._h, buf, int(max_n), C.byref(n)))
+        fields = [f for f, _ in lb_result._fields_]
+        return [{f: getattr(buf[i], f) for f in fields} for i in range(n.value)]
+
+    def clock(self):
+        return float(load().lb_server_clock(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            load().lb_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

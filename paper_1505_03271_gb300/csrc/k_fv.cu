@@ -112,8 +112,9 @@ __device__ void ghost_fill(R* P, int plane, int W, int H, int gx0, int gy0, cons
     }
 }
 
+// One FV step on the tile whose first cell is (x0, y0).
 template <typename R, typename S, bool TH, int TX, int TY>
-__global__ void __launch_bounds__(kFvThreads) k_fv(const StepArgs<R> A) {
+__device__ __forceinline__ void fv_tile(const StepArgs<R>& A, const int x0, const int y0) {
     constexpr int NQ = TH ? 2 * Q : Q;
     constexpr int EX = TX + 8, EY = TY + 8, NE = EX * EY;
     constexpr int BX = TX + 4, BY = TY + 4, NB = BX * BY;
@@ -121,7 +122,6 @@ __global__ void __launch_bounds__(kFvThreads) k_fv(const StepArgs<R> A) {
     R* sH = reinterpret_cast<R*>(smem_raw);  // [NQ][EY][EX]  h^n
     R* sFC = sH + NQ * NE;                   // [NQ][BY][BX]  f~ + Coll, then f~ + Coll - dt/2 A^n
     R* sHs = sFC + NQ * NB;                  // [NQ][BY][BX]  h*
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const S* fin = static_cast<const S*>(A.fin);
     const S* gin = static_cast<const S*>(A.gin);
 
@@ -213,6 +213,75 @@ __global__ void __launch_bounds__(kFvThreads) k_fv(const StepArgs<R> A) {
             if constexpr (TH) Store<S>::st(gout + a * A.plane + c, sFC[(Q + a) * NB + kb] - A.hf * adv[Q + a]);
         }
     }
+}
+
+template <typename R, typename S, bool TH, int TX, int TY>
+__global__ void __launch_bounds__(kFvThreads) k_fv(const StepArgs<R> A) {
+    fv_tile<R, S, TH, TX, TY>(A, blockIdx.x * TX, blockIdx.y * TY);
+}
+
+// Many grids in one launch: CTA b steps tile tiles[b] = (request, tile x,
+// tile y) of request reqs[tile.x], using step k of the launch sequence to
+// pick that request's input buffer; requests with fewer than k + 1 steps
+// left are skipped.  Each tile runs the tile code of k_fv with parameters
+// read from the table, so a request gives the same bits alone and in any
+// batch.
+template <typename R, typename S, bool TH, int TX, int TY>
+__global__ void __launch_bounds__(kFvThreads)
+k_fv_batched(const BatchReq<R>* reqs, const int4* tiles, const int* ntiles, const int k) {
+    if ((int)blockIdx.x >= *ntiles) return;
+    const int4 t = tiles[blockIdx.x];
+    const BatchReq<R>& B = reqs[t.x];
+    if (k >= B.remaining) return;
+    StepArgs<R> A = B.args;
+    const int p = (B.parity + k) & 1;
+    A.fin = B.f[p];
+    A.fout = B.f[p ^ 1];
+    A.gin = B.g[p];
+    A.gout = B.g[p ^ 1];
+    fv_tile<R, S, TH, TX, TY>(A, t.y * TX, t.z * TY);
+}
+
+template <typename R, typename S, bool TH, int TX, int TY>
+static cudaError_t run_fv_batched(const void* reqs, const int4* tiles, const int* ntiles, int capacity, int k,
+                                  cudaStream_t s) {
+    constexpr int NQ = TH ? 2 * Q : Q;
+    constexpr size_t smem = sizeof(R) * (size_t)NQ * ((TX + 8) * (TY + 8) + 2 * (TX + 4) * (TY + 4));
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_fv_batched<R, S, TH, TX, TY>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    k_fv_batched<R, S, TH, TX, TY><<<capacity, kFvThreads, smem, s>>>(static_cast<const BatchReq<R>*>(reqs),
+                                                                      tiles, ntiles, k);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fv_batched(Prec p, bool th, const void* reqs, const int4* tiles, const int* ntiles,
+                              int capacity, int k, cudaStream_t s) {
+    switch (p) {
+        case Prec::F64:
+            return th ? run_fv_batched<double, double, true, 16, 16>(reqs, tiles, ntiles, capacity, k, s)
+                      : run_fv_batched<double, double, false, 32, 16>(reqs, tiles, ntiles, capacity, k, s);
+        case Prec::F32:
+            return th ? run_fv_batched<float, float, true, 32, 16>(reqs, tiles, ntiles, capacity, k, s)
+                      : run_fv_batched<float, float, false, 32, 16>(reqs, tiles, ntiles, capacity, k, s);
+        case Prec::F16:
+            return th ? run_fv_batched<float, __half, true, 32, 16>(reqs, tiles, ntiles, capacity, k, s)
+                      : run_fv_batched<float, __half, false, 32, 16>(reqs, tiles, ntiles, capacity, k, s);
+        case Prec::BF16:
+            return th ? run_fv_batched<float, __nv_bfloat16, true, 32, 16>(reqs, tiles, ntiles, capacity, k, s)
+                      : run_fv_batched<float, __nv_bfloat16, false, 32, 16>(reqs, tiles, ntiles, capacity, k, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+void tile_shape(Prec p, bool th, int* tx, int* ty) {
+    *tx = (p == Prec::F64 && th) ? 16 : 32;
+    *ty = 16;
 }
 
 template <typename R, typename S, bool TH, int TX, int TY>

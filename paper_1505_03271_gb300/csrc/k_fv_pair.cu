@@ -16,111 +16,13 @@
 //     face values for two cells instead of four.
 // The kernel serves x-periodic grids (every workload here); grids with walls
 // on x use the scalar kernels.
-#include "lb_internal.cuh"
+#include "lb_pair.cuh"
 
 namespace lbgb {
 
 namespace {
 
-struct V2 {
-    float2 v;
-};
-__device__ __forceinline__ V2 mk(float a, float b) { return {make_float2(a, b)}; }
-__device__ __forceinline__ V2 bc(float s) { return {make_float2(s, s)}; }
-__device__ __forceinline__ V2 operator+(V2 a, V2 b) { return {__fadd2_rn(a.v, b.v)}; }
-__device__ __forceinline__ V2 operator*(V2 a, V2 b) { return {__fmul2_rn(a.v, b.v)}; }
-__device__ __forceinline__ V2 fma2(V2 a, V2 b, V2 c) { return {__ffma2_rn(a.v, b.v, c.v)}; }
-__device__ __forceinline__ V2 operator-(V2 a, V2 b) { return fma2(b, bc(-1.0f), a); }
-
-// Pair loads/stores of the deviation storage (see Store<> for the scales).
-template <typename S> struct PairIO;
-template <> struct PairIO<float> {
-    __device__ static V2 ld(const float* p) { return {__ldg(reinterpret_cast<const float2*>(p))}; }
-    __device__ static void st(float* p, V2 v) { *reinterpret_cast<float2*>(p) = v.v; }
-};
-template <> struct PairIO<__half> {
-    __device__ static V2 ld(const __half* p) {
-        float2 f = __half22float2(__ldg(reinterpret_cast<const __half2*>(p)));
-        return {make_float2(f.x * (1.0f / kF16Scale), f.y * (1.0f / kF16Scale))};
-    }
-    __device__ static void st(__half* p, V2 v) {
-        *reinterpret_cast<__half2*>(p) = __floats2half2_rn(v.v.x * kF16Scale, v.v.y * kF16Scale);
-    }
-};
-template <> struct PairIO<__nv_bfloat16> {
-    __device__ static V2 ld(const __nv_bfloat16* p) {
-        return {__bfloat1622float2(__ldg(reinterpret_cast<const __nv_bfloat162*>(p)))};
-    }
-    __device__ static void st(__nv_bfloat16* p, V2 v) {
-        *reinterpret_cast<__nv_bfloat162*>(p) = __floats2bfloat162_rn(v.v.x, v.v.y);
-    }
-};
-
-// Collision data of a pair of cells on one row (base-state frame, see
-// lb_internal.cuh): moments, then per population the deviation of f_eq, the
-// Guo force and (thermal) the deviation of g_eq.
-template <bool TH>
-struct PairCell {
-    V2 rp, rho, ux, uy, Td, T, ay, uuneg, ua3neg;
-    V2 feqd[Q], F[Q], geqd[Q];
-
-    __device__ __forceinline__ void build(const V2* d, const V2* e, const StepArgs<float>& A, float ro, float to) {
-        V2 r = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
-        V2 jx = (d[1] + d[5] + d[8]) - (d[3] + d[6] + d[7]);
-        V2 jy = (d[2] + d[5] + d[6]) - (d[4] + d[7] + d[8]);
-        rp = r;
-        rho = r + bc(1.0f + ro);
-        V2 ir = mk(__fdividef(1.0f, rho.v.x), __fdividef(1.0f, rho.v.y));
-        if (TH) {
-            Td = ((e[0] + e[1]) + (e[2] + e[3])) + ((e[4] + e[5]) + (e[6] + e[7])) + e[8];
-            const V2 dT0 = Td + bc(to);
-            T = dT0 + bc(A.T0);
-            ay = fma2(bc(A.bg), dT0, bc(A.ay));
-        } else {
-            ay = bc(A.ay);
-        }
-        ux = fma2(jx, ir, bc(A.hf * A.ax));
-        uy = fma2(ay, bc(A.hf), jy * ir);
-        uuneg = (ux * ux + uy * uy) * bc(-1.5f);
-        ua3neg = fma2(uy, ay, ux * bc(A.ax)) * bc(-3.0f);
-        // rest population: c = 0
-        const float w0 = wgt<float>(0);
-        const V2 wr0 = rho * bc(w0);
-        feqd[0] = fma2(wr0, uuneg, rp * bc(w0));
-        F[0] = wr0 * ua3neg;
-        if (TH) geqd[0] = fma2(T * bc(w0), uuneg, Td * bc(w0));
-        pair<1>(A);
-        pair<2>(A);
-        pair<5>(A);
-        pair<6>(A);
-    }
-
-    // populations a and inv(a): c.u and c.a flip sign, squares do not.
-    template <int a>
-    __device__ __forceinline__ void pair(const StepArgs<float>& A) {
-        constexpr int b = inv(a);
-        const float w = wgt<float>(a);
-        V2 cu, ca;
-        if constexpr (a == 1) { cu = ux; ca = bc(A.ax); }
-        else if constexpr (a == 2) { cu = uy; ca = ay; }
-        else if constexpr (a == 5) { cu = ux + uy; ca = ay + bc(A.ax); }
-        else { cu = uy - ux; ca = ay - bc(A.ax); }  // a == 6: c = (-1, 1)
-        const V2 q = fma2(cu * bc(4.5f), cu, uuneg);  // 4.5 (c.u)^2 - 1.5 u.u
-        const V2 pa = fma2(bc(3.0f), cu, q), pb = fma2(bc(-3.0f), cu, q);
-        const V2 wr = rho * bc(w), wrp = rp * bc(w);
-        feqd[a] = fma2(wr, pa, wrp);
-        feqd[b] = fma2(wr, pb, wrp);
-        const V2 t = ca * bc(3.0f);
-        const V2 m = fma2(cu * bc(3.0f), t, ua3neg);  // 9 (c.u)(c.a) - 3 u.a
-        F[a] = wr * (m + t);
-        F[b] = wr * (m - t);
-        if (TH) {
-            const V2 wT = T * bc(w), wTd = Td * bc(w);
-            geqd[a] = fma2(wT, pa, wTd);
-            geqd[b] = fma2(wT, pb, wTd);
-        }
-    }
-};
+using namespace pairmath;
 
 __device__ __forceinline__ int slot5(int r) {
     const int s = r % 5;

@@ -5,7 +5,7 @@
 // neighbour it streams to.  Walls: half-way bounce-back for f and
 // anti-bounce-back through the plate temperature for g,
 // g_inv(a)(x) = -g*_a(x) + 2 w_a T_wall.
-#include "lb_internal.cuh"
+#include "lb_pair.cuh"
 
 namespace lbgb {
 
@@ -68,12 +68,111 @@ __global__ void __launch_bounds__(256) k_st(const StepArgs<R> A) {
     }
 }
 
+// The same step for two adjacent cells per thread with packed FP32 pair
+// arithmetic: populations are loaded as pairs (8-byte FP32, 4-byte half2 /
+// bfloat162), the collision runs on f32x2 pairs, populations with c_x = 0
+// are stored as pairs and the others per cell (their neighbour is shifted by
+// one column).
+template <typename S, bool TH>
+__global__ void __launch_bounds__(256) k_st_pair(const StepArgs<float> A) {
+    using namespace pairmath;
+    const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = blockIdx.y;
+    if (x >= A.nx) return;
+    const bool two = x + 1 < A.nx;
+    const S* fin = static_cast<const S*>(A.fin);
+    S* fout = static_cast<S*>(A.fout);
+    const S* gin = static_cast<const S*>(A.gin);
+    S* gout = static_cast<S*>(A.gout);
+    const long long c = (long long)y * A.pitch + x;
+    auto ld = [&](const S* p) { return two ? PairIO<S>::ld(p) : bc(Store<S>::ld(p)); };
+    V2 d[Q], e[Q];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) d[a] = ld(fin + a * A.plane + c);
+    if (TH) {
+#pragma unroll
+        for (int a = 0; a < Q; ++a) e[a] = ld(gin + a * A.plane + c);
+    }
+    const float ro = A.roff[y], to = TH ? A.toff[y] : 0.0f;
+    PairCell<TH> m;
+    m.build(d, e, A, ro, to);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const V2 post = fma2(bc(A.om), m.feqd[a] - d[a], fma2(bc(A.cf), m.F[a], d[a]));
+        V2 gpost = bc(0.0f);
+        if (TH) gpost = fma2(bc(A.omg), m.geqd[a] - e[a], e[a]);
+        const float w = wgt<float>(a);
+        int ty = y + cy(a);
+        bool outy = false;
+        float dTw = 0.0f;
+        if (ty < 0 || ty >= A.ny) {
+            if (A.bcy == LB_BC_PERIODIC) {
+                ty = ty < 0 ? ty + A.ny : ty - A.ny;
+            } else {
+                outy = true;
+                dTw = ty < 0 ? A.dTb : A.dTt;
+            }
+        }
+        if (cx(a) == 0) {
+            // both cells stream to the same row: one pair store
+            long long o;
+            V2 fv, gv;
+            if (outy) {
+                o = inv(a) * A.plane + c;
+                fv = post;
+                gv = bc(2.0f * w * (dTw - to)) - gpost;
+            } else {
+                o = a * A.plane + (long long)ty * A.pitch + x;
+                fv = post + bc(w * (ro - A.roff[ty]));
+                if (TH) gv = gpost + bc(w * (to - A.toff[ty]));
+            }
+            if (two) {
+                PairIO<S>::st(fout + o, fv);
+                if (TH) PairIO<S>::st(gout + o, gv);
+            } else {
+                Store<S>::st(fout + o, fv.v.x);
+                if (TH) Store<S>::st(gout + o, gv.v.x);
+            }
+        } else {
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                if (i == 1 && !two) break;
+                const float pv = i ? post.v.y : post.v.x;
+                const float gp = i ? gpost.v.y : gpost.v.x;
+                int tx = x + i + cx(a);
+                bool out = outy;
+                if (tx < 0 || tx >= A.nx) {
+                    if (A.bcx == LB_BC_PERIODIC) tx = tx < 0 ? tx + A.nx : tx - A.nx;
+                    else out = true;
+                }
+                if (out) {
+                    const long long o = inv(a) * A.plane + c + i;
+                    Store<S>::st(fout + o, pv);
+                    if (TH) Store<S>::st(gout + o, -gp + 2.0f * w * (dTw - to));
+                } else {
+                    const long long o = a * A.plane + (long long)ty * A.pitch + tx;
+                    Store<S>::st(fout + o, pv + w * (ro - A.roff[ty]));
+                    if (TH) Store<S>::st(gout + o, gp + w * (to - A.toff[ty]));
+                }
+            }
+        }
+    }
+}
+
 template <typename R, typename S, bool TH>
 static cudaError_t run_st(const void* vargs, cudaStream_t s) {
     const StepArgs<R>& A = *static_cast<const StepArgs<R>*>(vargs);
-    int bx = A.nx >= 256 ? 256 : ((A.nx + 31) / 32) * 32;
-    dim3 grid((A.nx + bx - 1) / bx, A.ny);
-    k_st<R, S, TH><<<grid, bx, 0, s>>>(A);
+    if constexpr (sizeof(R) == 4) {
+        // packed pairs: one thread per two cells
+        const int half = (A.nx + 1) / 2;
+        int bx = half >= 256 ? 256 : ((half + 31) / 32) * 32;
+        dim3 grid((half + bx - 1) / bx, A.ny);
+        k_st_pair<S, TH><<<grid, bx, 0, s>>>(A);
+    } else {
+        int bx = A.nx >= 256 ? 256 : ((A.nx + 31) / 32) * 32;
+        dim3 grid((A.nx + bx - 1) / bx, A.ny);
+        k_st<R, S, TH><<<grid, bx, 0, s>>>(A);
+    }
     count_launch();
     return cudaGetLastError();
 }

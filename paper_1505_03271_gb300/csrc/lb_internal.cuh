@@ -179,6 +179,21 @@ enum class Prec { F64, F32, F16, BF16 };
 
 cudaError_t launch_st(Prec p, bool thermal, const void* args, cudaStream_t s);
 cudaError_t launch_fv(Prec p, bool thermal, const void* args, cudaStream_t s);
+// One request of a batched FV launch: its step parameters, both buffers
+// of each population set, the parity of its current state at step 0 of the
+// launch sequence and how many steps it still has to take.
+template <typename R>
+struct BatchReq {
+    StepArgs<R> args;
+    void* f[2];
+    void* g[2];
+    int parity;
+    int remaining;
+};
+// tiles[b] = (request, tile x, tile y, 0); CTAs beyond *ntiles exit
+cudaError_t launch_fv_batched(Prec p, bool thermal, const void* reqs, const int4* tiles, const int* ntiles,
+                              int capacity, int k, cudaStream_t s);
+void tile_shape(Prec p, bool thermal, int* tx, int* ty);
 // y-marching FV kernel: strips of march_width() output columns, `chunk` rows per CTA
 cudaError_t launch_fv_march(Prec p, bool thermal, const void* args, int chunk, cudaStream_t s);
 int march_width(Prec p, bool thermal);

@@ -109,6 +109,30 @@ def test_st_step_f64(lbgpu, oracle, case):
         assert np.abs(ggg - ggr).max() < 1e-14
 
 
+@pytest.mark.parametrize("case", ST_CASES, ids=lambda c: "x".join(map(str, c.values())))
+def test_st_step_f32_pairs(lbgpu, oracle, case):
+    """The FP32 ST path (two cells per thread, packed f32x2 arithmetic)
+    element by element against the oracle, odd widths included."""
+    nx, ny = case["nx"], case["ny"]
+    th = case.get("thermal", False)
+    kw = dict(tau=0.3, dt=1.0, ax=2e-4, ay=-1e-4)
+    if th:
+        kw.update(tau_g=0.25, beta=1e-2, grav=1.0, T0=1.0, T_bot=1.3, T_top=0.8)
+    g, r = pair(lbgpu, oracle, store=lbgpu.LB_STORE_F32, **case, **kw)
+    g.set_pops(inputs.random_populations(nx, ny, seed=nx + ny, amp=0.2),
+               inputs.random_populations(nx, ny, seed=7, amp=0.2) if th else None)
+    f, gg = g.get_pops()
+    r.set_pops(f, gg)
+    g.step_st(5)
+    r.step_st(5)
+    fg, ggg = g.get_pops()
+    fr, ggr = r.get_pops()
+    wts = oracle.lattice()[2][:, None, None]
+    assert np.abs(fg - fr).max() <= 2e-6 * np.abs(f - wts).max()
+    if th:
+        assert np.abs(ggg - ggr).max() <= 2e-6 * np.abs(gg - wts).max()
+
+
 FV_CASES = [
     dict(nx=70, ny=37),
     dict(nx=45, ny=33, sy=1, stretch_y=1.5),

@@ -1,0 +1,126 @@
+"""Continuous-batching server: each request's result is the same alone and in
+a mix (bit for bit: the batched kernel steps every tile with the same code
+whatever else is in the table), it matches the single-grid tile path within
+the storage precision, admission waits for memory, failures stay local, and a
+served request matches the FP64 oracle."""
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+RB = dict(tau=0.05, tau_g=0.05, beta=2e-4, grav=1.0, T0=1.0, T_bot=1.5, T_top=0.5)
+
+
+def _requests():
+    # different sizes, Rayleigh numbers (through beta) and step counts
+    return [
+        dict(rid=1, nsteps=37, nx=40, ny=40, sy=1, stretch_y=2.0, bcy=1, dt=0.1, amp=1e-2, seed=1, **RB),
+        dict(rid=2, nsteps=58, nx=96, ny=64, sy=1, stretch_y=2.0, bcy=1, dt=0.1, amp=1e-2, seed=2,
+             **{**RB, "beta": 5e-4}),
+        dict(rid=3, nsteps=21, nx=64, ny=64, bcy=1, dt=0.2, amp=1e-2, seed=3, **{**RB, "tau": 0.1, "tau_g": 0.1}),
+    ]
+
+
+def _alone_on_grid(lb, req, store):
+    """The same request through an ordinary grid with the tile schedule."""
+    kw = dict(req)
+    rid, nsteps = kw.pop("rid"), kw.pop("nsteps")
+    grid_keys = ("nx", "ny", "lx", "ly", "sx", "sy", "stretch_x", "stretch_y", "bcx", "bcy")
+    gk = {k: kw.pop(k) for k in list(kw) if k in grid_keys}
+    g = lb.Grid(thermal=True, store=store, **gk)
+    g.init(kind=lb.LB_INIT_RB, **kw)
+    g.set_fv_schedule(lb.LB_FV_TILE)
+    g.step_fv(nsteps)
+    return g.nusselt(), g.conservation()[0]
+
+
+def _drain(server):
+    out = {}
+    while True:
+        active, pending = server.pump()
+        for r in server.results():
+            out[r["id"]] = r
+        if active == 0 and pending == 0:
+            for r in server.results():
+                out[r["id"]] = r
+            return out
+
+
+@pytest.mark.parametrize("store", ["f32", "f16dev"])
+def test_alone_equals_mix(lbgpu, store):
+    lb = lbgpu
+    reqs = _requests()
+    mix = lb.Server(store=store, thermal=True, steps_per_launch=8)
+    for r in reqs:
+        mix.submit(**r)
+    got = _drain(mix)
+    assert set(got) == {1, 2, 3}
+    tol = 1e-7 if store == "f32" else 1e-5  # plate Nu amplifies rounding by ~H * 20
+    for r in reqs:
+        res = got[r["rid"]]
+        assert res["status"] == lb.LB_OK and res["steps"] == r["nsteps"]
+        mixed = (res["nu_vol"], res["nu_bot"], res["nu_top"], res["mass"])
+        # alone through its own server: identical bits
+        one = lb.Server(store=store, thermal=True, steps_per_launch=8)
+        one.submit(**r)
+        alone = _drain(one)[r["rid"]]
+        assert (alone["nu_vol"], alone["nu_bot"], alone["nu_top"], alone["mass"]) == mixed
+        # the ordinary grid path (separately compiled): within storage precision
+        nu, mass = _alone_on_grid(lb, r, store)
+        for a, b in zip(mixed, nu + (mass,)):
+            assert abs(a - b) <= tol * abs(b)
+        assert res["t_submit"] <= res["t_admit"] <= res["t_done"]
+
+
+def test_admission_waits_for_memory(lbgpu):
+    """A budget that holds one request at a time: they run one after another."""
+    lb = lbgpu
+    reqs = _requests()
+    s = lb.Server(store="f32", thermal=True, hbm_budget=1_258_291, steps_per_launch=8)
+    for r in reqs[:2]:
+        s.submit(**r)
+    got = _drain(s)
+    a, b = got[1], got[2]
+    assert a["status"] == b["status"] == lb.LB_OK
+    assert b["t_admit"] >= a["t_done"] - 1e-6
+    with pytest.raises(lb.LBError) as e:
+        s.submit(rid=9, nsteps=1, nx=2048, ny=2048, **RB)
+    assert e.value.status == lb.LB_ERR_ARG
+
+
+def test_unstable_request_fails_alone(lbgpu):
+    """A request far beyond the stability limit ends with LB_ERR_UNSTABLE; the
+    request batched with it is unaffected."""
+    lb = lbgpu
+    good = _requests()[0]
+    s = lb.Server(store="f32", thermal=True, steps_per_launch=8)
+    s.submit(**good)
+    bad = dict(good, rid=7, dt=40.0, nsteps=200, amp=0.5)
+    s.submit(**bad)
+    got = _drain(s)
+    assert got[7]["status"] == lb.LB_ERR_UNSTABLE
+    assert got[1]["status"] == lb.LB_OK
+    one = lb.Server(store="f32", thermal=True, steps_per_launch=8)
+    one.submit(**good)
+    alone = _drain(one)[1]
+    assert (got[1]["nu_vol"], got[1]["nu_bot"], got[1]["nu_top"]) == (alone["nu_vol"], alone["nu_bot"],
+                                                                       alone["nu_top"])
+
+
+def test_served_request_matches_oracle(lbgpu, oracle):
+    """FP64 server: the batched kernel's Nusselt numbers equal the oracle's."""
+    lb = lbgpu
+    oracle.set_threads(os.cpu_count() or 1)
+    r = _requests()[1]
+    s = lb.Server(store="f64", thermal=True, steps_per_launch=6)
+    s.submit(**r)
+    res = _drain(s)[2]
+    ref = oracle.RefGrid(r["nx"], r["ny"], sy=r["sy"], stretch_y=r["stretch_y"], bcy=r["bcy"], thermal=True)
+    ref.set_params(tau=r["tau"], dt=r["dt"], tau_g=r["tau_g"], beta=r["beta"], grav=r["grav"], T0=r["T0"],
+                   T_bot=r["T_bot"], T_top=r["T_top"])
+    ref.init_preset(oracle.INIT_RB, amp=r["amp"], seed=r["seed"])
+    ref.step_fv(r["nsteps"])
+    for a, b in zip((res["nu_vol"], res["nu_bot"], res["nu_top"]), ref.nusselt()):
+        assert abs(a - b) <= 1e-10 * max(1.0, abs(b))
