@@ -187,6 +187,23 @@ def _fv_big(cfg, n):
                         dict(tau=0.3, dt=0.5), dict(kind=LB_INIT_TGV, u0=0.01), 10, "fv")
 
 
+def serving_measure(lb, torch, count=120, rate=25.0):
+    """Scaled config-5 stream through the batching server and one at a time."""
+    from paper_1505_03271_gb300 import serving
+    reqs = serving.make_requests(count, rate)
+    srv = serving.run_server(lb, reqs)
+    seq = serving.run_sequential(lb, torch, reqs)
+    # the same request must give the same Nusselt numbers both ways
+    diffs = [abs(srv["results"][r.rid]["nu_vol"] - seq["results"][r.rid]["nu_vol"])
+             for r in reqs if srv["results"][r.rid]["status"] == 0 and seq["results"][r.rid]["status"] == 0]
+    keep = ("requests", "ok", "unstable", "cell_updates", "wall_s", "mlups", "tts_p50_s", "tts_p99_s")
+    return {"workload": "RB FV requests, N in {64..1024}^2 tanh plates, Ra log-uniform 1e4-1e8, Pr=1, "
+                        "steps uniform 50-1000 (config 5 steps / 20), FP16 deviation storage, "
+                        "Poisson arrivals %.0f/s, %d requests" % (rate, count),
+            "server": {k: srv[k] for k in keep}, "sequential": {k: seq[k] for k in keep},
+            "max_abs_nu_vol_diff_server_vs_sequential": max(diffs) if diffs else None}
+
+
 def e2e_measure(lb, torch, w, stream, reps=3, inner=1000):
     """Through the public API with host buffers: per iteration, upload rho, ux,
     uy from pinned host memory (lb_init FIELDS), advance `inner` FV steps,
@@ -318,6 +335,9 @@ def main():
     ap.add_argument("--case", default="channel",
                     help="workload to time: channel (headline), st8192, st4096, st4096_f16dev, "
                          "fv4096, fv2048, rb1024")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving stream")
+    ap.add_argument("--serving-requests", type=int, default=160)
+    ap.add_argument("--serving-rate", type=float, default=60.0, help="Poisson arrivals per second")
     ap.add_argument("--fv-schedule", default="tune",
                     help="tune (autotuner), tile, march[:rows per CTA] or pair[:rows per CTA]")
     args = ap.parse_args()
@@ -378,6 +398,8 @@ def main():
     if not args.no_extra and args.case == "channel":
         line["e2e"] = e2e_measure(lb, torch, w, stream)
         line["extra"] = extra_lines(lb, torch, cfg, stream, peak, peak_kind, flush)
+        if not args.no_serving:
+            line["extra"]["serving"] = serving_measure(lb, torch, args.serving_requests, args.serving_rate)
     if rank == 0 and world == 1 and not args.no_cpu and args.case == "channel":
         import oracle as O
         O.build()

@@ -75,3 +75,20 @@ def test_workload_rules():
     assert t.steps == 1000 and abs(t.params["tau"] - 0.3) < 1e-15
     assert cfg.bytes_per_cell(1, False) == 72 and cfg.bytes_per_cell(2, True) == 72
     assert cfg.bytes_per_cell(0, True) == 288
+
+
+def test_serving_request_recipe():
+    """The serving stream: seeded, sizes from the set, Ra in [1e4, 1e8],
+    Poisson arrivals with the requested mean rate."""
+    from paper_1505_03271_gb300 import serving
+    a = serving.make_requests(400, 20.0)
+    b = serving.make_requests(400, 20.0)
+    assert [(r.n, r.Ra, r.nsteps, r.arrival) for r in a] == [(r.n, r.Ra, r.nsteps, r.arrival) for r in b]
+    assert {r.n for r in a} <= set(serving.SIZES)
+    assert all(1e4 <= r.Ra <= 1e8 and 50 <= r.nsteps <= 1000 for r in a)
+    gaps = np.diff([0.0] + [r.arrival for r in a])
+    assert abs(gaps.mean() * 20.0 - 1.0) < 0.15
+    for r in a[:20]:
+        assert r.params["dt"] <= 0.9 * min(np.diff(__import__("paper_1505_03271_gb300.configs",
+                                                               fromlist=["x"]).faces(r.n, r.n, 1, 2.0)).min(),
+                                           8 * min(r.params["tau"], r.params["tau_g"])) + 1e-15
