@@ -113,8 +113,8 @@ def make_grid(lb, w, stream, tune=True):
     g = lb.Grid(store=store, stream=stream, **grid)
     g.init(**w.params, **w.init)
     if w.scheme == "fv":
-        if FV_SCHEDULE == "tile":
-            g.set_fv_schedule(lb.LB_FV_TILE)
+        if FV_SCHEDULE.startswith("tile"):
+            g.set_fv_schedule(lb.LB_FV_TILE, int(FV_SCHEDULE.split(":")[1]) if ":" in FV_SCHEDULE else 0)
         elif FV_SCHEDULE.startswith("march") or FV_SCHEDULE.startswith("pair"):
             kern = lb.LB_FV_MARCH if FV_SCHEDULE.startswith("march") else lb.LB_FV_PAIR
             g.set_fv_schedule(kern, int(FV_SCHEDULE.split(":")[1]) if ":" in FV_SCHEDULE else 0)
@@ -128,7 +128,7 @@ def schedule_name(lb, g, scheme):
         return "st push, one thread per cell"
     k, c = g.fv_schedule()
     if k == lb.LB_FV_TILE:
-        return "fv tile 32x16 (halo 4)"
+        return "fv tile %s (halo 4)" % {0: "32x16", 16: "16x16", 8: "16x8"}[c]
     return ("fv pair-march (f32x2)" if k == lb.LB_FV_PAIR else "fv march") + ", %d rows per CTA" % c
 
 

@@ -303,18 +303,31 @@ static cudaError_t run_fv(const void* vargs, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_fv(Prec p, bool th, const void* args, cudaStream_t s) {
+// Tile shape variants: 0 = 32 x 16 (16 x 16 for FP64 thermal), 16 = 16 x 16,
+// 8 = 16 x 8.  Smaller tiles recompute more halo but give more, shorter
+// CTAs, which is what small grids (latency-bound) want.
+template <typename R, typename S, bool TH>
+static cudaError_t run_fv_shape(const void* args, int shape, cudaStream_t s) {
+    if (shape == 8) return run_fv<R, S, TH, 16, 8>(args, s);
+    if (shape == 16) return run_fv<R, S, TH, 16, 16>(args, s);
+    if constexpr (sizeof(R) == 8 && TH) return run_fv<R, S, TH, 16, 16>(args, s);
+    else return run_fv<R, S, TH, 32, 16>(args, s);
+}
+
+cudaError_t launch_fv(Prec p, bool th, const void* args, int shape, cudaStream_t s) {
     switch (p) {
         case Prec::F64:
-            return th ? run_fv<double, double, true, 16, 16>(args, s)
-                      : run_fv<double, double, false, 32, 16>(args, s);
+            return th ? run_fv_shape<double, double, true>(args, shape, s)
+                      : run_fv_shape<double, double, false>(args, shape, s);
         case Prec::F32:
-            return th ? run_fv<float, float, true, 32, 16>(args, s) : run_fv<float, float, false, 32, 16>(args, s);
+            return th ? run_fv_shape<float, float, true>(args, shape, s)
+                      : run_fv_shape<float, float, false>(args, shape, s);
         case Prec::F16:
-            return th ? run_fv<float, __half, true, 32, 16>(args, s) : run_fv<float, __half, false, 32, 16>(args, s);
+            return th ? run_fv_shape<float, __half, true>(args, shape, s)
+                      : run_fv_shape<float, __half, false>(args, shape, s);
         case Prec::BF16:
-            return th ? run_fv<float, __nv_bfloat16, true, 32, 16>(args, s)
-                      : run_fv<float, __nv_bfloat16, false, 32, 16>(args, s);
+            return th ? run_fv_shape<float, __nv_bfloat16, true>(args, shape, s)
+                      : run_fv_shape<float, __nv_bfloat16, false>(args, shape, s);
     }
     return cudaErrorInvalidValue;
 }

@@ -37,20 +37,35 @@ struct XPair {
     V2 inv;
 };
 
-// y metric of one row, duplicated into pairs.
+// One row of the per-row table (20 floats, 80 bytes): QUICK weights of the
+// row's south and north faces for both upwind directions, 1/dy, the base
+// state offsets and the base state's y flux divergences.
 struct YPair {
     V2 ps[3], pn[3], ms[3], mn[3], inv;
+    float ro, to, dref[4];
 };
 
-__device__ __forceinline__ void load_ypair(const AxisMetric<float>& m, int g, YPair& Y) {
-#pragma unroll
-    for (int r = 0; r < 3; ++r) {
-        Y.ps[r] = bc(m.wp(r, g));
-        Y.pn[r] = bc(m.wp(r, g + 1));
-        Y.ms[r] = bc(m.wm(r, g));
-        Y.mn[r] = bc(m.wm(r, g + 1));
+__device__ __forceinline__ void load_row(const float* tab, int g, YPair& Y) {
+    const float4* p = reinterpret_cast<const float4*>(tab + 20 * g);
+    const float4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2), d = __ldg(p + 3), e = __ldg(p + 4);
+    Y.ps[0] = bc(a.x); Y.ps[1] = bc(a.y); Y.ps[2] = bc(a.z);
+    Y.pn[0] = bc(a.w); Y.pn[1] = bc(b.x); Y.pn[2] = bc(b.y);
+    Y.ms[0] = bc(b.z); Y.ms[1] = bc(b.w); Y.ms[2] = bc(c.x);
+    Y.mn[0] = bc(c.y); Y.mn[1] = bc(c.z); Y.mn[2] = bc(c.w);
+    Y.inv = bc(d.x);
+    Y.ro = d.y;
+    Y.to = d.z;
+    Y.dref[0] = d.w; Y.dref[1] = e.x; Y.dref[2] = e.y; Y.dref[3] = e.z;
+}
+
+// y flux divergence of the base state for population a (row data).
+template <int a>
+__device__ __forceinline__ float row_ref_flux(const YPair& Y, bool thermal) {
+    if constexpr (cy(a) == 0) {
+        return 0.0f;
+    } else {
+        return float(cy(a)) * wgt<float>(a) * Y.dref[(thermal ? 2 : 0) + (cy(a) > 0 ? 0 : 1)];
     }
-    Y.inv = bc(m.invd(g));
 }
 
 // Flux divergence of ring plane p (population a) for the thread's two
@@ -97,8 +112,8 @@ __device__ __forceinline__ V2 advect_pair(const V2* ring, const int* sl, int p, 
 template <bool TH, int NQ, int NT, int a>
 __device__ __forceinline__ void advect_all(const V2* ring, const int* sl, int k, const XPair& X, const YPair& Y,
                                            const StepArgs<float>& A, int gy, V2* out) {
-    out[a] = advect_pair<NQ, NT, a>(ring, sl, a, k, X, Y) + bc(ref_flux<float, a>(A, gy, false));
-    if constexpr (TH) out[Q + a] = advect_pair<NQ, NT, a>(ring, sl, Q + a, k, X, Y) + bc(ref_flux<float, a>(A, gy, true));
+    out[a] = advect_pair<NQ, NT, a>(ring, sl, a, k, X, Y) + bc(row_ref_flux<a>(Y, false));
+    if constexpr (TH) out[Q + a] = advect_pair<NQ, NT, a>(ring, sl, Q + a, k, X, Y) + bc(row_ref_flux<a>(Y, true));
     if constexpr (a + 1 < Q) advect_all<TH, NQ, NT, a + 1>(ring, sl, k, X, Y, A, gy, out);
 }
 
@@ -177,53 +192,69 @@ __global__ void __launch_bounds__(NT) k_fv_pair(const StepArgs<float> A, const i
         }
     };
 
-    // one row iteration; (bd, be) holds row t on entry and row t + 2 on exit
-    auto iteration = [&](const int t, V2* bd, V2* be) {
+    // register buffers: (b0, e0) hold row t, (b1, e1) row t + 1 (in flight)
+    V2 b0[Q], e0[Q], b1[Q], e1[Q];
+    prefetch(ys - 4, b0, e0);
+    prefetch(ys - 3, b1, e1);
+    int s0 = slot5(ys - 4);  // slot of row t
+    for (int t = ys - 4; t < ye + 4; ++t) {
+        // m[i] = slot of row t - 4 + i (rows t - 4 .. t; m[4] = s0), since
+        // rows five apart share a slot
+        int m[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) {
+            const int v = s0 + 1 + i;
+            m[i] = v >= 5 ? v - 5 : v;
+        }
         // ---- stage A on row t ----
         {
             int gy;
-            const int s = slot5(t);
-            if (fluid_row(t, gy)) {
-                V2 d[Q], e[Q];
+            const int s = s0;
+            V2 d[Q], e[Q];
 #pragma unroll
-                for (int a = 0; a < Q; ++a) {
-                    d[a] = bd[a];
-                    if constexpr (TH) e[a] = be[a];
+            for (int a = 0; a < Q; ++a) {
+                d[a] = b0[a];
+                b0[a] = b1[a];
+                if constexpr (TH) {
+                    e[a] = e0[a];
+                    e0[a] = e1[a];
                 }
-                prefetch(t + 2, bd, be);
-                PairCell<TH> m;
-                m.build(d, e, A, A.roff[gy], TH ? A.toff[gy] : 0.0f);
+            }
+            prefetch(t + 2, b1, e1);
+            if (fluid_row(t, gy)) {
+                const float4 o = __ldg(reinterpret_cast<const float4*>(A.rowtab + 20 * gy) + 3);
+                PairCell<TH> c;
+                c.build(d, e, A, o.y, TH ? o.z : 0.0f);
 #pragma unroll
                 for (int a = 0; a < Q; ++a) {
-                    const V2 neq = m.feqd[a] - d[a];
-                    sH[(s * NQ + a) * NT + k] = fma2(bc(A.omh), neq, fma2(bc(A.hf), m.F[a], d[a]));
-                    sP[(s * NQ + a) * NT + k] = fma2(bc(A.om), neq, fma2(bc(A.cf), m.F[a], d[a]));
+                    const V2 neq = c.feqd[a] - d[a];
+                    sH[(s * NQ + a) * NT + k] = fma2(bc(A.omh), neq, fma2(bc(A.hf), c.F[a], d[a]));
+                    sP[(s * NQ + a) * NT + k] = fma2(bc(A.om), neq, fma2(bc(A.cf), c.F[a], d[a]));
                     if constexpr (TH) {
-                        const V2 neqg = m.geqd[a] - e[a];
+                        const V2 neqg = c.geqd[a] - e[a];
                         sH[(s * NQ + Q + a) * NT + k] = fma2(bc(A.omgh), neqg, e[a]);
                         sP[(s * NQ + Q + a) * NT + k] = fma2(bc(A.omg), neqg, e[a]);
                     }
                 }
-            } else {
-                prefetch(t + 2, bd, be);
-                if (wally && (t == A.ny || t == A.ny + 1)) ghost_row<TH, NQ, NT>(sH, s, slot5(2 * A.ny - 1 - t), k);
+            } else if (wally && (t == A.ny || t == A.ny + 1)) {
+                ghost_row<TH, NQ, NT>(sH, s, slot5(2 * A.ny - 1 - t), k);
             }
             if (wally && t == 1 && ys == 0) {
                 ghost_row<TH, NQ, NT>(sH, slot5(-1), slot5(0), k);
                 ghost_row<TH, NQ, NT>(sH, slot5(-2), slot5(1), k);
             }
         }
-        // ---- stage B on row t - 2 ----
+        // ---- stage B on row t - 2: rows t-4 .. t are slots m[0] .. m[4] ----
         {
             const int r = t - 2;
             int gy;
             if (r >= ys - 2 && r < ye + 2) {
-                const int s = slot5(r);
+                const int s = m[2];
                 if (fluid_row(r, gy)) {
                     if (colB) {
                         YPair Y;
-                        load_ypair(A.my, gy, Y);
-                        const int sl[5] = {slot5(r - 2), slot5(r - 1), s, slot5(r + 1), slot5(r + 2)};
+                        load_row(A.rowtab, gy, Y);
+                        const int sl[5] = {m[0], m[1], m[2], m[3], m[4]};
                         V2 adv[NQ];
                         advect_all<TH, NQ, NT, 0>(sH, sl, k, X, Y, A, gy, adv);
                         V2 fs[Q], es[Q];
@@ -238,14 +269,14 @@ __global__ void __launch_bounds__(NT) k_fv_pair(const StepArgs<float> A, const i
                                 sP[(s * NQ + Q + a) * NT + k] = fma2(bc(-A.hf), adv[Q + a], gc);
                             }
                         }
-                        PairCell<TH> m;
-                        m.build(fs, es, A, A.roff[gy], TH ? A.toff[gy] : 0.0f);
+                        PairCell<TH> c;
+                        c.build(fs, es, A, Y.ro, TH ? Y.to : 0.0f);
 #pragma unroll
                         for (int a = 0; a < Q; ++a) {
                             sS[(s * NQ + a) * NT + k] =
-                                fma2(bc(A.omh), m.feqd[a] - fs[a], fma2(bc(A.hf), m.F[a], fs[a]));
+                                fma2(bc(A.omh), c.feqd[a] - fs[a], fma2(bc(A.hf), c.F[a], fs[a]));
                             if constexpr (TH)
-                                sS[(s * NQ + Q + a) * NT + k] = fma2(bc(A.omgh), m.geqd[a] - es[a], es[a]);
+                                sS[(s * NQ + Q + a) * NT + k] = fma2(bc(A.omgh), c.geqd[a] - es[a], es[a]);
                         }
                     }
                 } else if (wally && (r == A.ny || r == A.ny + 1)) {
@@ -257,14 +288,14 @@ __global__ void __launch_bounds__(NT) k_fv_pair(const StepArgs<float> A, const i
                 }
             }
         }
-        // ---- stage C on row t - 4 ----
+        // ---- stage C on row t - 4: rows t-6 .. t-2 are slots m[3], m[4], m[0], m[1], m[2] ----
         {
             const int r = t - 4;
             if (r >= ys && r < ye && colC) {
-                const int s = slot5(r);
+                const int s = m[0];
                 YPair Y;
-                load_ypair(A.my, r, Y);
-                const int sl[5] = {slot5(r - 2), slot5(r - 1), s, slot5(r + 1), slot5(r + 2)};
+                load_row(A.rowtab, r, Y);
+                const int sl[5] = {m[3], m[4], m[0], m[1], m[2]};
                 V2 adv[NQ];
                 advect_all<TH, NQ, NT, 0>(sS, sl, k, X, Y, A, r, adv);
                 const long long row = (long long)r * A.pitch;
@@ -279,15 +310,7 @@ __global__ void __launch_bounds__(NT) k_fv_pair(const StepArgs<float> A, const i
             }
         }
         __syncthreads();
-    };
-
-    // two register buffers in turn: even rows in (d0, e0), odd rows in (d1, e1)
-    V2 d0[Q], e0[Q], d1[Q], e1[Q];
-    prefetch(ys - 4, d0, e0);
-    prefetch(ys - 3, d1, e1);
-    for (int t = ys - 4; t < ye + 4; t += 2) {
-        iteration(t, d0, e0);
-        if (t + 1 < ye + 4) iteration(t + 1, d1, e1);
+        s0 = m[0];  // slot of row t + 1 (= slot of row t - 4)
     }
 }
 

@@ -48,7 +48,8 @@ namespace {
 
 void release(lb_grid* G) {
     void* ptrs[] = {G->f[0], G->f[1], G->g[0], G->g[1], G->mx, G->my, G->dxv, G->dyv, G->xc,
-                    G->yc, G->toff, G->toff_r, G->roff, G->roff_r, G->dref_r, G->fields, G->partial, G->red};
+                    G->yc, G->toff, G->toff_r, G->roff, G->roff_r, G->dref_r, G->rowtab, G->fields, G->partial,
+                    G->red};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -131,7 +132,7 @@ cudaError_t launch_fv_step(lb_grid* G) {
     const int k = resolved_kernel(G);
     if (k == LB_FV_PAIR) return launch_fv_pair(G->prec, th, &A, resolved_chunk(G), G->stream);
     if (k == LB_FV_MARCH) return launch_fv_march(G->prec, th, &A, resolved_chunk(G), G->stream);
-    return launch_fv(G->prec, th, &A, G->stream);
+    return launch_fv(G->prec, th, &A, G->fv_kernel == LB_FV_TILE ? G->fv_chunk : 0, G->stream);
 }
 
 lb_status upload(void** dst, const std::vector<double>& v, bool as_float) {
@@ -229,6 +230,7 @@ lb_status lb_create_grid(const lb_grid_desc* d, lb_grid** out) {
     alloc((void**)&G->roff, sizeof(double) * G->ny);
     alloc(&G->roff_r, (as_float ? sizeof(float) : sizeof(double)) * G->ny);
     alloc(&G->dref_r, (as_float ? sizeof(float) : sizeof(double)) * 4 * G->ny);
+    alloc((void**)&G->rowtab, sizeof(float) * 20 * G->ny);
     alloc((void**)&G->partial, sizeof(double) * kRed * G->nred);
     alloc((void**)&G->red, sizeof(double) * kRed);
     if (st == LB_OK) st = upload(&G->mx, G->ax.metric(), as_float);
@@ -327,6 +329,23 @@ lb_status lb_init(lb_grid* G, const lb_params* p, const lb_init_desc* in) {
             CK(cudaMemcpy(G->toff_r, tf.data(), sizeof(float) * G->ny, cudaMemcpyHostToDevice));
             CK(cudaMemcpy(G->roff_r, rf.data(), sizeof(float) * G->ny, cudaMemcpyHostToDevice));
             CK(cudaMemcpy(G->dref_r, df.data(), sizeof(float) * df.size(), cudaMemcpyHostToDevice));
+            // per-row table of the paired kernel: one 80-byte entry per row
+            const std::vector<double> my = G->ay.metric();
+            std::vector<float> tab(20 * (size_t)ny, 0.0f);
+            for (int j = 0; j < ny; ++j) {
+                float* e = &tab[20 * (size_t)j];
+                for (int q = 0; q < 3; ++q) {
+                    e[q] = (float)my[q * (ny + 1) + j];            // c > 0, south face j
+                    e[3 + q] = (float)my[q * (ny + 1) + j + 1];    // c > 0, north face j + 1
+                    e[6 + q] = (float)my[(3 + q) * (ny + 1) + j];  // c < 0, south
+                    e[9 + q] = (float)my[(3 + q) * (ny + 1) + j + 1];
+                }
+                e[12] = (float)my[6 * (ny + 1) + j];
+                e[13] = (float)ro[j];
+                e[14] = (float)to[j];
+                for (int q = 0; q < 4; ++q) e[15 + q] = (float)dref[q * ny + j];
+            }
+            CK(cudaMemcpy(G->rowtab, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice));
         }
     }
     InitArgs a{};
@@ -395,6 +414,8 @@ lb_status lb_set_fv_schedule(lb_grid* G, int kernel, int chunk) {
     if (!G) return fail(LB_ERR_ARG, "grid is NULL");
     if (kernel < LB_FV_AUTO || kernel > LB_FV_PAIR) return fail(LB_ERR_ARG, "unknown FV kernel %d", kernel);
     if (chunk < 0) return fail(LB_ERR_ARG, "chunk must be >= 0");
+    if (kernel == LB_FV_TILE && chunk != 0 && chunk != 8 && chunk != 16)
+        return fail(LB_ERR_ARG, "tile shape must be 0 (32 x 16), 16 (16 x 16) or 8 (16 x 8)");
     if (kernel == LB_FV_PAIR && !pair_ok(G))
         return fail(LB_ERR_ARG, "the paired FV kernel needs FP32/FP16/BF16 storage and a periodic x axis");
     G->fv_kernel = kernel;
@@ -405,7 +426,8 @@ lb_status lb_set_fv_schedule(lb_grid* G, int kernel, int chunk) {
 lb_status lb_get_fv_schedule(lb_grid* G, int* kernel, int* chunk) {
     if (!G) return fail(LB_ERR_ARG, "grid is NULL");
     if (kernel) *kernel = resolved_kernel(G);
-    if (chunk) *chunk = resolved_kernel(G) == LB_FV_TILE ? 0 : resolved_chunk(G);
+    if (chunk) *chunk = resolved_kernel(G) == LB_FV_TILE ? (G->fv_kernel == LB_FV_TILE ? G->fv_chunk : 0)
+                                                         : resolved_chunk(G);
     return LB_OK;
 }
 
@@ -425,7 +447,7 @@ lb_status lb_autotune_fv(lb_grid* G, int steps) {
     cudaMemcpyAsync(sf, G->f[cur0], bytes, cudaMemcpyDeviceToDevice, G->stream);
     if (sg) cudaMemcpyAsync(sg, G->g[cur0], bytes, cudaMemcpyDeviceToDevice, G->stream);
     const int k0 = G->fv_kernel, c0 = G->fv_chunk;
-    std::vector<std::pair<int, int>> cands = {{LB_FV_TILE, 0}};
+    std::vector<std::pair<int, int>> cands = {{LB_FV_TILE, 0}, {LB_FV_TILE, 16}, {LB_FV_TILE, 8}};
     for (int kern : {(int)LB_FV_MARCH, (int)LB_FV_PAIR}) {
         if (kern == LB_FV_PAIR && !pair_ok(G)) continue;
         G->fv_kernel = kern;

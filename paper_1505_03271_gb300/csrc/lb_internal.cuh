@@ -99,6 +99,7 @@ struct StepArgs {
     const R* toff;          // per row: T_r - T0 (thermal grids)
     const R* roff;          // per row: rho_r - 1
     const R* dref;          // [4][ny]: y flux divergence of rho_r (c_y > 0, < 0), of T_r (> 0, < 0)
+    const float* rowtab;    // [ny][20] per-row y data of the paired kernel (FP32 grids)
 };
 
 // Wrap or reject a global index on one axis: periodic axes wrap, wall axes
@@ -178,7 +179,7 @@ namespace lbgb {
 enum class Prec { F64, F32, F16, BF16 };
 
 cudaError_t launch_st(Prec p, bool thermal, const void* args, cudaStream_t s);
-cudaError_t launch_fv(Prec p, bool thermal, const void* args, cudaStream_t s);
+cudaError_t launch_fv(Prec p, bool thermal, const void* args, int shape, cudaStream_t s);
 // One request of a batched FV launch: its step parameters, both buffers
 // of each population set, the parity of its current state at step 0 of the
 // launch sequence and how many steps it still has to take.

@@ -146,7 +146,7 @@ FV_CASES = [
 ]
 
 
-SCHEDULES = [(1, 0), (2, 8), (2, 16), (2, 0)]  # tile; march with 8, 16 and auto rows per CTA
+SCHEDULES = [(1, 0), (1, 16), (1, 8), (2, 8), (2, 16), (2, 0)]  # tiles 32x16, 16x16, 16x8; march
 
 
 @pytest.mark.parametrize("sched", SCHEDULES, ids=lambda s: f"k{s[0]}c{s[1]}")
