@@ -113,7 +113,9 @@ def make_grid(lb, w, stream, tune=True):
     g = lb.Grid(store=store, stream=stream, **grid)
     g.init(**w.params, **w.init)
     if w.scheme == "fv":
-        if FV_SCHEDULE.startswith("tile"):
+        if FV_SCHEDULE.startswith("ptile"):
+            g.set_fv_schedule(lb.LB_FV_PTILE, int(FV_SCHEDULE.split(":")[1]) if ":" in FV_SCHEDULE else 0)
+        elif FV_SCHEDULE.startswith("tile"):
             g.set_fv_schedule(lb.LB_FV_TILE, int(FV_SCHEDULE.split(":")[1]) if ":" in FV_SCHEDULE else 0)
         elif FV_SCHEDULE.startswith("march") or FV_SCHEDULE.startswith("pair"):
             kern = lb.LB_FV_MARCH if FV_SCHEDULE.startswith("march") else lb.LB_FV_PAIR
@@ -129,6 +131,8 @@ def schedule_name(lb, g, scheme):
     k, c = g.fv_schedule()
     if k == lb.LB_FV_TILE:
         return "fv tile %s (halo 4)" % {0: "32x16", 16: "16x16", 8: "16x8"}[c]
+    if k == lb.LB_FV_PTILE:
+        return "fv pair-tile (f32x2) %s (halo 4)" % {0: "32x16", 16: "16x16"}[c]
     return ("fv pair-march (f32x2)" if k == lb.LB_FV_PAIR else "fv march") + ", %d rows per CTA" % c
 
 

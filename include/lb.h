@@ -139,13 +139,16 @@ lb_status lb_step_st(lb_grid* grid, int nsteps);
  *                `chunk` rows each, halo only in x;
  *   LB_FV_PAIR:  the marching strips with two columns per thread and packed
  *                FP32 pair arithmetic; FP32/FP16/BF16 storage and x-periodic
- *                grids only (LB_ERR_ARG otherwise).
+ *                grids only (LB_ERR_ARG otherwise);
+ *   LB_FV_PTILE: the tiles with two columns per thread-cell and packed FP32
+ *                pair arithmetic (same restrictions); chunk 0 = 32 x 16,
+ *                16 = 16 x 16.
  * LB_FV_AUTO picks by grid size.  For the marching kernels chunk = 0 lets
  * the library size the chunks to fill the GPU; for LB_FV_TILE chunk picks
  * the tile: 0 = 32 x 16, 16 = 16 x 16, 8 = 16 x 8 (smaller tiles recompute
  * more halo but suit small, latency-bound grids).  LB_ERR_ARG on an unknown
  * kernel or chunk. */
-typedef enum { LB_FV_AUTO = 0, LB_FV_TILE = 1, LB_FV_MARCH = 2, LB_FV_PAIR = 3 } lb_fv_kernel;
+typedef enum { LB_FV_AUTO = 0, LB_FV_TILE = 1, LB_FV_MARCH = 2, LB_FV_PAIR = 3, LB_FV_PTILE = 4 } lb_fv_kernel;
 lb_status lb_set_fv_schedule(lb_grid* grid, int kernel, int chunk);
 /* The schedule lb_step_fv will use now (after AUTO has been resolved). */
 lb_status lb_get_fv_schedule(lb_grid* grid, int* kernel, int* chunk);

@@ -75,7 +75,7 @@ SYMBOLS = ["lb_create_grid", "lb_init", "lb_step_fv", "lb_step_st", "lb_moments"
            "lb_conservation_noalloc", "lb_set_fv_schedule", "lb_get_fv_schedule",
            "lb_autotune_fv", "lb_server_create", "lb_server_submit", "lb_server_pump",
            "lb_server_results", "lb_server_clock", "lb_server_destroy"]
-LB_FV_AUTO, LB_FV_TILE, LB_FV_MARCH, LB_FV_PAIR = 0, 1, 2, 3
+LB_FV_AUTO, LB_FV_TILE, LB_FV_MARCH, LB_FV_PAIR, LB_FV_PTILE = 0, 1, 2, 3, 4
 
 _lib = None
 

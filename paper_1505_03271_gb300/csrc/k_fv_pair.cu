@@ -314,6 +314,250 @@ __global__ void __launch_bounds__(NT) k_fv_pair(const StepArgs<float> A, const i
     }
 }
 
+// ---------------------------------------------------------------------------
+// Paired tile kernel: the tile decomposition of k_fv.cu (TX x TY outputs,
+// regions E4 = tile + 4 and E2 = tile + 2 in shared memory) with two columns
+// per thread-cell and packed FP32 pair arithmetic.  For grids too small to
+// fill the GPU with marching strips, and for the 18-population thermal case.
+
+// x metric of the pair whose left column is g: from the per-column table
+// (20 floats: wp at faces g, g+1, g_r+1; wm at the same faces; 1/dx of both).
+__device__ __forceinline__ void load_col(const float* tab, int g, XPair& X) {
+    const float4* p = reinterpret_cast<const float4*>(tab + 20 * g);
+    const float4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2), d = __ldg(p + 3), e = __ldg(p + 4);
+    X.wp[0] = a.x; X.wp[1] = a.y; X.wp[2] = a.z;
+    X.mp[0] = a.w; X.mp[1] = b.x; X.mp[2] = b.y;
+    X.ep[0] = b.z; X.ep[1] = b.w; X.ep[2] = c.x;
+    X.wm[0] = c.y; X.wm[1] = c.z; X.wm[2] = c.w;
+    X.mm[0] = d.x; X.mm[1] = d.y; X.mm[2] = d.z;
+    X.em[0] = d.w; X.em[1] = e.x; X.em[2] = e.y;
+    X.inv = mk(e.z, e.w);
+}
+
+// Flux divergence of population a at pair-cell (px, y) of a region plane
+// with row stride W pairs.
+template <int a>
+__device__ __forceinline__ V2 advect_region(const V2* plane, int W, int px, int y, const XPair& X, const YPair& Y) {
+    V2 v = bc(0.0f);
+    if constexpr (cx(a) != 0) {
+        const V2* row = plane + y * W;
+        const float2 P0 = row[px - 1].v, P1 = row[px].v, P2 = row[px + 1].v;
+        float fw, fm, fe;
+        if constexpr (cx(a) > 0) {
+            fw = X.wp[0] * P0.x + X.wp[1] * P0.y + X.wp[2] * P1.x;
+            fm = X.mp[0] * P0.y + X.mp[1] * P1.x + X.mp[2] * P1.y;
+            fe = X.ep[0] * P1.x + X.ep[1] * P1.y + X.ep[2] * P2.x;
+        } else {
+            fw = X.wm[0] * P0.y + X.wm[1] * P1.x + X.wm[2] * P1.y;
+            fm = X.mm[0] * P1.x + X.mm[1] * P1.y + X.mm[2] * P2.x;
+            fe = X.em[0] * P1.y + X.em[1] * P2.x + X.em[2] * P2.y;
+        }
+        const V2 dx = (mk(fm, fe) - mk(fw, fm)) * X.inv;
+        v = cx(a) > 0 ? dx : v - dx;
+    }
+    if constexpr (cy(a) != 0) {
+        V2 c[5];
+#pragma unroll
+        for (int i = 0; i < 5; ++i) c[i] = plane[(y - 2 + i) * W + px];
+        if constexpr (cy(a) > 0) {
+            const V2 fn = fma2(Y.pn[0], c[1], fma2(Y.pn[1], c[2], Y.pn[2] * c[3]));
+            const V2 fs = fma2(Y.ps[0], c[0], fma2(Y.ps[1], c[1], Y.ps[2] * c[2]));
+            v = fma2(fn - fs, Y.inv, v);
+        } else {
+            const V2 fn = fma2(Y.mn[0], c[2], fma2(Y.mn[1], c[3], Y.mn[2] * c[4]));
+            const V2 fs = fma2(Y.ms[0], c[1], fma2(Y.ms[1], c[2], Y.ms[2] * c[3]));
+            v = v - (fn - fs) * Y.inv;
+        }
+    }
+    return v;
+}
+
+template <bool TH, int NQ, int H, int W, int a>
+__device__ __forceinline__ void advect_region_all(const V2* P, int px, int y, const XPair& X, const YPair& Y,
+                                                  V2* out) {
+    out[a] = advect_region<a>(P + a * H * W, W, px, y, X, Y) + bc(row_ref_flux<a>(Y, false));
+    if constexpr (TH) out[Q + a] = advect_region<a>(P + (Q + a) * H * W, W, px, y, X, Y) + bc(row_ref_flux<a>(Y, true));
+    if constexpr (a + 1 < Q) advect_region_all<TH, NQ, H, W, a + 1>(P, px, y, X, Y, out);
+}
+
+// Ghost rows of a region (walls on y), own pair-columns: h'_a = h'_inv(a)
+// for f, -h'_inv(a) for g.
+template <bool TH, int NQ, int H, int W>
+__device__ __forceinline__ void ghost_rows_region(V2* P, int gy0, const StepArgs<float>& A) {
+    if (A.bcy != LB_BC_WALLS) return;
+    for (int k = threadIdx.x; k < W * 4; k += blockDim.x) {
+        const int px = k % W, which = k / W;
+        const int kk = (which & 1) + 1;
+        const bool bot = which < 2;
+        const int gy = bot ? -kk : A.ny - 1 + kk;
+        const int gys = bot ? kk - 1 : A.ny - kk;
+        const int ey = gy - gy0, eys = gys - gy0;
+        if (ey < 0 || ey >= H) continue;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            P[(a * H + ey) * W + px] = P[(inv(a) * H + eys) * W + px];
+            if constexpr (TH) P[((Q + a) * H + ey) * W + px] = bc(0.0f) - P[((Q + inv(a)) * H + eys) * W + px];
+        }
+    }
+}
+
+template <typename S, bool TH, int TX, int TY, int NTH>
+__global__ void __launch_bounds__(NTH) k_fv_ptile(const StepArgs<float> A) {
+    constexpr int NQ = TH ? 2 * Q : Q;
+    constexpr int EW = (TX + 8) / 2, EH = TY + 8, NE = EW * EH;
+    constexpr int BW = (TX + 4) / 2, BH = TY + 4, NB = BW * BH;
+    constexpr int TW = TX / 2;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V2* sH = reinterpret_cast<V2*>(smem_raw);  // [NQ][EH][EW] h^n
+    V2* sFC = sH + NQ * NE;                    // [NQ][BH][BW] f~ + Coll, then - dt/2 A[h^n]
+    V2* sHs = sFC + NQ * NB;                   // [NQ][BH][BW] h*
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int nx = A.nx;
+    const S* fin = static_cast<const S*>(A.fin);
+    const S* gin = static_cast<const S*>(A.gin);
+
+    // ---- time level n on E4 ----
+    for (int k = threadIdx.x; k < NE; k += NTH) {
+        const int px = k % EW, ey = k / EW;
+        int gy;
+        if (!map_axis(y0 - 4 + ey, A.ny, A.bcy, gy)) continue;
+        const int xu = x0 - 4 + 2 * px;
+        const int gxl = ((xu % nx) + nx) % nx, gxr = ((xu + 1) % nx + nx) % nx;
+        const bool contiguous = xu >= 0 && xu + 1 < nx;
+        const long long row = (long long)gy * A.pitch;
+        V2 d[Q], e[Q];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const S* b = fin + a * A.plane + row;
+            d[a] = contiguous ? PairIO<S>::ld(b + xu) : mk(Store<S>::ld(b + gxl), Store<S>::ld(b + gxr));
+            if constexpr (TH) {
+                const S* bg = gin + a * A.plane + row;
+                e[a] = contiguous ? PairIO<S>::ld(bg + xu) : mk(Store<S>::ld(bg + gxl), Store<S>::ld(bg + gxr));
+            }
+        }
+        const float4 o = __ldg(reinterpret_cast<const float4*>(A.rowtab + 20 * gy) + 3);
+        PairCell<TH> c;
+        c.build(d, e, A, o.y, TH ? o.z : 0.0f);
+        const bool inB = px >= 1 && px < EW - 1 && ey >= 2 && ey < EH - 2;
+        const int kb = (ey - 2) * BW + (px - 1);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const V2 neq = c.feqd[a] - d[a];
+            sH[a * NE + k] = fma2(bc(A.omh), neq, fma2(bc(A.hf), c.F[a], d[a]));
+            if (inB) sFC[a * NB + kb] = fma2(bc(A.om), neq, fma2(bc(A.cf), c.F[a], d[a]));
+            if constexpr (TH) {
+                const V2 neqg = c.geqd[a] - e[a];
+                sH[(Q + a) * NE + k] = fma2(bc(A.omgh), neqg, e[a]);
+                if (inB) sFC[(Q + a) * NB + kb] = fma2(bc(A.omg), neqg, e[a]);
+            }
+        }
+    }
+    __syncthreads();
+    ghost_rows_region<TH, NQ, EH, EW>(sH, y0 - 4, A);
+    __syncthreads();
+
+    // ---- predictor on E2 ----
+    for (int k = threadIdx.x; k < NB; k += NTH) {
+        const int bx = k % BW, by = k / BW;
+        int gy;
+        if (!map_axis(y0 - 2 + by, A.ny, A.bcy, gy)) continue;
+        const int xu = x0 - 2 + 2 * bx;
+        const int gxl = ((xu % nx) + nx) % nx;
+        XPair X;
+        load_col(A.coltab, gxl, X);
+        YPair Y;
+        load_row(A.rowtab, gy, Y);
+        V2 adv[NQ];
+        advect_region_all<TH, NQ, EH, EW, 0>(sH, bx + 1, by + 2, X, Y, adv);
+        const bool tile = bx >= 1 && bx < BW - 1 && by >= 2 && by < BH - 2;
+        V2 fs[Q], es[Q];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const V2 fc = sFC[a * NB + k];
+            fs[a] = fma2(bc(-A.dt), adv[a], fc);
+            if (tile) sFC[a * NB + k] = fma2(bc(-A.hf), adv[a], fc);
+            if constexpr (TH) {
+                const V2 gc = sFC[(Q + a) * NB + k];
+                es[a] = fma2(bc(-A.dt), adv[Q + a], gc);
+                if (tile) sFC[(Q + a) * NB + k] = fma2(bc(-A.hf), adv[Q + a], gc);
+            }
+        }
+        PairCell<TH> c;
+        c.build(fs, es, A, Y.ro, TH ? Y.to : 0.0f);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            sHs[a * NB + k] = fma2(bc(A.omh), c.feqd[a] - fs[a], fma2(bc(A.hf), c.F[a], fs[a]));
+            if constexpr (TH) sHs[(Q + a) * NB + k] = fma2(bc(A.omgh), c.geqd[a] - es[a], es[a]);
+        }
+    }
+    __syncthreads();
+    ghost_rows_region<TH, NQ, BH, BW>(sHs, y0 - 2, A);
+    __syncthreads();
+
+    // ---- corrector on the tile ----
+    S* fout = static_cast<S*>(A.fout);
+    S* gout = static_cast<S*>(A.gout);
+    for (int k = threadIdx.x; k < TW * TY; k += NTH) {
+        const int tx = k % TW, ty = k / TW;
+        const int gx = x0 + 2 * tx, gy = y0 + ty;
+        if (gx >= nx || gy >= A.ny) continue;
+        XPair X;
+        load_col(A.coltab, gx, X);
+        YPair Y;
+        load_row(A.rowtab, gy, Y);
+        V2 adv[NQ];
+        advect_region_all<TH, NQ, BH, BW, 0>(sHs, tx + 1, ty + 2, X, Y, adv);
+        const int kb = (ty + 2) * BW + tx + 1;
+        const long long row = (long long)gy * A.pitch;
+        const bool both = gx + 1 < nx;
+#pragma unroll
+        for (int a = 0; a < NQ; ++a) {
+            const V2 o = fma2(bc(-A.hf), adv[a], sFC[a * NB + kb]);
+            S* base = (a < Q ? fout + a * A.plane : gout + (a - Q) * A.plane) + row;
+            if (both) PairIO<S>::st(base + gx, o);
+            else Store<S>::st(base + gx, o.v.x);
+        }
+    }
+}
+
+template <typename S, bool TH, int TX, int TY, int NTH>
+static cudaError_t run_ptile(const void* vargs, cudaStream_t s) {
+    const StepArgs<float>& A = *static_cast<const StepArgs<float>*>(vargs);
+    constexpr int NQ = TH ? 2 * Q : Q;
+    constexpr size_t smem = sizeof(V2) * NQ * (((TX + 8) / 2) * (TY + 8) + 2 * ((TX + 4) / 2) * (TY + 4));
+    static_assert(smem <= 232448, "shared memory per CTA");
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_fv_ptile<S, TH, TX, TY, NTH>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    dim3 grid((A.nx + TX - 1) / TX, (A.ny + TY - 1) / TY);
+    k_fv_ptile<S, TH, TX, TY, NTH><<<grid, NTH, smem, s>>>(A);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <typename S, bool TH>
+static cudaError_t run_ptile_shape(const void* args, int shape, cudaStream_t s) {
+    if (shape == 16) return run_ptile<S, TH, 16, 16, 128>(args, s);
+    return run_ptile<S, TH, 32, 16, 256>(args, s);
+}
+
+cudaError_t launch_fv_ptile(Prec p, bool th, const void* args, int shape, cudaStream_t s) {
+    switch (p) {
+        case Prec::F32:
+            return th ? run_ptile_shape<float, true>(args, shape, s) : run_ptile_shape<float, false>(args, shape, s);
+        case Prec::F16:
+            return th ? run_ptile_shape<__half, true>(args, shape, s) : run_ptile_shape<__half, false>(args, shape, s);
+        case Prec::BF16:
+            return th ? run_ptile_shape<__nv_bfloat16, true>(args, shape, s)
+                      : run_ptile_shape<__nv_bfloat16, false>(args, shape, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 template <typename S, bool TH, int NT>
 static cudaError_t run_pair(const void* vargs, int chunk, cudaStream_t s) {
     const StepArgs<float>& A = *static_cast<const StepArgs<float>*>(vargs);

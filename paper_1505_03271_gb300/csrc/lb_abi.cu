@@ -48,8 +48,8 @@ namespace {
 
 void release(lb_grid* G) {
     void* ptrs[] = {G->f[0], G->f[1], G->g[0], G->g[1], G->mx, G->my, G->dxv, G->dyv, G->xc,
-                    G->yc, G->toff, G->toff_r, G->roff, G->roff_r, G->dref_r, G->rowtab, G->fields, G->partial,
-                    G->red};
+                    G->yc, G->toff, G->toff_r, G->roff, G->roff_r, G->dref_r, G->rowtab, G->coltab, G->fields,
+                    G->partial, G->red};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -101,8 +101,8 @@ bool pair_ok(const lb_grid* G) { return G->prec != Prec::F64 && G->d.bcx == LB_B
 // strips, else the tile kernel.
 int resolved_kernel(const lb_grid* G) {
     if (G->fv_kernel != LB_FV_AUTO) return G->fv_kernel;
-    if (G->nx >= 480 && G->ny >= 256) return pair_ok(G) ? LB_FV_PAIR : LB_FV_MARCH;
-    return LB_FV_TILE;
+    if (G->nx >= 480 && G->ny >= 256 && !G->d.thermal) return pair_ok(G) ? LB_FV_PAIR : LB_FV_MARCH;
+    return pair_ok(G) ? LB_FV_PTILE : LB_FV_TILE;
 }
 
 // Rows per CTA of the marching kernels: one wave of resident CTAs.
@@ -131,6 +131,8 @@ cudaError_t launch_fv_step(lb_grid* G) {
     const bool th = G->d.thermal != 0;
     const int k = resolved_kernel(G);
     if (k == LB_FV_PAIR) return launch_fv_pair(G->prec, th, &A, resolved_chunk(G), G->stream);
+    if (k == LB_FV_PTILE) return launch_fv_ptile(G->prec, th, &A, G->fv_kernel == LB_FV_PTILE ? G->fv_chunk : 0,
+                                                 G->stream);
     if (k == LB_FV_MARCH) return launch_fv_march(G->prec, th, &A, resolved_chunk(G), G->stream);
     return launch_fv(G->prec, th, &A, G->fv_kernel == LB_FV_TILE ? G->fv_chunk : 0, G->stream);
 }
@@ -231,6 +233,31 @@ lb_status lb_create_grid(const lb_grid_desc* d, lb_grid** out) {
     alloc(&G->roff_r, (as_float ? sizeof(float) : sizeof(double)) * G->ny);
     alloc(&G->dref_r, (as_float ? sizeof(float) : sizeof(double)) * 4 * G->ny);
     alloc((void**)&G->rowtab, sizeof(float) * 20 * G->ny);
+    alloc((void**)&G->coltab, sizeof(float) * 20 * G->nx);
+    if (st == LB_OK && as_float) {
+        // x data of the column pair starting at each column (the right column wraps)
+        const int nx = G->nx;
+        const std::vector<double> mxv = G->ax.metric();
+        auto wpv = [&](int r, int k) { return (float)mxv[r * (nx + 1) + k]; };
+        auto wmv = [&](int r, int k) { return (float)mxv[(3 + r) * (nx + 1) + k]; };
+        std::vector<float> tab(20 * (size_t)nx, 0.0f);
+        for (int c = 0; c < nx; ++c) {
+            const int cr = (c + 1) % nx;
+            float* e = &tab[20 * (size_t)c];
+            for (int r = 0; r < 3; ++r) {
+                e[r] = wpv(r, c);
+                e[3 + r] = wpv(r, c + 1);
+                e[6 + r] = wpv(r, cr + 1);
+                e[9 + r] = wmv(r, c);
+                e[12 + r] = wmv(r, c + 1);
+                e[15 + r] = wmv(r, cr + 1);
+            }
+            e[18] = (float)mxv[6 * (nx + 1) + c];
+            e[19] = (float)mxv[6 * (nx + 1) + cr];
+        }
+        if (cudaMemcpy(G->coltab, tab.data(), sizeof(float) * tab.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            st = fail(LB_ERR_CUDA, "coltab upload failed");
+    }
     alloc((void**)&G->partial, sizeof(double) * kRed * G->nred);
     alloc((void**)&G->red, sizeof(double) * kRed);
     if (st == LB_OK) st = upload(&G->mx, G->ax.metric(), as_float);
@@ -412,11 +439,13 @@ lb_status lb_step_fv(lb_grid* G, int nsteps) {
 
 lb_status lb_set_fv_schedule(lb_grid* G, int kernel, int chunk) {
     if (!G) return fail(LB_ERR_ARG, "grid is NULL");
-    if (kernel < LB_FV_AUTO || kernel > LB_FV_PAIR) return fail(LB_ERR_ARG, "unknown FV kernel %d", kernel);
+    if (kernel < LB_FV_AUTO || kernel > LB_FV_PTILE) return fail(LB_ERR_ARG, "unknown FV kernel %d", kernel);
     if (chunk < 0) return fail(LB_ERR_ARG, "chunk must be >= 0");
     if (kernel == LB_FV_TILE && chunk != 0 && chunk != 8 && chunk != 16)
         return fail(LB_ERR_ARG, "tile shape must be 0 (32 x 16), 16 (16 x 16) or 8 (16 x 8)");
-    if (kernel == LB_FV_PAIR && !pair_ok(G))
+    if (kernel == LB_FV_PTILE && chunk != 0 && chunk != 16)
+        return fail(LB_ERR_ARG, "paired tile shape must be 0 (32 x 16) or 16 (16 x 16)");
+    if ((kernel == LB_FV_PAIR || kernel == LB_FV_PTILE) && !pair_ok(G))
         return fail(LB_ERR_ARG, "the paired FV kernel needs FP32/FP16/BF16 storage and a periodic x axis");
     G->fv_kernel = kernel;
     G->fv_chunk = chunk;
@@ -426,8 +455,10 @@ lb_status lb_set_fv_schedule(lb_grid* G, int kernel, int chunk) {
 lb_status lb_get_fv_schedule(lb_grid* G, int* kernel, int* chunk) {
     if (!G) return fail(LB_ERR_ARG, "grid is NULL");
     if (kernel) *kernel = resolved_kernel(G);
-    if (chunk) *chunk = resolved_kernel(G) == LB_FV_TILE ? (G->fv_kernel == LB_FV_TILE ? G->fv_chunk : 0)
-                                                         : resolved_chunk(G);
+    if (chunk) {
+        const int k = resolved_kernel(G);
+        *chunk = (k == LB_FV_TILE || k == LB_FV_PTILE) ? (G->fv_kernel == k ? G->fv_chunk : 0) : resolved_chunk(G);
+    }
     return LB_OK;
 }
 
@@ -448,6 +479,10 @@ lb_status lb_autotune_fv(lb_grid* G, int steps) {
     if (sg) cudaMemcpyAsync(sg, G->g[cur0], bytes, cudaMemcpyDeviceToDevice, G->stream);
     const int k0 = G->fv_kernel, c0 = G->fv_chunk;
     std::vector<std::pair<int, int>> cands = {{LB_FV_TILE, 0}, {LB_FV_TILE, 16}, {LB_FV_TILE, 8}};
+    if (pair_ok(G)) {
+        cands.push_back({LB_FV_PTILE, 0});
+        cands.push_back({LB_FV_PTILE, 16});
+    }
     for (int kern : {(int)LB_FV_MARCH, (int)LB_FV_PAIR}) {
         if (kern == LB_FV_PAIR && !pair_ok(G)) continue;
         G->fv_kernel = kern;

@@ -121,7 +121,8 @@ struct lb_grid {
     double* roff = nullptr;     // per-row storage offset of f, FP64 (ny)
     void* roff_r = nullptr;
     void* dref_r = nullptr;     // [4][ny] y flux divergence of the base state, compute precision
-    float* rowtab = nullptr;    // [ny][20] y weights, 1/dy, offsets, base-state fluxes (paired kernel)
+    float* rowtab = nullptr;    // [ny][20] y weights, 1/dy, offsets, base-state fluxes (paired kernels)
+    float* coltab = nullptr;    // [nx][20] x weights of a column pair and its 1/dx (paired tile kernel)
     double* fields = nullptr;   // [4][ny][nx] staging for init/moments
     double* partial = nullptr;  // reduction partials
     double* red = nullptr;      // reduction totals
@@ -168,6 +169,7 @@ inline StepArgs<R> step_args(const lb_grid* G, double dt) {
     A.roff = static_cast<const R*>(G->roff_r);
     A.dref = static_cast<const R*>(G->dref_r);
     A.rowtab = G->rowtab;
+    A.coltab = G->coltab;
     return A;
 }
 

@@ -99,7 +99,8 @@ struct StepArgs {
     const R* toff;          // per row: T_r - T0 (thermal grids)
     const R* roff;          // per row: rho_r - 1
     const R* dref;          // [4][ny]: y flux divergence of rho_r (c_y > 0, < 0), of T_r (> 0, < 0)
-    const float* rowtab;    // [ny][20] per-row y data of the paired kernel (FP32 grids)
+    const float* rowtab;    // [ny][20] per-row y data of the paired kernels (FP32 grids)
+    const float* coltab;    // [nx][20] per-column-pair x data of the paired tile kernel
 };
 
 // Wrap or reject a global index on one axis: periodic axes wrap, wall axes
@@ -203,6 +204,8 @@ size_t march_smem(Prec p, bool thermal);
 cudaError_t launch_fv_pair(Prec p, bool thermal, const void* args, int chunk, cudaStream_t s);
 int pair_width();
 size_t pair_smem(bool thermal);
+// paired tile kernel: shape 0 = 32 x 16, 16 = 16 x 16 (x-periodic, FP32 arithmetic)
+cudaError_t launch_fv_ptile(Prec p, bool thermal, const void* args, int shape, cudaStream_t s);
 
 struct AuxArgs {
     const void* f;  // state buffers (deviation storage)
