@@ -127,7 +127,9 @@ def make_grid(lb, w, stream, tune=True):
 
 def schedule_name(lb, g, scheme):
     if scheme != "fv":
-        return "st push, one thread per cell"
+        if g.store == lb.LB_STORE_F64:
+            return "st push, one thread per cell"
+        return "st pair (f32x2), two cells per thread"
     k, c = g.fv_schedule()
     if k == lb.LB_FV_TILE:
         return "fv tile %s (halo 4)" % {0: "32x16", 16: "16x16", 8: "16x8"}[c]
@@ -156,6 +158,24 @@ def time_steps(lb, torch, g, scheme, steps, warmup, flush=None):
     return [a.elapsed_time(b) for a, b in evs], launches
 
 
+def measured_traffic(schedule, case):
+    """DRAM bytes per launch from the committed ncu summary of this kernel
+    and workload, or None if there is none or the kernel's sources have
+    changed since it was captured."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            table = json.load(fh)
+        e = table["%s|%s" % (schedule, case)]
+        m = hashlib.sha256()
+        for f in e["files"]:
+            with open(os.path.join(ROOT, "paper_1505_03271_gb300", "csrc", f), "rb") as fh:
+                m.update(fh.read())
+        return e["bytes"] if m.hexdigest()[:16] == e["sources"] else None
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def roofline(bytes_per_step, mean_ms, peak, peak_kind, traffic=None):
     achieved = bytes_per_step / (mean_ms * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -165,19 +185,21 @@ def roofline(bytes_per_step, mean_ms, peak, peak_kind, traffic=None):
 
 def extra_lines(lb, torch, cfg, stream, peak, peak_kind, flush):
     out = {}
-    specs = [("st8192_f32", cfg.st_sweep(8192, lb.LB_STORE_F32), 20, None),
-             ("st8192_bf16dev", cfg.st_sweep(8192, lb.LB_STORE_BF16DEV), 20, None),
-             ("st8192_f16dev", cfg.st_sweep(8192, lb.LB_STORE_F16DEV), 20, None),
-             ("fv4096_f32", _fv_big(cfg, 4096), 10, None),
-             ("fv_rb1024_f16dev", cfg.rayleigh_benard(1024, 1e8), 20, flush)]
-    for name, w, k, fl in specs:
+    specs = [("st8192_f32", cfg.st_sweep(8192, lb.LB_STORE_F32), 20, None, None),
+             ("st8192_bf16dev", cfg.st_sweep(8192, lb.LB_STORE_BF16DEV), 20, None, None),
+             ("st8192_f16dev", cfg.st_sweep(8192, lb.LB_STORE_F16DEV), 20, None, None),
+             ("fv4096_f32", _fv_big(cfg, 4096), 10, None, None),
+             ("fv_rb1024_f16dev", cfg.rayleigh_benard(1024, 1e8), 20, flush, "rb1024")]
+    for name, w, k, fl, case in specs:
         g = make_grid(lb, w, stream)
         ms, _ = time_steps(lb, torch, g, w.scheme, k, 3, fl)
         mean = sum(ms) / len(ms)
         bpc = cfg.bytes_per_cell(w.grid["store"], w.grid.get("thermal", False))
+        sched = schedule_name(lb, g, w.scheme)
         out[name] = {"mlups": round(w.cells / (mean * 1e-3) / 1e6, 1), "ms_per_step": round(mean, 5),
-                     "bytes_per_cell": bpc, "schedule": schedule_name(lb, g, w.scheme),
-                     "roofline": roofline(bpc * w.cells, mean, peak, peak_kind),
+                     "bytes_per_cell": bpc, "schedule": sched,
+                     "roofline": roofline(bpc * w.cells, mean, peak, peak_kind,
+                                          measured_traffic(sched, case) if case else None),
                      "cells": w.cells, "l2": "flushed" if fl is not None else "state > L2"}
         g.close()
         torch.cuda.empty_cache()
@@ -195,7 +217,8 @@ def serving_measure(lb, torch, count=120, rate=25.0):
     """Scaled config-5 stream through the batching server and one at a time."""
     from paper_1505_03271_gb300 import serving
     reqs = serving.make_requests(count, rate)
-    srv = serving.run_server(lb, reqs)
+    srv = serving.run_server(lb, reqs, policy=lb.LB_SERVE_SHORTEST)
+    share = serving.run_server(lb, reqs, policy=lb.LB_SERVE_SHARE)
     seq = serving.run_sequential(lb, torch, reqs)
     # the same request must give the same Nusselt numbers both ways
     diffs = [abs(srv["results"][r.rid]["nu_vol"] - seq["results"][r.rid]["nu_vol"])
@@ -204,7 +227,8 @@ def serving_measure(lb, torch, count=120, rate=25.0):
     return {"workload": "RB FV requests, N in {64..1024}^2 tanh plates, Ra log-uniform 1e4-1e8, Pr=1, "
                         "steps uniform 50-1000 (config 5 steps / 20), FP16 deviation storage, "
                         "Poisson arrivals %.0f/s, %d requests" % (rate, count),
-            "server": {k: srv[k] for k in keep}, "sequential": {k: seq[k] for k in keep},
+            "server": {k: srv[k] for k in keep}, "server_equal_share": {k: share[k] for k in keep},
+            "sequential": {k: seq[k] for k in keep},
             "max_abs_nu_vol_diff_server_vs_sequential": max(diffs) if diffs else None}
 
 
@@ -395,7 +419,8 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(mean_ms, 5),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
             "data": "synthetic", "config": _config(w, args.case), "gpu_launches": launches,
-            "roofline": roofline(bpc * w.cells, mean_ms, peak, peak_kind),
+            "roofline": roofline(bpc * w.cells, mean_ms, peak, peak_kind,
+                                 measured_traffic(schedule_name(lb, g, w.scheme), args.case)),
             "clocks": clk.summary()}
     line["config"]["parallelism"] = "replicas" if world > 1 else "single"
     line["config"]["schedule"] = schedule_name(lb, g, w.scheme)

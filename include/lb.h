@@ -249,12 +249,20 @@ typedef struct {
     double t_submit, t_admit, t_done; /* seconds on the server clock          */
 } lb_result;
 
+/* Which admitted requests take steps in a pump:
+ *   LB_SERVE_SHARE:    all of them (equal steps for everyone);
+ *   LB_SERVE_SHORTEST: least remaining work (cells x steps) first, as many as
+ *                      fit about two waves of CTAs (at least one); the others
+ *                      keep their memory and wait. */
+typedef enum { LB_SERVE_SHARE = 0, LB_SERVE_SHORTEST = 1 } lb_serve_policy;
+
 /* store/thermal: the one storage type and model all requests use.
  * hbm_budget: bytes of device memory the requests may hold at once.
- * steps_per_launch: >= 1 (steps per pump).  cuda_stream: NULL lets the server create
- * its own non-blocking stream (graph capture needs a non-default stream). */
+ * steps_per_launch: >= 1 (steps per pump).  policy: lb_serve_policy.
+ * cuda_stream: NULL lets the server create its own non-blocking stream
+ * (graph capture needs a non-default stream). */
 lb_status lb_server_create(int store, int thermal, unsigned long long hbm_budget, int steps_per_launch,
-                           void* cuda_stream, lb_server** out);
+                           int policy, void* cuda_stream, lb_server** out);
 /* Queue a request (host side only).  LB_ERR_ARG if its storage or thermal
  * flag differs from the server's or it alone exceeds the budget. */
 lb_status lb_server_submit(lb_server* server, const lb_request* request);

@@ -76,6 +76,7 @@ SYMBOLS = ["lb_create_grid", "lb_init", "lb_step_fv", "lb_step_st", "lb_moments"
            "lb_autotune_fv", "lb_server_create", "lb_server_submit", "lb_server_pump",
            "lb_server_results", "lb_server_clock", "lb_server_destroy"]
 LB_FV_AUTO, LB_FV_TILE, LB_FV_MARCH, LB_FV_PAIR, LB_FV_PTILE = 0, 1, 2, 3, 4
+LB_SERVE_SHARE, LB_SERVE_SHORTEST = 0, 1
 
 _lib = None
 
@@ -111,7 +112,7 @@ def load(build: bool = True) -> C.CDLL:
     L.lb_set_fv_schedule.argtypes = [G, C.c_int, C.c_int]
     L.lb_get_fv_schedule.argtypes = [G, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.lb_autotune_fv.argtypes = [G, C.c_int]
-    L.lb_server_create.argtypes = [C.c_int, C.c_int, C.c_ulonglong, C.c_int, C.c_void_p,
+    L.lb_server_create.argtypes = [C.c_int, C.c_int, C.c_ulonglong, C.c_int, C.c_int, C.c_void_p,
                                    C.POINTER(C.c_void_p)]
     L.lb_server_submit.argtypes = [C.c_void_p, C.POINTER(lb_request)]
     L.lb_server_pump.argtypes = [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]
@@ -346,13 +347,14 @@ class Server:
     """Continuous-batching server of FV requests (see include/lb.h)."""
 
     def __init__(self, store=LB_STORE_F32, thermal=True, hbm_budget=64 << 30, steps_per_launch=50,
-                 stream=None):
+                 policy=None, stream=None):
         if isinstance(store, str):
             store = STORE_NAMES[store]
         self.store, self.thermal = int(store), bool(thermal)
         h = C.c_void_p()
+        policy = LB_SERVE_SHORTEST if policy is None else int(policy)
         _check(load().lb_server_create(self.store, int(self.thermal), int(hbm_budget),
-                                       int(steps_per_launch), stream, C.byref(h)))
+                                       int(steps_per_launch), policy, stream, C.byref(h)))
         self._h = h
         self._keep = {}
 

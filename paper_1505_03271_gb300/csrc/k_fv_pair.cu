@@ -402,7 +402,7 @@ __device__ __forceinline__ void ghost_rows_region(V2* P, int gy0, const StepArgs
 }
 
 template <typename S, bool TH, int TX, int TY, int NTH>
-__global__ void __launch_bounds__(NTH) k_fv_ptile(const StepArgs<float> A) {
+__device__ __forceinline__ void ptile_body(const StepArgs<float>& A, const int x0, const int y0) {
     constexpr int NQ = TH ? 2 * Q : Q;
     constexpr int EW = (TX + 8) / 2, EH = TY + 8, NE = EW * EH;
     constexpr int BW = (TX + 4) / 2, BH = TY + 4, NB = BW * BH;
@@ -411,7 +411,6 @@ __global__ void __launch_bounds__(NTH) k_fv_ptile(const StepArgs<float> A) {
     V2* sH = reinterpret_cast<V2*>(smem_raw);  // [NQ][EH][EW] h^n
     V2* sFC = sH + NQ * NE;                    // [NQ][BH][BW] f~ + Coll, then - dt/2 A[h^n]
     V2* sHs = sFC + NQ * NB;                   // [NQ][BH][BW] h*
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int nx = A.nx;
     const S* fin = static_cast<const S*>(A.fin);
     const S* gin = static_cast<const S*>(A.gin);
@@ -517,6 +516,65 @@ __global__ void __launch_bounds__(NTH) k_fv_ptile(const StepArgs<float> A) {
             if (both) PairIO<S>::st(base + gx, o);
             else Store<S>::st(base + gx, o.v.x);
         }
+    }
+}
+
+template <typename S, bool TH, int TX, int TY, int NTH>
+__global__ void __launch_bounds__(NTH) k_fv_ptile(const StepArgs<float> A) {
+    ptile_body<S, TH, TX, TY, NTH>(A, blockIdx.x * TX, blockIdx.y * TY);
+}
+
+// Many grids in one launch (the serving path): CTA b steps tile tiles[b] =
+// (request, tile x, tile y) with that request's parameters, picking its
+// input buffer from step k of the launch sequence; requests with fewer than
+// k + 1 steps left are skipped.  Same tile code whatever else is batched.
+template <typename S, bool TH, int TX, int TY, int NTH>
+__global__ void __launch_bounds__(NTH)
+k_fv_ptile_batched(const BatchReq<float>* reqs, const int4* tiles, const int* ntiles, const int k) {
+    if ((int)blockIdx.x >= *ntiles) return;
+    const int4 t = tiles[blockIdx.x];
+    const BatchReq<float>& B = reqs[t.x];
+    if (k >= B.remaining) return;
+    StepArgs<float> A = B.args;
+    const int p = (B.parity + k) & 1;
+    A.fin = B.f[p];
+    A.fout = B.f[p ^ 1];
+    A.gin = B.g[p];
+    A.gout = B.g[p ^ 1];
+    ptile_body<S, TH, TX, TY, NTH>(A, t.y * TX, t.z * TY);
+}
+
+template <typename S, bool TH>
+static cudaError_t run_ptile_batched(const void* reqs, const int4* tiles, const int* ntiles, int capacity, int k,
+                                     cudaStream_t s) {
+    constexpr int NQ = TH ? 2 * Q : Q;
+    constexpr size_t smem = sizeof(V2) * NQ * (((32 + 8) / 2) * (16 + 8) + 2 * ((32 + 4) / 2) * (16 + 4));
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_fv_ptile_batched<S, TH, 32, 16, 256>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    k_fv_ptile_batched<S, TH, 32, 16, 256><<<capacity, 256, smem, s>>>(static_cast<const BatchReq<float>*>(reqs),
+                                                                      tiles, ntiles, k);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fv_ptile_batched(Prec p, bool th, const void* reqs, const int4* tiles, const int* ntiles,
+                                    int capacity, int k, cudaStream_t s) {
+    switch (p) {
+        case Prec::F32:
+            return th ? run_ptile_batched<float, true>(reqs, tiles, ntiles, capacity, k, s)
+                      : run_ptile_batched<float, false>(reqs, tiles, ntiles, capacity, k, s);
+        case Prec::F16:
+            return th ? run_ptile_batched<__half, true>(reqs, tiles, ntiles, capacity, k, s)
+                      : run_ptile_batched<__half, false>(reqs, tiles, ntiles, capacity, k, s);
+        case Prec::BF16:
+            return th ? run_ptile_batched<__nv_bfloat16, true>(reqs, tiles, ntiles, capacity, k, s)
+                      : run_ptile_batched<__nv_bfloat16, false>(reqs, tiles, ntiles, capacity, k, s);
+        default: return cudaErrorInvalidValue;
     }
 }
 

@@ -206,6 +206,9 @@ int pair_width();
 size_t pair_smem(bool thermal);
 // paired tile kernel: shape 0 = 32 x 16, 16 = 16 x 16 (x-periodic, FP32 arithmetic)
 cudaError_t launch_fv_ptile(Prec p, bool thermal, const void* args, int shape, cudaStream_t s);
+// batched paired tile (32 x 16) over a request table, as launch_fv_batched
+cudaError_t launch_fv_ptile_batched(Prec p, bool thermal, const void* reqs, const int4* tiles, const int* ntiles,
+                                    int capacity, int k, cudaStream_t s);
 
 struct AuxArgs {
     const void* f;  // state buffers (deviation storage)

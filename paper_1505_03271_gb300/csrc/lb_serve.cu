@@ -12,6 +12,7 @@
 //      mass are computed, the grid is freed, the result is queued.
 // Every tile is stepped by the same code whatever else is in the table, so a
 // request's result does not depend on what it was batched with.
+#include <algorithm>
 #include <chrono>
 #include <deque>
 #include <string>
@@ -74,7 +75,11 @@ struct lb_server {
     int* h_ntiles = nullptr;
     cudaGraphExec_t graph = nullptr;
     int graph_cap = 0;
+    bool graph_paired = false;
     bool warmed = false;
+    bool all_periodic_x = true;  // every active request has a periodic x axis
+    int policy = LB_SERVE_SHARE;
+    int sms = 152;
 
     double now() const {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -123,10 +128,16 @@ void fill_req(lb_server* S, int i, const Active& a) {
     t->remaining = a.remaining;
 }
 
+// The paired tile kernel (packed FP32 arithmetic) serves FP32/FP16/BF16
+// requests with periodic x; FP64 and x-wall requests use the scalar tile.
+bool paired(const lb_server* S) { return S->prec != Prec::F64 && S->all_periodic_x; }
+
 lb_status launch_steps(lb_server* S, int ncap) {
     for (int k = 0; k < S->K; ++k) {
-        cudaError_t e = launch_fv_batched(S->prec, S->thermal != 0, S->d_reqs, S->d_tiles, S->d_ntiles, ncap, k,
-                                          S->stream);
+        cudaError_t e = paired(S) ? launch_fv_ptile_batched(S->prec, S->thermal != 0, S->d_reqs, S->d_tiles,
+                                                            S->d_ntiles, ncap, k, S->stream)
+                                  : launch_fv_batched(S->prec, S->thermal != 0, S->d_reqs, S->d_tiles, S->d_ntiles,
+                                                      ncap, k, S->stream);
         if (e != cudaSuccess) return fail(LB_ERR_CUDA, std::string("server launch: ") + cudaGetErrorString(e));
     }
     return LB_OK;
@@ -141,7 +152,7 @@ lb_status run_batch(lb_server* S) {
         S->warmed = true;
         return launch_steps(S, ncap);
     }
-    if (!S->graph || S->graph_cap != ncap) {
+    if (!S->graph || S->graph_cap != ncap || S->graph_paired != paired(S)) {
         if (S->graph) cudaGraphExecDestroy(S->graph);
         S->graph = nullptr;
         cudaGraph_t g = nullptr;
@@ -155,6 +166,7 @@ lb_status run_batch(lb_server* S) {
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return fail(LB_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
         S->graph_cap = ncap;
+        S->graph_paired = paired(S);
     }
     cudaError_t e = cudaGraphLaunch(S->graph, S->stream);
     if (e != cudaSuccess) return fail(LB_ERR_CUDA, std::string("graph launch: ") + cudaGetErrorString(e));
@@ -188,8 +200,9 @@ void retire(lb_server* S, Active& a, lb_status status) {
 extern "C" {
 
 lb_status lb_server_create(int store, int thermal, unsigned long long hbm_budget, int steps_per_launch,
-                           void* cuda_stream, lb_server** out) {
+                           int policy, void* cuda_stream, lb_server** out) {
     if (!out) return fail(LB_ERR_ARG, "NULL output");
+    if (policy != LB_SERVE_SHARE && policy != LB_SERVE_SHORTEST) return fail(LB_ERR_ARG, "unknown policy");
     if (store < LB_STORE_F64 || store > LB_STORE_BF16DEV) return fail(LB_ERR_ARG, "bad store");
     if (steps_per_launch < 1) return fail(LB_ERR_ARG, "steps_per_launch must be >= 1");
     lb_server* S = new lb_server();
@@ -198,6 +211,7 @@ lb_status lb_server_create(int store, int thermal, unsigned long long hbm_budget
     S->prec = prec_of(store);
     S->budget = hbm_budget;
     S->K = steps_per_launch;
+    S->policy = policy;
     S->stream = static_cast<cudaStream_t>(cuda_stream);
     if (!S->stream) {
         if (cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking) != cudaSuccess) {
@@ -209,6 +223,8 @@ lb_status lb_server_create(int store, int thermal, unsigned long long hbm_budget
     }
     S->t0 = std::chrono::steady_clock::now();
     cudaGetDevice(&S->device);
+    cudaDeviceGetAttribute(&S->sms, cudaDevAttrMultiProcessorCount, S->device);
+    if (S->sms <= 0) S->sms = 152;
     if (cudaMalloc((void**)&S->d_ntiles, sizeof(int)) != cudaSuccess ||
         cudaMallocHost((void**)&S->h_ntiles, sizeof(int)) != cudaSuccess) {
         cudaGetLastError();
@@ -250,7 +266,7 @@ lb_status lb_server_pump(lb_server* S, int* n_active, int* n_pending) {
         lb_status st = lb_create_grid(&d, &a.grid);
         if (st == LB_OK) st = lb_init(a.grid, &p.req.params, &p.req.init);
         if (st == LB_OK) {
-            // the batched kernel uses the tile kernel's arithmetic
+            // the batched kernels use the tile decomposition
             a.grid->fv_kernel = LB_FV_TILE;
             a.t_admit = S->now();
             S->used += need;
@@ -281,11 +297,35 @@ lb_status lb_server_pump(lb_server* S, int* n_active, int* n_pending) {
     }
     if (!S->active.empty()) {
         // 2. tile table of the active set and one batched launch sequence
+        S->all_periodic_x = true;
+        for (const Active& a : S->active) S->all_periodic_x = S->all_periodic_x && a.req.grid.bcx == LB_BC_PERIODIC;
         int tx = 32, ty = 16;
-        tile_shape(S->prec, S->thermal != 0, &tx, &ty);
+        if (!paired(S)) tile_shape(S->prec, S->thermal != 0, &tx, &ty);
+        auto tiles_of = [&](const Active& a) {
+            return ((a.req.grid.nx + tx - 1) / tx) * ((a.req.grid.ny + ty - 1) / ty);
+        };
+        // which requests take steps this pump
+        std::vector<int> order(S->active.size());
+        for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+        std::vector<char> run(S->active.size(), 1);
+        if (S->policy == LB_SERVE_SHORTEST) {
+            // least remaining work first, within about two waves of CTAs
+            std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+                const Active &p = S->active[x], &q = S->active[y];
+                return (double)p.req.grid.nx * p.req.grid.ny * p.remaining <
+                       (double)q.req.grid.nx * q.req.grid.ny * q.remaining;
+            });
+            const int target = 2 * S->sms * (S->thermal ? 1 : 2);
+            int sum = 0;
+            for (size_t j = 0; j < order.size(); ++j) {
+                const int t = tiles_of(S->active[order[j]]);
+                run[order[j]] = (j == 0 || sum + t <= target) ? 1 : 0;
+                if (run[order[j]]) sum += t;
+            }
+        }
         int ntiles = 0;
-        for (const Active& a : S->active)
-            ntiles += ((a.req.grid.nx + tx - 1) / tx) * ((a.req.grid.ny + ty - 1) / ty);
+        for (size_t i = 0; i < S->active.size(); ++i)
+            if (run[i]) ntiles += tiles_of(S->active[i]);
         lb_status st = ensure_capacity(S, (int)S->active.size(), ntiles);
         if (st != LB_OK) return st;
         int b = 0;
@@ -293,6 +333,7 @@ lb_status lb_server_pump(lb_server* S, int* n_active, int* n_pending) {
             const Active& a = S->active[i];
             if (S->prec == Prec::F64) fill_req<double>(S, i, a);
             else fill_req<float>(S, i, a);
+            if (!run[i]) continue;
             const int nbx = (a.req.grid.nx + tx - 1) / tx, nby = (a.req.grid.ny + ty - 1) / ty;
             for (int y = 0; y < nby; ++y)
                 for (int x = 0; x < nbx; ++x) S->h_tiles[b++] = make_int4(i, x, y, 0);
@@ -306,8 +347,12 @@ lb_status lb_server_pump(lb_server* S, int* n_active, int* n_pending) {
         cudaError_t e = cudaStreamSynchronize(S->stream);
         if (e != cudaSuccess) return fail(LB_ERR_CUDA, std::string("server step: ") + cudaGetErrorString(e));
         // 3. bookkeeping and retirement
-        for (size_t i = 0; i < S->active.size();) {
+        for (size_t i = 0, j = 0; i < S->active.size(); ++j) {
             Active& a = S->active[i];
+            if (!run[j]) {
+                ++i;
+                continue;
+            }
             const int taken = a.remaining < S->K ? a.remaining : S->K;
             a.remaining -= taken;
             a.done += taken;

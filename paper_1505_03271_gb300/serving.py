@@ -66,10 +66,11 @@ def _percentiles(x):
     return float(np.percentile(x, 50)), float(np.percentile(x, 99))
 
 
-def run_server(lb, requests, store=LB_STORE_F16DEV, steps_per_launch=50, hbm_budget=200 << 30):
+def run_server(lb, requests, store=LB_STORE_F16DEV, steps_per_launch=50, hbm_budget=200 << 30, policy=None):
     """Submit each request at its arrival time (server clock), pump until all
     are done.  Returns per-request results and aggregate figures."""
-    s = lb.Server(store=store, thermal=True, hbm_budget=hbm_budget, steps_per_launch=steps_per_launch)
+    s = lb.Server(store=store, thermal=True, hbm_budget=hbm_budget, steps_per_launch=steps_per_launch,
+                  policy=policy)
     pending = list(requests)
     results = {}
     t_start = s.clock()

@@ -450,3 +450,29 @@ def test_deterministic(lbgpu):
     assert np.array_equal(outs[0][0][0], outs[1][0][0])
     assert np.array_equal(outs[0][0][1], outs[1][0][1])
     assert outs[0][1] == outs[1][1]
+
+
+@pytest.mark.parametrize("scheme", ["st", "fv"])
+def test_rb_ra1e4_nusselt_gpu(lbgpu, scheme):
+    """Sec. IV: Ra = 1e4, Pr = 1, Ar = 2.02 reaches Nu ~= 2.66; ST on the
+    uniform lattice and FV on a tanh-refined grid (delta = 1.5), H = 64, FP32."""
+    import os
+    from paper_1505_03271_gb300 import configs as cfg
+    path = os.path.join(os.path.dirname(__file__), "golden", "rb_ra1e4.txt")
+    Ra, Pr, Ar, Nu_ref, tol = [float(v) for v in
+                               [l for l in open(path) if l.strip() and not l.startswith("#")][0].split()]
+    H = 64
+    nx = int(round(Ar * H))
+    p = cfg.rb_params(Ra, Pr, float(H))
+    if scheme == "st":
+        g = lbgpu.Grid(nx, H, bcy=1, thermal=True, store="f32")
+        dt = 1.0
+    else:
+        g = lbgpu.Grid(nx, H, sy=1, stretch_y=1.5, bcy=1, thermal=True, store="f32")
+        dt = cfg.fv_dt(cfg.min_cell(H, float(H), 1, 1.5), min(p.tau, p.tau_g))
+    g.init(tau=p.tau, dt=dt, tau_g=p.tau_g, beta=p.beta, grav=p.grav, T0=p.T0, T_bot=p.T_bot,
+           T_top=p.T_top, kind=lbgpu.LB_INIT_RB, amp=1e-2, seed=3)
+    steps = int(0.9 * H * H / p.kappa / dt)
+    (g.step_st if scheme == "st" else g.step_fv)(steps)
+    for nu in g.nusselt():
+        assert abs(nu - Nu_ref) < tol, g.nusselt()

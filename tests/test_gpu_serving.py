@@ -31,7 +31,8 @@ def _alone_on_grid(lb, req, store):
     gk = {k: kw.pop(k) for k in list(kw) if k in grid_keys}
     g = lb.Grid(thermal=True, store=store, **gk)
     g.init(kind=lb.LB_INIT_RB, **kw)
-    g.set_fv_schedule(lb.LB_FV_TILE)
+    # the server's batched kernels use the (paired) tile decomposition
+    g.set_fv_schedule(lb.LB_FV_PTILE if store != "f64" else lb.LB_FV_TILE)
     g.step_fv(nsteps)
     return g.nusselt(), g.conservation()[0]
 
@@ -48,11 +49,12 @@ def _drain(server):
             return out
 
 
+@pytest.mark.parametrize("policy", [0, 1], ids=["share", "shortest"])
 @pytest.mark.parametrize("store", ["f32", "f16dev"])
-def test_alone_equals_mix(lbgpu, store):
+def test_alone_equals_mix(lbgpu, store, policy):
     lb = lbgpu
     reqs = _requests()
-    mix = lb.Server(store=store, thermal=True, steps_per_launch=8)
+    mix = lb.Server(store=store, thermal=True, steps_per_launch=8, policy=policy)
     for r in reqs:
         mix.submit(**r)
     got = _drain(mix)

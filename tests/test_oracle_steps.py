@@ -281,3 +281,31 @@ def test_rb_preset_perturbation_is_seeded(oracle):
         for i in range(4):
             U = oracle.splitmix_uniform(1234, j * 4 + i)
             assert np.isclose(T[j, i], 1.0 + (0.5 - yc[j] / 6) + 1e-3 * (2 * U - 1), rtol=0, atol=1e-15)
+
+
+def _golden_rb():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "rb_ra1e4.txt")
+    for line in open(path):
+        if line.strip() and not line.startswith("#"):
+            Ra, Pr, Ar, Nu, tol = map(float, line.split())
+            return Ra, Pr, Ar, Nu, tol
+
+
+def test_rb_ra1e4_nusselt(oracle):
+    """Sec. IV: 2-D Rayleigh-Benard at Ra = 1e4, Pr = 1, Ar = 2.02 settles on a
+    steady roll pair with Nu ~= 2.66 (the Clever & Busse value the paper
+    compares to).  ST oracle, H = 32, 0.9 diffusive times; every Nusselt
+    number (volume, both plates) within the stated tolerance."""
+    from paper_1505_03271_gb300 import configs as cfg
+    Ra, Pr, Ar, Nu_ref, tol = _golden_rb()
+    H = 32
+    nx = int(round(Ar * H))
+    p = cfg.rb_params(Ra, Pr, float(H))
+    g = oracle.RefGrid(nx, H, lx=float(nx), ly=float(H), bcy=oracle.WALLS, thermal=True)
+    g.set_params(tau=p.tau, dt=1.0, tau_g=p.tau_g, beta=p.beta, grav=p.grav, T0=p.T0, T_bot=p.T_bot,
+                 T_top=p.T_top)
+    g.init_preset(oracle.INIT_RB, amp=1e-2, seed=3)
+    g.step_st(int(0.9 * H * H / p.kappa))
+    for nu in g.nusselt():
+        assert abs(nu - Nu_ref) < tol, g.nusselt()
