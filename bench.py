@@ -176,6 +176,18 @@ def measured_traffic(schedule, case):
         return None
 
 
+def aggregate(local_s, cells, steps, world, dist=None, device="cpu"):
+    """Whole-job throughput of independent replicas (one per rank): the
+    slowest rank's time bounds the job, every rank did cells x steps."""
+    import torch
+    total_s = local_s
+    if dist is not None and world > 1:
+        t = torch.tensor([local_s], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    return total_s, cells * steps * world / total_s / 1e6
+
+
 def roofline(bytes_per_step, mean_ms, peak, peak_kind, traffic=None):
     achieved = bytes_per_step / (mean_ms * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
@@ -406,13 +418,8 @@ def main():
     with ClockSampler(gpu_index) as clk:
         ms, launches = time_steps(lb, torch, g, w.scheme, args.steps, args.warmup, flush)
     barrier()
-    total_s = sum(ms) * 1e-3
-    if dist is not None:
-        t = torch.tensor([total_s], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s, value = aggregate(sum(ms) * 1e-3, w.cells, args.steps, world, dist, "cuda")
     mean_ms = total_s * 1e3 / args.steps
-    value = w.cells * args.steps * world / total_s / 1e6
     bpc = cfg.bytes_per_cell(w.grid["store"], w.grid.get("thermal", False))
     dtype = "f64" if w.grid["store"] == lb.LB_STORE_F64 else "f32"
     line = {"metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world,

@@ -96,6 +96,34 @@ __global__ void __launch_bounds__(256) k_st_pair(const StepArgs<float> A) {
     const float ro = A.roff[y], to = TH ? A.toff[y] : 0.0f;
     PairCell<TH> m;
     m.build(d, e, A, ro, to);
+    // Interior pairs (both cells and all their neighbours inside the grid)
+    // stream to fixed offsets with no wrap or wall test.
+    if (x >= 1 && x + 2 < A.nx && y >= 1 && y + 1 < A.ny) {
+        const float rdn = A.roff[y - 1], rup = A.roff[y + 1];
+        const float tdn = TH ? A.toff[y - 1] : 0.0f, tup = TH ? A.toff[y + 1] : 0.0f;
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const float w = wgt<float>(a);
+            const float rt = cy(a) > 0 ? rup : (cy(a) < 0 ? rdn : ro);
+            const float tt = cy(a) > 0 ? tup : (cy(a) < 0 ? tdn : to);
+            const V2 post = fma2(bc(A.om), m.feqd[a] - d[a], fma2(bc(A.cf), m.F[a], d[a])) + bc(w * (ro - rt));
+            V2 gpost = bc(0.0f);
+            if (TH) gpost = fma2(bc(A.omg), m.geqd[a] - e[a], e[a]) + bc(w * (to - tt));
+            const long long o = a * A.plane + c + (long long)cy(a) * A.pitch + cx(a);
+            if (cx(a) == 0) {
+                PairIO<S>::st(fout + o, post);
+                if (TH) PairIO<S>::st(gout + o, gpost);
+            } else {
+                Store<S>::st(fout + o, post.v.x);
+                Store<S>::st(fout + o + 1, post.v.y);
+                if (TH) {
+                    Store<S>::st(gout + o, gpost.v.x);
+                    Store<S>::st(gout + o + 1, gpost.v.y);
+                }
+            }
+        }
+        return;
+    }
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
         const V2 post = fma2(bc(A.om), m.feqd[a] - d[a], fma2(bc(A.cf), m.F[a], d[a]));
