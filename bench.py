@@ -201,7 +201,8 @@ def extra_lines(lb, torch, cfg, stream, peak, peak_kind, flush):
              ("st8192_bf16dev", cfg.st_sweep(8192, lb.LB_STORE_BF16DEV), 20, None, None),
              ("st8192_f16dev", cfg.st_sweep(8192, lb.LB_STORE_F16DEV), 20, None, None),
              ("fv4096_f32", _fv_big(cfg, 4096), 10, None, None),
-             ("fv_rb1024_f16dev", cfg.rayleigh_benard(1024, 1e8), 20, flush, "rb1024")]
+             ("fv_rb1024_f16dev", cfg.rayleigh_benard(1024, 1e8), 20, flush, "rb1024"),
+             ("fv_rb1024_f32", cfg.rayleigh_benard(1024, 1e8, store=lb.LB_STORE_F32), 20, flush, None)]
     for name, w, k, fl, case in specs:
         g = make_grid(lb, w, stream)
         ms, _ = time_steps(lb, torch, g, w.scheme, k, 3, fl)
