@@ -134,7 +134,7 @@ def schedule_name(lb, g, scheme):
     if k == lb.LB_FV_TILE:
         return "fv tile %s (halo 4)" % {0: "32x16", 16: "16x16", 8: "16x8"}[c]
     if k == lb.LB_FV_PTILE:
-        return "fv pair-tile (f32x2) %s (halo 4)" % {0: "32x16", 16: "16x16"}[c]
+        return "fv pair-tile (f32x2) %s (halo 4)" % {0: "32x16", 16: "16x16", 512: "32x16, 512 threads"}[c]
     return ("fv pair-march (f32x2)" if k == lb.LB_FV_PAIR else "fv march") + ", %d rows per CTA" % c
 
 
@@ -195,6 +195,20 @@ def roofline(bytes_per_step, mean_ms, peak, peak_kind, traffic=None):
             "peak_source": f"{peak_kind} hbm_gbs"}
 
 
+def alu_roofline(cfg, w, mean_ms, clocks):
+    """The second roof of the step: algorithmic FP32 flops per second
+    against the non-tensor FP32 peak at the GPU's maximum SM clock."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz = (clocks or {}).get("sm_max_mhz") or 2070.0
+    fpc = cfg.flops_per_cell(w.scheme, w.grid.get("thermal", False))
+    achieved = fpc * w.cells / (mean_ms * 1e-3) / 1e12
+    peak = cfg.fp32_peak_tflops(sms, mhz)
+    return {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak, 2), "unit": "TFLOP/s",
+            "frac": round(achieved / peak, 4), "flops_per_cell": fpc,
+            "peak_source": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (derived)" % (sms, mhz)}
+
+
 def extra_lines(lb, torch, cfg, stream, peak, peak_kind, flush):
     out = {}
     specs = [("st8192_f32", cfg.st_sweep(8192, lb.LB_STORE_F32), 20, None, None),
@@ -213,6 +227,7 @@ def extra_lines(lb, torch, cfg, stream, peak, peak_kind, flush):
                      "bytes_per_cell": bpc, "schedule": sched,
                      "roofline": roofline(bpc * w.cells, mean, peak, peak_kind,
                                           measured_traffic(sched, case) if case else None),
+                     "roofline_alu": alu_roofline(cfg, w, mean, None),
                      "cells": w.cells, "l2": "flushed" if fl is not None else "state > L2"}
         g.close()
         torch.cuda.empty_cache()
@@ -430,6 +445,7 @@ def main():
             "roofline": roofline(bpc * w.cells, mean_ms, peak, peak_kind,
                                  measured_traffic(schedule_name(lb, g, w.scheme), args.case)),
             "clocks": clk.summary()}
+    line["roofline_alu"] = alu_roofline(cfg, w, mean_ms, line["clocks"])
     line["config"]["parallelism"] = "replicas" if world > 1 else "single"
     line["config"]["schedule"] = schedule_name(lb, g, w.scheme)
     if not args.no_extra and args.case == "channel":

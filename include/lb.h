@@ -142,7 +142,9 @@ lb_status lb_step_st(lb_grid* grid, int nsteps);
  *                grids only (LB_ERR_ARG otherwise);
  *   LB_FV_PTILE: the tiles with two columns per thread-cell and packed FP32
  *                pair arithmetic (same restrictions); chunk 0 = 32 x 16,
- *                16 = 16 x 16.
+ *                16 = 16 x 16, 512 = 32 x 16 with 512 threads per CTA
+ *                (one pass per stage; the corrector splits each cell's
+ *                populations over two threads).
  * LB_FV_AUTO picks by grid size.  For the marching kernels chunk = 0 lets
  * the library size the chunks to fill the GPU; for LB_FV_TILE chunk picks
  * the tile: 0 = 32 x 16, 16 = 16 x 16, 8 = 16 x 8 (smaller tiles recompute

@@ -146,6 +146,41 @@ def st_sweep(n: int = 8192, store: int = LB_STORE_F32, steps: int = 500) -> Work
                     dict(kind=LB_INIT_TGV, u0=0.01, amp=0.01, mode=2), steps, "st")
 
 
+def flops_per_cell(scheme: str, thermal: bool) -> int:
+    """Algorithmic FP32 operations per cell update (an FMA counts 2), from
+    the formulas the step evaluates, each shared subexpression once and
+    each QUICK face once (a face belongs to two cells).  Halo recomputation
+    in the kernels is not counted.
+
+    Per evaluation of the cell macro routine (Sec. II, Eq. (F2)):
+      moments rho, j (18), 1/rho (1), u = j/rho + dt/2 a (4)            23
+      equilibrium: u^2 (3), c.u of the diagonals (4), 1 - 1.5u^2 (2),
+        w rho (3), 5 per moving population, 1 for the rest one          53
+      Guo force: u.a (3), 6 per moving population, 1 for the rest one   52
+      advected field h = f + dt/(2 tau~)(f_eq - f) + dt/2 F, 5 x 9       45
+      f + Coll (reusing f_eq - f), 4 x 9 (only at time level n)         36
+    Per flux evaluation (Eq. (fv), Sec. II B 3): 12 face values (6
+    populations move in x, 6 in y) of 5 each = 60; 12 differences scaled
+    by 1/dx (2 each) and 4 sums for the diagonals = 28.
+    FV (Eq. (semi-heun)): 209 + 88 + 16 (predictor) + 173 + 88 + 24
+    (corrector) = 598.  The thermal populations add T (8), the buoyant
+    a_y (2), g_eq = (T/rho) f_eq (10), h^g (27), g + Coll_g (18) at time
+    level n, the same less Coll_g at the starred level (47), two more
+    flux evaluations (176) and the two updates (40): 328, so 926.
+    ST (Eq. (ST)): moments, equilibrium, force and the post-collision
+    value f + (f_eq - f)/tau~ + (1 - 1/(2 tau~)) F (45) = 173; thermal adds
+    T, a_y, g_eq and the g collision (47): 220."""
+    if scheme == "fv":
+        return 926 if thermal else 598
+    return 220 if thermal else 173
+
+
+def fp32_peak_tflops(sms: int, sm_mhz: float) -> float:
+    """Non-tensor FP32 peak: 128 FP32 lanes per SM, one FMA (2 flops) per
+    lane per clock."""
+    return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
 def bytes_per_cell(store: int, thermal: bool) -> int:
     """Compulsory HBM bytes per cell update: every population read and
     written once (9 or 18 populations)."""

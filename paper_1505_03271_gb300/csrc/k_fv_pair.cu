@@ -380,6 +380,19 @@ __device__ __forceinline__ void advect_region_all(const V2* P, int px, int y, co
     if constexpr (a + 1 < Q) advect_region_all<TH, NQ, H, W, a + 1>(P, px, y, X, Y, out);
 }
 
+// The populations i (0..NQ-1; i >= Q are thermal) whose bit is set in M,
+// for a corrector split over two threads per pair-cell.
+template <bool TH, int H, int W, unsigned M, int i>
+__device__ __forceinline__ void advect_region_mask(const V2* P, int px, int y, const XPair& X, const YPair& Y,
+                                                   V2* out) {
+    constexpr int NQ = TH ? 2 * Q : Q;
+    if constexpr ((M >> i) & 1u) {
+        constexpr int a = i < Q ? i : i - Q;
+        out[i] = advect_region<a>(P + i * H * W, W, px, y, X, Y) + bc(row_ref_flux<a>(Y, i >= Q));
+    }
+    if constexpr (i + 1 < NQ) advect_region_mask<TH, H, W, M, i + 1>(P, px, y, X, Y, out);
+}
+
 // Ghost rows of a region (walls on y), own pair-columns: h'_a = h'_inv(a)
 // for f, -h'_inv(a) for g.
 template <bool TH, int NQ, int H, int W>
@@ -398,6 +411,30 @@ __device__ __forceinline__ void ghost_rows_region(V2* P, int gy0, const StepArgs
             P[(a * H + ey) * W + px] = P[(inv(a) * H + eys) * W + px];
             if constexpr (TH) P[((Q + a) * H + ey) * W + px] = bc(0.0f) - P[((Q + inv(a)) * H + eys) * W + px];
         }
+    }
+}
+
+// Corrector output of the populations in M at tile pair-cell (tx, ty):
+// f~^(n+1) = (f~ + Coll - dt/2 A[h^n]) - dt/2 A[h*].
+template <typename S, bool TH, int BH, int BW, unsigned M>
+__device__ __forceinline__ void corrector_write(const V2* sHs, const V2* sFC, int tx, int ty, int gx, int gy,
+                                                const XPair& X, const YPair& Y, const StepArgs<float>& A) {
+    constexpr int NQ = TH ? 2 * Q : Q;
+    constexpr int NB = BW * BH;
+    V2 adv[NQ];
+    advect_region_mask<TH, BH, BW, M, 0>(sHs, tx + 1, ty + 2, X, Y, adv);
+    const int kb = (ty + 2) * BW + tx + 1;
+    const long long row = (long long)gy * A.pitch;
+    const bool both = gx + 1 < A.nx;
+    S* fout = static_cast<S*>(A.fout);
+    S* gout = static_cast<S*>(A.gout);
+#pragma unroll
+    for (int a = 0; a < NQ; ++a) {
+        if (!((M >> a) & 1u)) continue;
+        const V2 o = fma2(bc(-A.hf), adv[a], sFC[a * NB + kb]);
+        S* base = (a < Q ? fout + a * A.plane : gout + (a - Q) * A.plane) + row;
+        if (both) PairIO<S>::st(base + gx, o);
+        else Store<S>::st(base + gx, o.v.x);
     }
 }
 
@@ -494,33 +531,34 @@ __device__ __forceinline__ void ptile_body(const StepArgs<float>& A, const int x
     __syncthreads();
 
     // ---- corrector on the tile ----
-    S* fout = static_cast<S*>(A.fout);
-    S* gout = static_cast<S*>(A.gout);
-    for (int k = threadIdx.x; k < TW * TY; k += NTH) {
-        const int tx = k % TW, ty = k / TW;
+    // With at least two threads per tile pair-cell the populations are split
+    // between them: every corrector population is independent of the others.
+    // Flow: {0, 1, 2, 5, 6} and {3, 4, 7, 8} (two axis and two diagonal
+    // fluxes each); thermal: the nine f and the nine g.
+    constexpr bool SPLIT = NTH >= 2 * TW * TY;
+    constexpr unsigned ALL = (1u << NQ) - 1u;
+    constexpr unsigned HALF0 = TH ? 0x1FFu : 0x67u;
+    for (int k = threadIdx.x; k < (SPLIT ? 2 : 1) * TW * TY; k += NTH) {
+        const int kp = SPLIT ? k % (TW * TY) : k;
+        const int tx = kp % TW, ty = kp / TW;
         const int gx = x0 + 2 * tx, gy = y0 + ty;
         if (gx >= nx || gy >= A.ny) continue;
         XPair X;
         load_col(A.coltab, gx, X);
         YPair Y;
         load_row(A.rowtab, gy, Y);
-        V2 adv[NQ];
-        advect_region_all<TH, NQ, BH, BW, 0>(sHs, tx + 1, ty + 2, X, Y, adv);
-        const int kb = (ty + 2) * BW + tx + 1;
-        const long long row = (long long)gy * A.pitch;
-        const bool both = gx + 1 < nx;
-#pragma unroll
-        for (int a = 0; a < NQ; ++a) {
-            const V2 o = fma2(bc(-A.hf), adv[a], sFC[a * NB + kb]);
-            S* base = (a < Q ? fout + a * A.plane : gout + (a - Q) * A.plane) + row;
-            if (both) PairIO<S>::st(base + gx, o);
-            else Store<S>::st(base + gx, o.v.x);
+        if (!SPLIT) {
+            corrector_write<S, TH, BH, BW, ALL>(sHs, sFC, tx, ty, gx, gy, X, Y, A);
+        } else if (k < TW * TY) {
+            corrector_write<S, TH, BH, BW, HALF0>(sHs, sFC, tx, ty, gx, gy, X, Y, A);
+        } else {
+            corrector_write<S, TH, BH, BW, ALL & ~HALF0>(sHs, sFC, tx, ty, gx, gy, X, Y, A);
         }
     }
 }
 
-template <typename S, bool TH, int TX, int TY, int NTH>
-__global__ void __launch_bounds__(NTH) k_fv_ptile(const StepArgs<float> A) {
+template <typename S, bool TH, int TX, int TY, int NTH, int MINB>
+__global__ void __launch_bounds__(NTH, MINB) k_fv_ptile(const StepArgs<float> A) {
     ptile_body<S, TH, TX, TY, NTH>(A, blockIdx.x * TX, blockIdx.y * TY);
 }
 
@@ -578,7 +616,7 @@ cudaError_t launch_fv_ptile_batched(Prec p, bool th, const void* reqs, const int
     }
 }
 
-template <typename S, bool TH, int TX, int TY, int NTH>
+template <typename S, bool TH, int TX, int TY, int NTH, int MINB>
 static cudaError_t run_ptile(const void* vargs, cudaStream_t s) {
     const StepArgs<float>& A = *static_cast<const StepArgs<float>*>(vargs);
     constexpr int NQ = TH ? 2 * Q : Q;
@@ -586,21 +624,22 @@ static cudaError_t run_ptile(const void* vargs, cudaStream_t s) {
     static_assert(smem <= 232448, "shared memory per CTA");
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_fv_ptile<S, TH, TX, TY, NTH>,
+        cudaError_t e = cudaFuncSetAttribute(k_fv_ptile<S, TH, TX, TY, NTH, MINB>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
     dim3 grid((A.nx + TX - 1) / TX, (A.ny + TY - 1) / TY);
-    k_fv_ptile<S, TH, TX, TY, NTH><<<grid, NTH, smem, s>>>(A);
+    k_fv_ptile<S, TH, TX, TY, NTH, MINB><<<grid, NTH, smem, s>>>(A);
     count_launch();
     return cudaGetLastError();
 }
 
 template <typename S, bool TH>
 static cudaError_t run_ptile_shape(const void* args, int shape, cudaStream_t s) {
-    if (shape == 16) return run_ptile<S, TH, 16, 16, 128>(args, s);
-    return run_ptile<S, TH, 32, 16, 256>(args, s);
+    if (shape == 16) return run_ptile<S, TH, 16, 16, 128, 1>(args, s);
+    if (shape == 512) return run_ptile<S, TH, 32, 16, 512, TH ? 1 : 2>(args, s);
+    return run_ptile<S, TH, 32, 16, 256, 1>(args, s);
 }
 
 cudaError_t launch_fv_ptile(Prec p, bool th, const void* args, int shape, cudaStream_t s) {

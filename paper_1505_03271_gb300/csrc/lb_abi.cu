@@ -443,8 +443,8 @@ lb_status lb_set_fv_schedule(lb_grid* G, int kernel, int chunk) {
     if (chunk < 0) return fail(LB_ERR_ARG, "chunk must be >= 0");
     if (kernel == LB_FV_TILE && chunk != 0 && chunk != 8 && chunk != 16)
         return fail(LB_ERR_ARG, "tile shape must be 0 (32 x 16), 16 (16 x 16) or 8 (16 x 8)");
-    if (kernel == LB_FV_PTILE && chunk != 0 && chunk != 16)
-        return fail(LB_ERR_ARG, "paired tile shape must be 0 (32 x 16) or 16 (16 x 16)");
+    if (kernel == LB_FV_PTILE && chunk != 0 && chunk != 16 && chunk != 512)
+        return fail(LB_ERR_ARG, "paired tile shape must be 0 (32 x 16), 16 (16 x 16) or 512 (32 x 16, 512 threads)");
     if ((kernel == LB_FV_PAIR || kernel == LB_FV_PTILE) && !pair_ok(G))
         return fail(LB_ERR_ARG, "the paired FV kernel needs FP32/FP16/BF16 storage and a periodic x axis");
     G->fv_kernel = kernel;
@@ -482,6 +482,7 @@ lb_status lb_autotune_fv(lb_grid* G, int steps) {
     if (pair_ok(G)) {
         cands.push_back({LB_FV_PTILE, 0});
         cands.push_back({LB_FV_PTILE, 16});
+        cands.push_back({LB_FV_PTILE, 512});
     }
     for (int kern : {(int)LB_FV_MARCH, (int)LB_FV_PAIR}) {
         if (kern == LB_FV_PAIR && !pair_ok(G)) continue;
