@@ -50,8 +50,16 @@ typedef enum {
     LB_ERR_TIMEOUT = 6   /* a bounded device-side wait gave up                  */
 } lb_status;
 
-typedef enum { LB_AXIS_UNIFORM = 0, LB_AXIS_TANH = 1, LB_AXIS_SINH = 2 } lb_spacing;
-typedef enum { LB_BC_PERIODIC = 0, LB_BC_WALLS = 1 } lb_bc;
+/* Face spacing of an axis, Eq. (grids) of Sec. III B: uniform; tanh with
+ * stretch delta (s1 = tanh delta); sinh with stretch s2 (even n); Chebyshev
+ * faces xi_i = L/2 (1 - cos(i pi / n)) (stretch unused). */
+typedef enum { LB_AXIS_UNIFORM = 0, LB_AXIS_TANH = 1, LB_AXIS_SINH = 2, LB_AXIS_CHEB = 3 } lb_spacing;
+/* Boundary of an axis (both ends): periodic; no-slip walls (double
+ * reflection, Sec. II B 5); or fixed density, where the ghost density is
+ * extrapolated linearly through the imposed face value from the node it
+ * mirrors and the ghost populations are that node's rescaled by the density
+ * ratio (Sec. II B 5; FV on flow grids only, see lb_set_boundary_density). */
+typedef enum { LB_BC_PERIODIC = 0, LB_BC_WALLS = 1, LB_BC_DENSITY = 2 } lb_bc;
 typedef enum {
     LB_STORE_F64 = 0,    /* FP64 storage, FP64 arithmetic                      */
     LB_STORE_F32 = 1,    /* FP32 storage of f - w (and g - w T0), FP32 math    */
@@ -154,6 +162,31 @@ typedef enum { LB_FV_AUTO = 0, LB_FV_TILE = 1, LB_FV_MARCH = 2, LB_FV_PAIR = 3, 
 lb_status lb_set_fv_schedule(lb_grid* grid, int kernel, int chunk);
 /* The schedule lb_step_fv will use now (after AUTO has been resolved). */
 lb_status lb_get_fv_schedule(lb_grid* grid, int* kernel, int* chunk);
+
+/* FV time integration (Sec. II B 2).  LB_FV_HEUN (default) is the
+ * semi-implicit collision with the Heun predictor-corrector on the
+ * advection, Eq. (semi-heun).  LB_FV_SEMI stops after the predictor,
+ * Eq. (semi).  LB_FV_EULER is explicit Euler on the plain populations with
+ * the physical tau, Eq. (euler): the advected field is f itself, the source
+ * dt/tau (f_eq - f) + dt F, and the moments carry no dt/2 a shift.
+ * The scheme fixes what the state holds (tilded populations, or plain ones
+ * for Euler), so setting a different scheme on an initialised grid returns
+ * it to the uninitialised state: steps return LB_ERR_STATE until the next
+ * lb_init, which then starts from the scheme's equilibrium.  The two
+ * single-stage schemes run on the scalar tile kernel whatever the schedule;
+ * lb_step_st on an Euler grid returns LB_ERR_STATE.  LB_ERR_ARG on an unknown
+ * scheme. */
+typedef enum { LB_FV_HEUN = 0, LB_FV_SEMI = 1, LB_FV_EULER = 2 } lb_fv_scheme;
+
+/* Densities imposed on the faces of LB_BC_DENSITY axes (Sec. II B 5):
+ * x = 0, x = L_x, y = 0, y = L_y (each > 0; default 1; values for periodic
+ * or wall axes are ignored).  They apply from the next FV step on; any time
+ * after lb_create_grid.  Grids with a density axis step on the scalar tile
+ * kernel whatever the schedule, and lb_step_st returns LB_ERR_ARG on them.
+ * LB_ERR_ARG on a non-positive density. */
+lb_status lb_set_boundary_density(lb_grid* grid, double rho_x0, double rho_x1, double rho_y0, double rho_y1);
+lb_status lb_set_fv_scheme(lb_grid* grid, int scheme);
+lb_status lb_get_fv_scheme(lb_grid* grid, int* scheme);
 
 /* Autotuner: times `steps` FV steps for each candidate schedule (tile; march
  * and pair with several chunk lengths) on the grid's current state, restores the

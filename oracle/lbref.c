@@ -62,6 +62,8 @@ struct ref_grid {
     double *fs, *gs;       /* starred (predictor) state                   */
     double *fn, *gn;       /* next state                                  */
     double *scr, *scrg;    /* collision of the starred state (unused)     */
+    int scheme;            /* REF_FV_HEUN / REF_FV_SEMI / REF_FV_EULER     */
+    double rho_bc[4];      /* imposed densities: x0, x1, y0, y1             */
 };
 
 /* ------------------------------------------------------------------ */
@@ -80,7 +82,10 @@ void ref_lattice(int* cx, int* cy, double* w, int* inv) {
 /* Face coordinates xi_0..xi_n of one axis, Eq. (grids) of Sec. III B.
  * tanh: xi_i = L/2 (1 + tanh[(2i/n - 1) delta] / tanh(delta)), which is the
  * paper's formula with s1 = tanh(delta); "stretch" is delta.
- * sinh: the paper's two branches with s2 = stretch (n even). */
+ * sinh: the paper's two branches with s2 = stretch (n even).
+ * Chebyshev: xi_i = L/2 (1 - cos(i pi / n)).  The paper's formula, with
+ * (i - 1/2) in place of i, puts neither xi_0 nor xi_n on a wall; these are
+ * the Chebyshev-Gauss-Lobatto points, which do. */
 void ref_faces(int n, double L, int spacing, double stretch, double* xi) {
     for (int i = 0; i <= n; ++i) {
         double v;
@@ -92,6 +97,8 @@ void ref_faces(int n, double L, int spacing, double stretch, double* xi) {
                 v = A * sinh(stretch * i / n);
             else
                 v = L - A * sinh(stretch * (double)(n - i) / n);
+        } else if (spacing == REF_CHEB) {
+            v = 0.5 * L * (1.0 - cos(3.14159265358979323846 * i / n));
         } else {
             v = L * i / n;
         }
@@ -196,13 +203,16 @@ static void build_axis(int n, double L, int sp, double st, int bc, double** xi, 
 
 ref_grid* ref_create(const ref_desc* d) {
     if (!d || d->nx < 1 || d->ny < 1) return NULL;
-    if (d->bcx == REF_WALLS && d->nx < 2) return NULL;
-    if (d->bcy == REF_WALLS && d->ny < 2) return NULL;
-    if (d->thermal && d->bcx == REF_WALLS) return NULL; /* isothermal walls are on y only */
+    if (d->bcx != REF_PERIODIC && d->nx < 2) return NULL;
+    if (d->bcy != REF_PERIODIC && d->ny < 2) return NULL;
+    if (d->bcx < REF_PERIODIC || d->bcx > REF_DENSITY || d->bcy < REF_PERIODIC || d->bcy > REF_DENSITY) return NULL;
+    if (d->thermal && d->bcx != REF_PERIODIC) return NULL; /* isothermal walls are on y only */
+    if (d->thermal && d->bcy == REF_DENSITY) return NULL;
     if (d->sx == REF_SINH && (d->nx % 2)) return NULL;
     if (d->sy == REF_SINH && (d->ny % 2)) return NULL;
     ref_grid* G = (ref_grid*)calloc(1, sizeof(ref_grid));
     G->d = *d;
+    for (int k = 0; k < 4; ++k) G->rho_bc[k] = 1.0;
     G->nx = d->nx;
     G->ny = d->ny;
     build_axis(d->nx, d->lx, d->sx, d->stretch_x, d->bcx, &G->xi_x, &G->xc, &G->dx, &G->posx);
@@ -272,8 +282,10 @@ static void macro(const ref_grid* G, const double* fc, const double* gc, double*
     *T = t;
     *ax = fx;
     *ay = fy;
-    *ux = jx / r + 0.5 * p->dt * fx;
-    *uy = jy / r + 0.5 * p->dt * fy;
+    /* the plain populations of the Euler scheme carry the momentum itself */
+    const double shift = G->scheme == REF_FV_EULER ? 0.0 : 0.5 * p->dt;
+    *ux = jx / r + shift * fx;
+    *uy = jy / r + shift * fy;
 }
 
 static void gather(const ref_grid* G, const double* src, int i, int j, double* out) {
@@ -301,8 +313,9 @@ int ref_init_fields(ref_grid* G, const double* rho, const double* ux, const doub
             double feq[Q], F[Q];
             ref_equilibrium(r, vx, vy, feq);
             ref_guo_force(r, vx, vy, fx, fy, F);
+            const double shift = G->scheme == REF_FV_EULER ? 0.0 : 0.5 * p->dt;
             for (int a = 0; a < Q; ++a) {
-                G->f[IDX(G, a, i, j)] = feq[a] - 0.5 * p->dt * F[a];
+                G->f[IDX(G, a, i, j)] = feq[a] - shift * F[a];
                 G->g[IDX(G, a, i, j)] = G->d.thermal ? (t / r) * feq[a] : 0.0;
             }
         }
@@ -390,6 +403,8 @@ int ref_step_st(ref_grid* G, int nsteps) {
     if (!G || !G->has_params || nsteps < 0) return -1;
     const ref_params* p = &G->p;
     if (fabs(p->dt - 1.0) > 1e-12) return -1;
+    if (G->scheme == REF_FV_EULER) return -1;
+    if (G->d.bcx == REF_DENSITY || G->d.bcy == REF_DENSITY) return -1; /* FV boundary only */
     if (!axis_uniform_unit(G->d.sx, G->nx, G->d.lx) || !axis_uniform_unit(G->d.sy, G->ny, G->d.ly))
         return -1;
     const int nx = G->nx, ny = G->ny, th = G->d.thermal;
@@ -480,6 +495,48 @@ static void fv_eval(ref_grid* G, const double* f, const double* gsrc, double* co
         }
 }
 
+/* Explicit Euler, Eq. (euler): the advected field is the population
+ * itself, h = f and hg = g, and the source is
+ *   coll = dt/tau (f_eq - f) + dt F,   collg = dt/tau_g (g_eq - g)
+ * with the physical relaxation times and the moments of the plain
+ * populations. */
+static void fv_eval_euler(ref_grid* G, const double* f, const double* gsrc, double* coll,
+                          double* collg) {
+    const ref_params* p = &G->p;
+    const double dt = p->dt;
+    const int th = G->d.thermal;
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < G->ny; ++j)
+        for (int i = 0; i < G->nx; ++i) {
+            double fc[Q], gc[Q], feq[Q], F[Q];
+            double rho, ux, uy, T, ax, ay;
+            gather(G, f, i, j, fc);
+            if (th) gather(G, gsrc, i, j, gc);
+            macro(G, fc, gc, &rho, &ux, &uy, &T, &ax, &ay);
+            ref_equilibrium(rho, ux, uy, feq);
+            ref_guo_force(rho, ux, uy, ax, ay, F);
+            for (int a = 0; a < Q; ++a) {
+                G->h[PIDX(G, a, i, j)] = fc[a];
+                coll[IDX(G, a, i, j)] = dt / p->tau * (feq[a] - fc[a]) + dt * F[a];
+                if (th) {
+                    G->hg[PIDX(G, a, i, j)] = gc[a];
+                    collg[IDX(G, a, i, j)] = dt / p->tau_g * ((T / rho) * feq[a] - gc[a]);
+                }
+            }
+        }
+}
+
+/* Fixed-density ghost (Sec. II B 5): the density at the ghost centre is
+ * extrapolated linearly through the imposed face value rho_S from the fluid
+ * node it mirrors, rho_g = 2 rho_S - rho_k, and the ghost takes that node's
+ * populations rescaled, h_a(ghost) = (rho_g / rho_k) h_a(node). */
+static void density_ghost(ref_grid* G, int i, int j, int gi, int gj, double rho_s) {
+    double rk = 0.0;
+    for (int a = 0; a < Q; ++a) rk += G->h[PIDX(G, a, i, j)];
+    const double s = (2.0 * rho_s - rk) / rk;
+    for (int a = 0; a < Q; ++a) G->h[PIDX(G, a, gi, gj)] = s * G->h[PIDX(G, a, i, j)];
+}
+
 /* Ghost cells of the padded advected fields (two per side, Sec. II B 5).
  * Periodic axes copy the opposite side.  Wall axes apply the double
  * reflection h_a(x_-k) = h_inv(a)(x_k); the thermal field is anti-reflected,
@@ -497,10 +554,16 @@ static void fv_ghosts(ref_grid* G) {
                         G->hg[PIDX(G, a, -k, j)] = G->hg[PIDX(G, a, il, j)];
                         G->hg[PIDX(G, a, nx - 1 + k, j)] = G->hg[PIDX(G, a, ir, j)];
                     }
-                } else {
+                } else if (G->d.bcx == REF_WALLS) {
                     G->h[PIDX(G, a, -k, j)] = G->h[PIDX(G, INV[a], k - 1, j)];
                     G->h[PIDX(G, a, nx - 1 + k, j)] = G->h[PIDX(G, INV[a], nx - k, j)];
                 }
+            }
+    if (G->d.bcx == REF_DENSITY)
+        for (int j = 0; j < ny; ++j)
+            for (int k = 1; k <= 2; ++k) {
+                density_ghost(G, k - 1, j, -k, j, G->rho_bc[0]);
+                density_ghost(G, nx - k, j, nx - 1 + k, j, G->rho_bc[1]);
             }
     for (int i = 0; i < nx; ++i)
         for (int k = 1; k <= 2; ++k) {
@@ -514,6 +577,9 @@ static void fv_ghosts(ref_grid* G) {
                         G->hg[PIDX(G, a, i, ny - 1 + k)] = G->hg[PIDX(G, a, i, jr)];
                     }
                 }
+            } else if (G->d.bcy == REF_DENSITY) {
+                density_ghost(G, i, k - 1, i, -k, G->rho_bc[2]);
+                density_ghost(G, i, ny - k, i, ny - 1 + k, G->rho_bc[3]);
             } else {
                 int jb = k - 1, jt = ny - k;
                 for (int a = 0; a < Q; ++a) {
@@ -569,6 +635,21 @@ static void fv_advect(const ref_grid* G, const double* hp, double* A) {
             }
 }
 
+int ref_set_boundary_density(ref_grid* G, double rho_x0, double rho_x1, double rho_y0, double rho_y1) {
+    if (!G || !(rho_x0 > 0) || !(rho_x1 > 0) || !(rho_y0 > 0) || !(rho_y1 > 0)) return -1;
+    G->rho_bc[0] = rho_x0;
+    G->rho_bc[1] = rho_x1;
+    G->rho_bc[2] = rho_y0;
+    G->rho_bc[3] = rho_y1;
+    return 0;
+}
+
+int ref_set_scheme(ref_grid* G, int scheme) {
+    if (!G || scheme < REF_FV_HEUN || scheme > REF_FV_EULER) return -1;
+    G->scheme = scheme;
+    return 0;
+}
+
 int ref_step_fv(ref_grid* G, int nsteps) {
     if (!G || !G->has_params || nsteps < 0) return -1;
     const double dt = G->p.dt;
@@ -576,14 +657,23 @@ int ref_step_fv(ref_grid* G, int nsteps) {
     const size_t N = (size_t)G->nx * G->ny * Q;
     for (int s = 0; s < nsteps; ++s) {
         /* time level n: h^n, Coll^n, A^n */
-        fv_eval(G, G->f, G->g, G->coll, G->collg);
+        if (G->scheme == REF_FV_EULER)
+            fv_eval_euler(G, G->f, G->g, G->coll, G->collg);
+        else
+            fv_eval(G, G->f, G->g, G->coll, G->collg);
         fv_ghosts(G);
         fv_advect(G, G->h, G->adv);
         if (th) fv_advect(G, G->hg, G->advg);
-        /* predictor f~* of Eq. (semi) */
+        /* predictor f~* of Eq. (semi); for Eq. (euler) the same update of
+         * the plain populations.  Both single-stage schemes end here. */
         for (size_t k = 0; k < N; ++k) {
             G->fs[k] = G->f[k] - dt * G->adv[k] + G->coll[k];
             if (th) G->gs[k] = G->g[k] - dt * G->advg[k] + G->collg[k];
+        }
+        if (G->scheme != REF_FV_HEUN) {
+            double* t = G->f; G->f = G->fs; G->fs = t;
+            t = G->g; G->g = G->gs; G->gs = t;
+            continue;
         }
         /* starred advected field h*, with its own moments and force */
         fv_eval(G, G->fs, G->gs, G->scr, G->scrg);

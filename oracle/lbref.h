@@ -24,14 +24,22 @@
 extern "C" {
 #endif
 
-enum { REF_UNIFORM = 0, REF_TANH = 1, REF_SINH = 2 };
-enum { REF_PERIODIC = 0, REF_WALLS = 1 };
+enum { REF_UNIFORM = 0, REF_TANH = 1, REF_SINH = 2, REF_CHEB = 3 };
+/* Axis boundaries: periodic; no-slip walls (double reflection, Sec. II B 5);
+ * fixed density at both faces of the axis (extrapolated and rescaled ghosts,
+ * Sec. II B 5; flow grids only). */
+enum { REF_PERIODIC = 0, REF_WALLS = 1, REF_DENSITY = 2 };
 enum { REF_INIT_TGV = 0, REF_INIT_SHEAR = 1, REF_INIT_POISEUILLE = 2, REF_INIT_RB = 3 };
+/* FV time integration (Sec. II B 2): the semi-implicit collision with the
+ * Heun corrector on the advection (Eq. (semi-heun), the default), the same
+ * without the corrector (Eq. (semi)), or explicit Euler on the plain
+ * populations with the physical tau (Eq. (euler)). */
+enum { REF_FV_HEUN = 0, REF_FV_SEMI = 1, REF_FV_EULER = 2 };
 
 typedef struct {
     int nx, ny;
     double lx, ly;
-    int sx, sy;                 /* REF_UNIFORM / REF_TANH / REF_SINH        */
+    int sx, sy;                 /* REF_UNIFORM / TANH / SINH / CHEB          */
     double stretch_x, stretch_y;/* tanh: delta = atanh(s1); sinh: s2        */
     int bcx, bcy;               /* REF_PERIODIC / REF_WALLS                 */
     int thermal;                /* 1: second population set g               */
@@ -72,6 +80,14 @@ int ref_get_pops(const ref_grid* g, double* f, double* gg);
 
 int ref_step_st(ref_grid* g, int nsteps);
 int ref_step_fv(ref_grid* g, int nsteps);
+/* Select the FV scheme.  It fixes what the state holds: tilded populations
+ * for REF_FV_HEUN and REF_FV_SEMI, plain ones for REF_FV_EULER (whose
+ * moments carry no dt/2 a shift and whose initial state is f_eq).  Call it
+ * before initialising; ref_step_st refuses an Euler grid (-1). */
+int ref_set_scheme(ref_grid* g, int scheme);
+/* Densities imposed on the faces of REF_DENSITY axes: x = 0, x = L_x,
+ * y = 0, y = L_y (default 1). */
+int ref_set_boundary_density(ref_grid* g, double rho_x0, double rho_x1, double rho_y0, double rho_y1);
 
 int ref_moments(const ref_grid* g, double* rho, double* ux, double* uy, double* T);
 int ref_conservation(const ref_grid* g, double* mass, double* momx, double* momy,

@@ -19,8 +19,8 @@ from . import _build
 Q = 9
 
 LB_OK, LB_ERR_ARG, LB_ERR_OOM, LB_ERR_CUDA, LB_ERR_STATE, LB_ERR_UNSTABLE, LB_ERR_TIMEOUT = range(7)
-LB_AXIS_UNIFORM, LB_AXIS_TANH, LB_AXIS_SINH = 0, 1, 2
-LB_BC_PERIODIC, LB_BC_WALLS = 0, 1
+LB_AXIS_UNIFORM, LB_AXIS_TANH, LB_AXIS_SINH, LB_AXIS_CHEB = 0, 1, 2, 3
+LB_BC_PERIODIC, LB_BC_WALLS, LB_BC_DENSITY = 0, 1, 2
 LB_STORE_F64, LB_STORE_F32, LB_STORE_F16DEV, LB_STORE_BF16DEV = 0, 1, 2, 3
 LB_INIT_TGV, LB_INIT_SHEAR, LB_INIT_POISEUILLE, LB_INIT_RB, LB_INIT_FIELDS = 0, 1, 2, 3, 4
 
@@ -73,10 +73,12 @@ SYMBOLS = ["lb_create_grid", "lb_init", "lb_step_fv", "lb_step_st", "lb_moments"
            "lb_conservation", "lb_nusselt", "lb_set_populations", "lb_get_populations",
            "lb_get_window", "lb_sync", "lb_destroy", "lb_last_error", "lb_kernel_launches",
            "lb_conservation_noalloc", "lb_set_fv_schedule", "lb_get_fv_schedule",
+           "lb_set_fv_scheme", "lb_get_fv_scheme", "lb_set_boundary_density",
            "lb_autotune_fv", "lb_server_create", "lb_server_submit", "lb_server_pump",
            "lb_server_results", "lb_server_clock", "lb_server_destroy"]
 LB_FV_AUTO, LB_FV_TILE, LB_FV_MARCH, LB_FV_PAIR, LB_FV_PTILE = 0, 1, 2, 3, 4
 LB_SERVE_SHARE, LB_SERVE_SHORTEST = 0, 1
+LB_FV_HEUN, LB_FV_SEMI, LB_FV_EULER = 0, 1, 2
 
 _lib = None
 
@@ -112,6 +114,9 @@ def load(build: bool = True) -> C.CDLL:
     L.lb_set_fv_schedule.argtypes = [G, C.c_int, C.c_int]
     L.lb_get_fv_schedule.argtypes = [G, C.POINTER(C.c_int), C.POINTER(C.c_int)]
     L.lb_autotune_fv.argtypes = [G, C.c_int]
+    L.lb_set_fv_scheme.argtypes = [G, C.c_int]
+    L.lb_set_boundary_density.argtypes = [G] + [C.c_double] * 4
+    L.lb_get_fv_scheme.argtypes = [G, C.POINTER(C.c_int)]
     L.lb_server_create.argtypes = [C.c_int, C.c_int, C.c_ulonglong, C.c_int, C.c_int, C.c_void_p,
                                    C.POINTER(C.c_void_p)]
     L.lb_server_submit.argtypes = [C.c_void_p, C.POINTER(lb_request)]
@@ -209,6 +214,20 @@ def lb_conservation_noalloc(f_ptr, g_ptr, nx, ny, pitch, dx_ptr, dy_ptr, dt, ax,
 
 def lb_set_fv_schedule(grid, kernel: int, chunk: int = 0) -> None:
     _check(load().lb_set_fv_schedule(grid, int(kernel), int(chunk)))
+
+
+def lb_set_fv_scheme(grid, scheme: int) -> None:
+    _check(load().lb_set_fv_scheme(grid, int(scheme)))
+
+
+def lb_set_boundary_density(grid, rho_x0=1.0, rho_x1=1.0, rho_y0=1.0, rho_y1=1.0) -> None:
+    _check(load().lb_set_boundary_density(grid, float(rho_x0), float(rho_x1), float(rho_y0), float(rho_y1)))
+
+
+def lb_get_fv_scheme(grid) -> int:
+    v = C.c_int()
+    _check(load().lb_get_fv_scheme(grid, C.byref(v)))
+    return v.value
 
 
 def lb_get_fv_schedule(grid):
@@ -333,6 +352,19 @@ class Grid:
 
     def fv_schedule(self):
         return lb_get_fv_schedule(self._h)
+
+    def set_fv_scheme(self, scheme):
+        """LB_FV_HEUN, LB_FV_SEMI or LB_FV_EULER; a change needs init() again."""
+        lb_set_fv_scheme(self._h, scheme)
+        return self
+
+    def fv_scheme(self):
+        return lb_get_fv_scheme(self._h)
+
+    def set_boundary_density(self, rho_x0=1.0, rho_x1=1.0, rho_y0=1.0, rho_y1=1.0):
+        """Densities on the faces of LB_BC_DENSITY axes (Sec. II B 5)."""
+        lb_set_boundary_density(self._h, rho_x0, rho_x1, rho_y0, rho_y1)
+        return self
 
     def autotune_fv(self, steps=5):
         lb_autotune_fv(self._h, steps)

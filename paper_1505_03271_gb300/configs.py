@@ -18,7 +18,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import (LB_AXIS_TANH, LB_AXIS_UNIFORM, LB_BC_PERIODIC, LB_BC_WALLS, LB_INIT_POISEUILLE,
+from . import (LB_AXIS_CHEB, LB_AXIS_SINH, LB_AXIS_TANH, LB_AXIS_UNIFORM, LB_BC_PERIODIC, LB_BC_WALLS, LB_INIT_POISEUILLE,
                LB_INIT_RB, LB_INIT_TGV, LB_STORE_F16DEV, LB_STORE_F32, LB_STORE_F64)
 
 CS2 = 1.0 / 3.0
@@ -30,10 +30,17 @@ def tau_from_st_tau(tau_tilde_st: float) -> float:
 
 
 def faces(n: int, L: float, spacing: int, stretch: float) -> np.ndarray:
-    """Face coordinates of Eq. (grids) (uniform or tanh with delta = stretch)."""
+    """Face coordinates of Eq. (grids), as the library builds them: uniform;
+    tanh with delta = stretch; sinh with s2 = stretch (even n); Chebyshev
+    xi_i = L/2 (1 - cos(i pi / n))."""
     i = np.arange(n + 1)
     if spacing == LB_AXIS_TANH:
         xi = 0.5 * L * (1.0 + np.tanh((2.0 * i / n - 1.0) * stretch) / np.tanh(stretch))
+    elif spacing == LB_AXIS_SINH:
+        amp = 0.5 * L / np.sinh(0.5 * stretch)
+        xi = np.where(2 * i <= n, amp * np.sinh(stretch * i / n), L - amp * np.sinh(stretch * (n - i) / n))
+    elif spacing == LB_AXIS_CHEB:
+        xi = 0.5 * L * (1.0 - np.cos(np.pi * i / n))
     else:
         xi = L * i / n
     xi[0], xi[-1] = 0.0, L

@@ -73,8 +73,50 @@ __device__ __forceinline__ void unroll_advect(const R* P, int plane, int stride,
 // for g the anti-reflection hg_a(x_-k) = 2 w_a T_wall - hg_inv(a)(x_k), which
 // on base-state deviations (T_r odd about T_wall) reads h'_a = -h'_inv(a).
 // Thermal grids have their plates on y only.
+// Fixed density (flow grids, whose base state is rho_r = 1): the ghost
+// density 2 rho_S - rho_k is extrapolated through the face value from the
+// mirrored node k and h_a(ghost) = (rho_g / rho_k) h_a(k); on deviations
+// h' = h - w this is h'_g = h'_k + s (h'_k + w) with
+// s = rho_g / rho_k - 1 = 2 ((rho_S - 1) - sum h'_k) / (1 + sum h'_k).
+template <typename R>
+__device__ __forceinline__ void density_ghost(R* P, int plane, int dst, int src, R rsd) {
+    R sum = 0;
+#pragma unroll
+    for (int a = 0; a < Q; ++a) sum += P[a * plane + src];
+    const R s = R(2) * (rsd - sum) / (R(1) + sum);
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const R v = P[a * plane + src];
+        P[a * plane + dst] = v + s * (v + wgt<R>(a));
+    }
+}
+
 template <typename R, bool TH>
 __device__ void ghost_fill(R* P, int plane, int W, int H, int gx0, int gy0, const StepArgs<R>& A) {
+    if (!TH && A.bcy == LB_BC_DENSITY) {
+        for (int k = threadIdx.x; k < W * 4; k += blockDim.x) {
+            const int ex = k % W, which = k / W;
+            int gxx;
+            if (!map_axis(gx0 + ex, A.nx, A.bcx, gxx)) continue;
+            const int kk = (which & 1) + 1;
+            const bool bot = which < 2;
+            const int ey = (bot ? -kk : A.ny - 1 + kk) - gy0, eys = (bot ? kk - 1 : A.ny - kk) - gy0;
+            if (ey < 0 || ey >= H) continue;
+            density_ghost<R>(P, plane, ey * W + ex, eys * W + ex, bot ? A.rhobd[2] : A.rhobd[3]);
+        }
+    }
+    if (!TH && A.bcx == LB_BC_DENSITY) {
+        for (int k = threadIdx.x; k < H * 4; k += blockDim.x) {
+            const int ey = k % H, which = k / H;
+            int gyy;
+            if (!map_axis(gy0 + ey, A.ny, A.bcy, gyy)) continue;
+            const int kk = (which & 1) + 1;
+            const bool lft = which < 2;
+            const int ex = (lft ? -kk : A.nx - 1 + kk) - gx0, exs = (lft ? kk - 1 : A.nx - kk) - gx0;
+            if (ex < 0 || ex >= W) continue;
+            density_ghost<R>(P, plane, ey * W + ex, ey * W + exs, lft ? A.rhobd[0] : A.rhobd[1]);
+        }
+    }
     if (A.bcy == LB_BC_WALLS) {
         for (int k = threadIdx.x; k < W * 4; k += blockDim.x) {
             const int ex = k % W, which = k / W;  // 0,1: bottom ghost 1,2; 2,3: top ghost 1,2
@@ -182,6 +224,23 @@ __device__ __forceinline__ void fv_tile(const StepArgs<R>& A, const int x0, cons
                 if (tile) sFC[(Q + a) * NB + k] = gc - A.hf * adv[Q + a];
             }
         }
+        if (A.stages == 1) {
+            // single-stage schemes (Eqs. (semi), (euler)): the predictor is
+            // the new state of the tile's cells
+            // (a ragged tile's cells past the grid edge wrap on a periodic
+            // axis; the CTA that owns them writes them)
+            if (tile && x0 - 2 + bx < A.nx && y0 - 2 + by < A.ny) {
+                const long long c = (long long)gy * A.pitch + gx;
+                S* fout = static_cast<S*>(A.fout);
+                S* gout = static_cast<S*>(A.gout);
+#pragma unroll
+                for (int a = 0; a < Q; ++a) {
+                    Store<S>::st(fout + a * A.plane + c, fs[a]);
+                    if constexpr (TH) Store<S>::st(gout + a * A.plane + c, es[a]);
+                }
+            }
+            continue;
+        }
         Cell<R, TH> m;
         m.moments(fs, es, A, A.roff[gy], A.toff[gy]);
 #pragma unroll
@@ -192,6 +251,7 @@ __device__ __forceinline__ void fv_tile(const StepArgs<R>& A, const int x0, cons
             if constexpr (TH) sHs[(Q + a) * NB + k] = es[a] + A.omgh * (geqd - es[a]);
         }
     }
+    if (A.stages == 1) return;  // uniform over the CTA
     __syncthreads();
     ghost_fill<R, TH>(sHs, NB, BX, BY, x0 - 2, y0 - 2, A);
     __syncthreads();

@@ -73,7 +73,7 @@ AuxArgs aux_args(const lb_grid* G) {
     a.ny = G->ny;
     a.pitch = G->pitch;
     a.plane = G->plane;
-    a.dt = G->p.dt;
+    a.dt = G->fv_scheme == LB_FV_EULER ? 0.0 : G->p.dt;  // dt/2 a shift of the tilded moments
     a.ax = G->p.ax;
     a.ay = G->p.ay;
     a.bg = G->p.beta * G->p.grav;
@@ -94,7 +94,11 @@ lb_status check_ready(lb_grid* G) {
     return LB_OK;
 }
 
-bool pair_ok(const lb_grid* G) { return G->prec != Prec::F64 && G->d.bcx == LB_BC_PERIODIC; }
+bool pair_ok(const lb_grid* G) {
+    return G->prec != Prec::F64 && G->d.bcx == LB_BC_PERIODIC && G->d.bcy != LB_BC_DENSITY;
+}
+
+bool has_density_axis(const lb_grid* G) { return G->d.bcx == LB_BC_DENSITY || G->d.bcy == LB_BC_DENSITY; }
 
 // Schedule actually used: AUTO takes a marching kernel (the paired one when
 // it applies) once the grid is wide and tall enough to fill the GPU with
@@ -129,6 +133,8 @@ template <typename R>
 cudaError_t launch_fv_step(lb_grid* G) {
     StepArgs<R> A = step_args<R>(G, G->p.dt);
     const bool th = G->d.thermal != 0;
+    if (A.stages == 1 || has_density_axis(G))  // single-stage schemes, density boundaries: scalar tile kernel
+        return launch_fv(G->prec, th, &A, G->fv_kernel == LB_FV_TILE ? G->fv_chunk : 0, G->stream);
     const int k = resolved_kernel(G);
     if (k == LB_FV_PAIR) return launch_fv_pair(G->prec, th, &A, resolved_chunk(G), G->stream);
     if (k == LB_FV_PTILE) return launch_fv_ptile(G->prec, th, &A, G->fv_kernel == LB_FV_PTILE ? G->fv_chunk : 0,
@@ -169,19 +175,21 @@ lb_status lb_create_grid(const lb_grid_desc* d, lb_grid** out) {
     if (d->nx < 1 || d->ny < 1) return fail(LB_ERR_ARG, "nx, ny must be >= 1 (got %d, %d)", d->nx, d->ny);
     if ((long long)d->nx * d->ny > (1LL << 31))
         return fail(LB_ERR_ARG, "grid of %d x %d cells is larger than supported", d->nx, d->ny);
-    if (d->bcx != LB_BC_PERIODIC && d->bcx != LB_BC_WALLS) return fail(LB_ERR_ARG, "bad bcx");
-    if (d->bcy != LB_BC_PERIODIC && d->bcy != LB_BC_WALLS) return fail(LB_ERR_ARG, "bad bcy");
-    if ((d->bcx == LB_BC_WALLS && d->nx < 2) || (d->bcy == LB_BC_WALLS && d->ny < 2))
-        return fail(LB_ERR_ARG, "a wall axis needs at least 2 cells (two ghost layers)");
-    if (d->thermal && d->bcx == LB_BC_WALLS)
+    if (d->bcx < LB_BC_PERIODIC || d->bcx > LB_BC_DENSITY) return fail(LB_ERR_ARG, "bad bcx");
+    if (d->bcy < LB_BC_PERIODIC || d->bcy > LB_BC_DENSITY) return fail(LB_ERR_ARG, "bad bcy");
+    if ((d->bcx != LB_BC_PERIODIC && d->nx < 2) || (d->bcy != LB_BC_PERIODIC && d->ny < 2))
+        return fail(LB_ERR_ARG, "a wall or density axis needs at least 2 cells (two ghost layers)");
+    if (d->thermal && d->bcx != LB_BC_PERIODIC)
         return fail(LB_ERR_ARG, "thermal grids have their isothermal plates on y; x must be periodic");
+    if (d->thermal && d->bcy == LB_BC_DENSITY)
+        return fail(LB_ERR_ARG, "thermal grids have isothermal plates on y, not a density boundary");
     if (d->store < LB_STORE_F64 || d->store > LB_STORE_BF16DEV) return fail(LB_ERR_ARG, "bad store");
     for (int k = 0; k < 2; ++k) {
         const int sp = k ? d->sy : d->sx, n = k ? d->ny : d->nx;
         const double L = k ? d->ly : d->lx, st = k ? d->stretch_y : d->stretch_x;
-        if (sp < LB_AXIS_UNIFORM || sp > LB_AXIS_SINH) return fail(LB_ERR_ARG, "bad spacing");
+        if (sp < LB_AXIS_UNIFORM || sp > LB_AXIS_CHEB) return fail(LB_ERR_ARG, "bad spacing");
         if (!(L > 0)) return fail(LB_ERR_ARG, "domain length must be > 0");
-        if (sp != LB_AXIS_UNIFORM && !(st > 0)) return fail(LB_ERR_ARG, "stretch must be > 0");
+        if ((sp == LB_AXIS_TANH || sp == LB_AXIS_SINH) && !(st > 0)) return fail(LB_ERR_ARG, "stretch must be > 0");
         if (sp == LB_AXIS_SINH && (n % 2)) return fail(LB_ERR_ARG, "sinh spacing needs an even cell count");
     }
     lb_grid* G = new lb_grid();
@@ -389,7 +397,7 @@ lb_status lb_init(lb_grid* G, const lb_params* p, const lb_init_desc* in) {
     a.seed = in->seed;
     a.lx = G->d.lx;
     a.ly = G->d.ly;
-    a.dt = p->dt;
+    a.dt = G->fv_scheme == LB_FV_EULER ? 0.0 : p->dt;  // f~ = f_eq - dt/2 F; Euler starts at f_eq
     a.ax = p->ax;
     a.ay = p->ay;
     a.bg = p->beta * p->grav;
@@ -449,6 +457,33 @@ lb_status lb_set_fv_schedule(lb_grid* G, int kernel, int chunk) {
         return fail(LB_ERR_ARG, "the paired FV kernel needs FP32/FP16/BF16 storage and a periodic x axis");
     G->fv_kernel = kernel;
     G->fv_chunk = chunk;
+    return LB_OK;
+}
+
+lb_status lb_set_fv_scheme(lb_grid* G, int scheme) {
+    if (!G) return fail(LB_ERR_ARG, "grid is NULL");
+    if (scheme < LB_FV_HEUN || scheme > LB_FV_EULER) return fail(LB_ERR_ARG, "unknown FV scheme %d", scheme);
+    if (scheme != G->fv_scheme) {
+        G->fv_scheme = scheme;
+        G->has_params = false;  // the state's meaning changed: lb_init again
+    }
+    return LB_OK;
+}
+
+lb_status lb_set_boundary_density(lb_grid* G, double rho_x0, double rho_x1, double rho_y0, double rho_y1) {
+    if (!G) return fail(LB_ERR_ARG, "grid is NULL");
+    if (!(rho_x0 > 0) || !(rho_x1 > 0) || !(rho_y0 > 0) || !(rho_y1 > 0))
+        return fail(LB_ERR_ARG, "boundary densities must be > 0");
+    G->rho_bc[0] = rho_x0;
+    G->rho_bc[1] = rho_x1;
+    G->rho_bc[2] = rho_y0;
+    G->rho_bc[3] = rho_y1;
+    return LB_OK;
+}
+
+lb_status lb_get_fv_scheme(lb_grid* G, int* scheme) {
+    if (!G || !scheme) return fail(LB_ERR_ARG, "NULL argument");
+    *scheme = G->fv_scheme;
     return LB_OK;
 }
 
@@ -546,6 +581,8 @@ lb_status lb_step_st(lb_grid* G, int nsteps) {
     lb_status s = check_ready(G);
     if (s != LB_OK) return s;
     if (nsteps < 0) return fail(LB_ERR_ARG, "nsteps must be >= 0");
+    if (G->fv_scheme == LB_FV_EULER) return fail(LB_ERR_STATE, "ST steps tilded populations, not an Euler grid");
+    if (has_density_axis(G)) return fail(LB_ERR_ARG, "the fixed-density boundary is an FV boundary (no ST form)");
     for (int k = 0; k < 2; ++k) {
         const int sp = k ? G->d.sy : G->d.sx, n = k ? G->ny : G->nx;
         const double L = k ? G->d.ly : G->d.lx;

@@ -19,6 +19,8 @@ inline std::vector<double> axis_faces(int n, double L, int sp, double st) {
         } else if (sp == LB_AXIS_SINH) {
             const double amp = 0.5 * L / std::sinh(0.5 * st);
             xi[i] = 2 * i <= n ? amp * std::sinh(st * s) : L - amp * std::sinh(st * (double)(n - i) / n);
+        } else if (sp == LB_AXIS_CHEB) {
+            xi[i] = 0.5 * L * (1.0 - std::cos(3.14159265358979323846 * s));
         } else {
             xi[i] = L * s;
         }
@@ -127,6 +129,8 @@ struct lb_grid {
     double* partial = nullptr;  // reduction partials
     double* red = nullptr;      // reduction totals
     int nred = 0;
+    int fv_scheme = LB_FV_HEUN;  // time integration of lb_step_fv
+    double rho_bc[4] = {1.0, 1.0, 1.0, 1.0};  // imposed densities of LB_BC_DENSITY axes
     int fv_kernel = LB_FV_AUTO;  // requested schedule
     int fv_chunk = 0;
     int sms = 0;                 // streaming multiprocessors of the device
@@ -159,12 +163,23 @@ inline StepArgs<R> step_args(const lb_grid* G, double dt) {
     A.hf = (R)(0.5 * dt);
     A.omg = (R)(dt / taugt);
     A.omgh = (R)(dt / (2.0 * taugt));
+    A.stages = G->fv_scheme == LB_FV_HEUN ? 2 : 1;
+    if (G->fv_scheme == LB_FV_EULER) {
+        // Eq. (euler): h = f, source dt/tau (f_eq - f) + dt F, u = sum c f / rho
+        A.om = (R)(dt / p.tau);
+        A.omh = (R)0;
+        A.cf = (R)dt;
+        A.hf = (R)0;
+        A.omg = (R)(dt / p.tau_g);
+        A.omgh = (R)0;
+    }
     A.ax = (R)p.ax;
     A.ay = (R)p.ay;
     A.bg = (R)(p.beta * p.grav);
     A.dTb = (R)(p.T_bot - p.T0);
     A.dTt = (R)(p.T_top - p.T0);
     A.T0 = (R)p.T0;
+    for (int k = 0; k < 4; ++k) A.rhobd[k] = (R)(G->rho_bc[k] - 1.0);
     A.toff = static_cast<const R*>(G->toff_r);
     A.roff = static_cast<const R*>(G->roff_r);
     A.dref = static_cast<const R*>(G->dref_r);

@@ -91,11 +91,13 @@ struct StepArgs {
     long long plane;  // pitch * ny
     int bcx, bcy;
     AxisMetric<R> mx, my;
-    R dt, om, omh, cf, hf;  // dt/tau~, dt/(2 tau~), dt (1 - dt/(2 tau~)), dt/2
+    int stages;             // 2: Heun corrector (Eq. (semi-heun)); 1: the predictor is the new state
+    R dt, om, omh, cf, hf;  // dt/tau~, dt/(2 tau~), dt (1 - dt/(2 tau~)), dt/2 (Euler: dt/tau, 0, dt, 0)
     R omg, omgh;            // dt/tau~_g, dt/(2 tau~_g)
     R ax, ay, bg;           // external acceleration, beta * grav
     R dTb, dTt;             // T_bot - T0, T_top - T0
     R T0;                   // reference temperature
+    R rhobd[4];             // imposed face density - 1 of LB_BC_DENSITY axes: x0, x1, y0, y1
     const R* toff;          // per row: T_r - T0 (thermal grids)
     const R* roff;          // per row: rho_r - 1
     const R* dref;          // [4][ny]: y flux divergence of rho_r (c_y > 0, < 0), of T_r (> 0, < 0)

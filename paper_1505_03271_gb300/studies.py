@@ -1,0 +1,254 @@
+"""Accuracy and stability studies of Secs. III and V, run through the library.
+
+  * ``poiseuille_vs_n``: relative L2 error of the Re = 10 Poiseuille profile
+    against the parabola for a fixed channel width L = 64 and a varying
+    number of cells N (Fig. POI2), for FV on uniform, tanh, sinh and
+    Chebyshev grids and for ST on the uniform lattice.
+  * ``poiseuille_vs_spacing``: the same at fixed N = 64 for a varying mean
+    spacing <dx> = L/N, with the forcing rescaled to keep Re = 10 (Fig. POI3).
+  * ``dt_max``: the largest stable FV time step as a function of tau for the
+    Euler, semi-implicit and Heun schemes on the decaying [1, 64] shear wave
+    (Fig. KOL3).
+
+Conventions (readings of the paper):
+  * tau = 0.5 (physical) for the Poiseuille studies: the paper puts the best
+    viscosity accuracy, and dt ~ 2 tau at dx ~ 1, there.  nu = tau/3,
+    U = Re nu / L, a_x = 8 nu U / L^2, started on the parabola.
+  * FV: dt = 0.9 min(dx_min, 8 tau) on every grid.  Grid stretchings are the
+    paper's s1 = 0.98 (tanh, delta = atanh 0.98) and s2 = 6.5 (sinh).
+  * ST at N cells over L runs in lattice units with dx = dt = L/N (the
+    acoustic scaling of FV's unit lattice speeds): tau_lat = tau N / L, the
+    same U (Mach number) and Re.
+  * Steady state: each run lasts `relax` decay times of the slowest viscous
+    mode, L^2 / (pi^2 nu), from the exact parabola; the remaining transient
+    is exp(-relax) of the discretisation error.
+  * Error: (sum (u_x - U)^2 dy / sum U^2 dy)^(1/2) over cell centres (the
+    discrete L2 norm of Sec. III B).
+  * Stability: the shear wave u_x = A sin(2 pi y / 64), A = 1e-5, plus 1e-6
+    w_a Gaussian noise on every population (seed 1), is unstable when its
+    kinetic energy grows tenfold or turns non-finite within 3000 steps;
+    dt_max by bisection on [0.01, 4].
+
+Independent runs are stepped concurrently, each grid on its own CUDA stream.
+Run ``python -m paper_1505_03271_gb300.studies`` on a GPU to print the tables
+as JSON lines.
+"""
+from __future__ import annotations
+
+import json
+import math
+import sys
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import (LB_AXIS_CHEB, LB_AXIS_SINH, LB_AXIS_TANH, LB_AXIS_UNIFORM, LB_BC_WALLS, LB_FV_EULER,
+               LB_FV_HEUN, LB_FV_SEMI, LB_INIT_POISEUILLE, LB_INIT_SHEAR, LB_STORE_F64)
+from . import configs as cfg
+
+TANH_DELTA = math.atanh(0.98)
+SINH_S2 = 6.5
+FV_GRIDS = {"uniform": (LB_AXIS_UNIFORM, 0.0), "tanh": (LB_AXIS_TANH, TANH_DELTA),
+            "sinh": (LB_AXIS_SINH, SINH_S2), "cheb": (LB_AXIS_CHEB, 0.0)}
+SCHEMES = {"euler": LB_FV_EULER, "semi": LB_FV_SEMI, "heun": LB_FV_HEUN}
+W = np.array([4 / 9] + [1 / 9] * 4 + [1 / 36] * 4)
+
+
+@dataclass(frozen=True)
+class Poiseuille:
+    """One steady Poiseuille run: method "st" or "fv-<grid>"."""
+    method: str
+    n: int
+    L: float
+    tau: float = 0.5
+    Re: float = 10.0
+    relax: float = 5.0
+
+    def spec(self):
+        nu = self.tau * cfg.CS2
+        U = self.Re * nu / self.L
+        if self.method == "st":
+            dx = self.L / self.n
+            tau_l = self.tau / dx
+            nu_l = tau_l * cfg.CS2
+            grid = dict(nx=1, ny=self.n, lx=1.0, ly=float(self.n), bcy=LB_BC_WALLS)
+            params = dict(tau=tau_l, dt=1.0, ax=8.0 * nu_l * U / self.n**2)
+            steps = int(math.ceil(self.relax * self.n**2 / (math.pi**2 * nu_l)))
+            xi = np.arange(self.n + 1, dtype=float)
+            return grid, params, U, steps, xi, float(self.n), "st"
+        sp, st = FV_GRIDS[self.method.split("-", 1)[1]]
+        grid = dict(nx=1, ny=self.n, lx=1.0, ly=self.L, sy=sp, stretch_y=st, bcy=LB_BC_WALLS)
+        xi = cfg.faces(self.n, self.L, sp, st)
+        dt = cfg.fv_dt(float(np.diff(xi).min()), self.tau)
+        params = dict(tau=self.tau, dt=dt, ax=8.0 * nu * U / self.L**2)
+        steps = int(math.ceil(self.relax * self.L**2 / (math.pi**2 * nu) / dt))
+        return grid, params, U, steps, xi, self.L, "fv"
+
+    def error(self, ux, xi, L, U):
+        y = 0.5 * (xi[1:] + xi[:-1])
+        dy = np.diff(xi)
+        ref = 4.0 * U * y * (L - y) / L**2
+        return float(np.sqrt(((ux - ref) ** 2 * dy).sum() / (ref**2 * dy).sum()))
+
+
+def _run_concurrent(lb, torch, jobs, start, advance, finish, streams=8, chunk=256, after_round=None):
+    """Step independent jobs round-robin, each on its own stream.
+    start(job, stream) -> state with .remaining; advance(state, k) enqueues
+    k steps; after_round(state), if given, runs once every active job has
+    been advanced (it may synchronise); finish(state) -> result."""
+    pending = list(jobs)
+    active, out = [], {}
+    while pending or active:
+        while pending and len(active) < streams:
+            job = pending.pop(0)
+            s = torch.cuda.Stream()
+            active.append((job, s, start(job, s.cuda_stream)))
+        for job, s, st in active:
+            k = min(chunk, st.remaining)
+            if k > 0:
+                advance(st, k)
+                st.remaining -= k
+        if after_round is not None:
+            for job, s, st in active:
+                after_round(st)
+        for item in [a for a in active if a[2].remaining == 0]:
+            job, s, st = item
+            out[job] = finish(st)
+            active.remove(item)
+    return out
+
+
+class _State:
+    pass
+
+
+def run_poiseuille(lb, torch, cases, streams=8):
+    """Relative L2 error of each Poiseuille case (FP64 storage)."""
+    def start(c, stream):
+        grid, params, U, steps, xi, L, scheme = c.spec()
+        st = _State()
+        st.g = lb.Grid(store=LB_STORE_F64, stream=stream, **grid)
+        st.g.init(kind=LB_INIT_POISEUILLE, u0=U, **params)
+        st.scheme, st.remaining, st.c = scheme, steps, c
+        st.aux = (U, steps, xi, L, params["dt"])
+        return st
+
+    def advance(st, k):
+        (st.g.step_st if st.scheme == "st" else st.g.step_fv)(k)
+
+    def finish(st):
+        U, steps, xi, L, dt = st.aux
+        _, ux, _, _ = st.g.moments()
+        st.g.close()
+        return {"method": st.c.method, "n": st.c.n, "L": st.c.L, "mean_dx": st.c.L / st.c.n,
+                "U": U, "dt": dt, "steps": steps, "err": st.c.error(ux[:, 0], xi, L, U)}
+
+    return _run_concurrent(lb, torch, cases, start, advance, finish, streams)
+
+
+def poiseuille_vs_n(lb, torch, ns=(8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256), cheb_max=128):
+    cases = []
+    for n in ns:
+        cases.append(Poiseuille("st", n, 64.0))
+        for gname in FV_GRIDS:
+            if gname == "cheb" and n > cheb_max:
+                continue
+            cases.append(Poiseuille("fv-" + gname, n, 64.0))
+    res = run_poiseuille(lb, torch, cases)
+    return [res[c] for c in cases]
+
+
+def poiseuille_vs_spacing(lb, torch, mean_dx=(0.25, 0.5, 1, 2, 4, 8, 16), n=64, cheb_max=8):
+    cases = []
+    for d in mean_dx:
+        cases.append(Poiseuille("st", n, n * float(d)))
+        for gname in FV_GRIDS:
+            if gname == "cheb" and d > cheb_max:
+                continue
+            cases.append(Poiseuille("fv-" + gname, n, n * float(d)))
+    res = run_poiseuille(lb, torch, cases)
+    return [res[c] for c in cases]
+
+
+def _shear_state(lb, scheme, tau, dt, stream, n=64, seed=1):
+    g = lb.Grid(1, n, lx=1.0, ly=float(n), store=LB_STORE_F64, stream=stream).set_fv_scheme(scheme)
+    g.init(tau=tau, dt=dt, kind=LB_INIT_SHEAR, amp=1e-5)
+    f, _ = g.get_pops()
+    rng = np.random.default_rng(seed)
+    g.set_pops(f + 1e-6 * W[:, None, None] * rng.standard_normal(f.shape))
+    return g
+
+
+def _energy(g):
+    _, ux, uy, _ = g.moments()
+    return float((ux**2 + uy**2).sum())
+
+
+def stable_many(lb, torch, probes, steps=3000, check=100, streams=16):
+    """Stability verdict of each (scheme, tau, dt) probe."""
+    def start(p, stream):
+        scheme, tau, dt = p
+        st = _State()
+        st.g = _shear_state(lb, SCHEMES[scheme], tau, dt, stream)
+        st.k0 = _energy(st.g)
+        st.ok = True
+        st.remaining = steps
+        return st
+
+    def advance(st, k):
+        if st.ok:
+            st.g.step_fv(k)
+
+    def after_round(st):
+        if not st.ok:
+            return
+        try:
+            e = _energy(st.g)
+        except lb.LBError:
+            e = float("nan")
+        if not math.isfinite(e) or e > 10 * st.k0:
+            st.ok = False
+            st.remaining = 0
+
+    def finish(st):
+        st.g.close()
+        return st.ok
+
+    return _run_concurrent(lb, torch, probes, start, advance, finish, streams, chunk=check,
+                           after_round=after_round)
+
+
+def dt_max(lb, torch, taus=(0.03, 0.05, 0.08, 0.125, 0.2, 0.3, 0.5, 0.7, 1.0, 1.5),
+           schemes=("euler", "semi", "heun"), lo=0.01, hi=4.0, iters=9):
+    """Largest stable dt by bisection for every (scheme, tau), all pairs
+    bisected together."""
+    keys = [(s, t) for s in schemes for t in taus]
+    bounds = {k: [lo, hi] for k in keys}
+    for _ in range(iters):
+        probes = [(s, t, 0.5 * sum(bounds[(s, t)])) for s, t in keys]
+        verdict = stable_many(lb, torch, probes)
+        for (s, t, dt) in probes:
+            bounds[(s, t)][0 if verdict[(s, t, dt)] else 1] = dt
+    return [{"scheme": s, "tau": t, "dt_max": round(bounds[(s, t)][0], 4)} for s, t in keys]
+
+
+def main(argv=None):
+    import time
+
+    import torch
+
+    from . import load
+    import paper_1505_03271_gb300 as lb
+    argv = sys.argv[1:] if argv is None else argv
+    which = set(argv) or {"kol3", "poi2", "poi3"}
+    load()
+    for name, fn in (("kol3", dt_max), ("poi2", poiseuille_vs_n), ("poi3", poiseuille_vs_spacing)):
+        if name in which:
+            t0 = time.perf_counter()
+            rows = fn(lb, torch)
+            print(json.dumps({"study": name, "seconds": round(time.perf_counter() - t0, 1), "rows": rows}),
+                  flush=True)
+
+
+if __name__ == "__main__":
+    main()

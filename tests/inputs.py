@@ -30,5 +30,16 @@ def random_fields(nx: int, ny: int, seed: int, u_amp: float = 0.02, rho_amp: flo
     return rho, ux, uy, T
 
 
+# D3Q19 weights in the library's order (rest, 6 axis, 12 edge velocities).
+_W3 = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+
+
+def random_populations3(nx: int, ny: int, nz: int, seed: int, amp: float = 0.05, base: float = 1.0):
+    """D3Q19 populations base*w_a*(1 + amp*U(-1,1)), shape [19, nz, ny, nx]."""
+    rng = np.random.default_rng(seed)
+    noise = rng.uniform(-1.0, 1.0, size=(19, nz, ny, nx))
+    return (_W3[:, None, None, None] * base * (1.0 + amp * noise)).astype(np.float64)
+
+
 def random_vector(n: int, seed: int, lo: float = -1.0, hi: float = 1.0):
     return np.random.default_rng(seed).uniform(lo, hi, n)

@@ -135,6 +135,7 @@ def test_st_step_f32_pairs(lbgpu, oracle, case):
 
 FV_CASES = [
     dict(nx=70, ny=37),
+    dict(nx=18, ny=24, sy=3, bcy=1),
     dict(nx=45, ny=33, sy=1, stretch_y=1.5),
     dict(nx=50, ny=40, sy=1, stretch_y=2.0, bcy=1),
     dict(nx=35, ny=34, sx=1, stretch_x=1.0, sy=2, stretch_y=4.0, bcx=1, bcy=1),
@@ -202,6 +203,134 @@ def test_fv_step_f32_schedules(lbgpu, oracle, case, sched):
     assert np.abs(fg - fr).max() <= 2e-6 * scale
     if th:
         assert np.abs(ggg - ggr).max() <= 2e-6 * np.abs(gg - wts).max()
+
+
+SINGLE_STAGE_CASES = [
+    dict(nx=40, ny=36, sy=1, stretch_y=2.0, bcy=1, thermal=True),
+    dict(nx=35, ny=34, sx=1, stretch_x=1.0, sy=2, stretch_y=4.0, bcx=1, bcy=1),
+    dict(nx=37, ny=19),
+    dict(nx=1, ny=64, lx=1.0),
+]
+
+
+@pytest.mark.parametrize("store", ["f64", "f32"])
+@pytest.mark.parametrize("scheme", [1, 2], ids=["semi", "euler"])
+@pytest.mark.parametrize("case", SINGLE_STAGE_CASES, ids=lambda c: "-".join(f"{k}{v}" for k, v in c.items()))
+def test_fv_single_stage_schemes(lbgpu, oracle, case, scheme, store):
+    """Eq. (semi) and Eq. (euler) through the C ABI against the oracle after
+    4 steps from the same random state: FP64 to 1e-13, FP32 to 2e-6 of the
+    deviation scale, thermal populations included."""
+    lb = lbgpu
+    nx, ny = case["nx"], case["ny"]
+    th = case.get("thermal", False)
+    kw = dict(tau=0.3, dt=0.05, ax=2e-4, ay=-1e-4)
+    if th:
+        kw.update(tau_g=0.25, beta=1e-2, grav=1.0, T0=1.0, T_bot=1.3, T_top=0.8)
+    gk = {k: v for k, v in case.items() if k not in ("nx", "ny")}
+    st = lb.LB_STORE_F64 if store == "f64" else lb.LB_STORE_F32
+    g = lb.Grid(nx, ny, store=st, **gk).set_fv_scheme(scheme)
+    g.init(**kw)
+    r = oracle.RefGrid(nx, ny, **gk).set_scheme(scheme).set_params(**kw)
+    f = inputs.random_populations(nx, ny, seed=5 * nx + ny, amp=0.2)
+    gg = inputs.random_populations(nx, ny, seed=13, amp=0.2) if th else None
+    g.set_pops(f, gg)
+    f, gg = g.get_pops()
+    r.set_pops(f, gg)
+    g.step_fv(4)
+    r.step_fv(4)
+    fg, ggg = g.get_pops()
+    fr, ggr = r.get_pops()
+    wts = oracle.lattice()[2][:, None, None]
+    tol = 1e-13 if store == "f64" else 2e-6 * np.abs(f - wts).max()
+    assert np.abs(fg - fr).max() <= tol
+    if th:
+        assert np.abs(ggg - ggr).max() <= (1e-13 if store == "f64" else 2e-6 * np.abs(gg - wts).max())
+
+
+DENSITY_CASES = [
+    dict(nx=37, ny=20, bcx=2, bcy=1, sy=1, stretch_y=2.0),
+    dict(nx=24, ny=33, bcy=2),
+    dict(nx=19, ny=22, bcx=2, bcy=2, sx=2, stretch_x=3.0),
+]
+
+
+@pytest.mark.parametrize("store", ["f64", "f32"])
+@pytest.mark.parametrize("scheme", [0, 2], ids=["heun", "euler"])
+@pytest.mark.parametrize("case", DENSITY_CASES, ids=lambda c: "-".join(f"{k}{v}" for k, v in c.items()))
+def test_fv_density_boundary(lbgpu, oracle, case, scheme, store):
+    """Fixed-density boundaries (Sec. II B 5) through the C ABI against the
+    oracle after 4 steps from a random state: FP64 to 1e-13, FP32 to 2e-6 of
+    the deviation scale."""
+    lb = lbgpu
+    nx, ny = case["nx"], case["ny"]
+    gk = {k: v for k, v in case.items() if k not in ("nx", "ny")}
+    kw = dict(tau=0.3, dt=0.05, ax=2e-4, ay=-1e-4)
+    rb = (1.01, 0.99, 1.005, 0.997)
+    st = lb.LB_STORE_F64 if store == "f64" else lb.LB_STORE_F32
+    g = lb.Grid(nx, ny, store=st, **gk).set_fv_scheme(scheme).set_boundary_density(*rb)
+    g.set_fv_schedule(lb.LB_FV_MARCH, 16)  # density grids step on the tile kernel whatever the schedule
+    g.init(**kw)
+    r = oracle.RefGrid(nx, ny, **gk).set_scheme(scheme).set_params(**kw).set_boundary_density(*rb)
+    f = inputs.random_populations(nx, ny, seed=7 * nx + ny, amp=0.2)
+    g.set_pops(f)
+    f, _ = g.get_pops()
+    r.set_pops(f)
+    g.step_fv(4)
+    r.step_fv(4)
+    wts = oracle.lattice()[2][:, None, None]
+    tol = 1e-13 if store == "f64" else 2e-6 * np.abs(f - wts).max()
+    assert np.abs(g.get_pops()[0] - r.get_pops()[0]).max() <= tol
+
+
+def test_pressure_driven_channel_gpu(lbgpu, oracle):
+    """The density-driven channel of the oracle pins, 600 steps in FP32:
+    u within 1e-5 relative L2 of the oracle."""
+    lb = lbgpu
+    nx, ny, drho = 32, 16, 2e-3
+    kw = dict(tau=0.5, dt=0.9)
+    xc = np.arange(nx) + 0.5
+    rho = np.broadcast_to(1 + drho / 2 - drho * xc / nx, (ny, nx)).copy()
+    g = lb.Grid(nx, ny, bcx=lb.LB_BC_DENSITY, bcy=lb.LB_BC_WALLS, store=lb.LB_STORE_F32)
+    g.set_boundary_density(1 + drho / 2, 1 - drho / 2)
+    g.init(rho=rho, **kw)
+    r = oracle.RefGrid(nx, ny, bcx=oracle.DENSITY, bcy=oracle.WALLS).set_params(**kw)
+    r.set_boundary_density(1 + drho / 2, 1 - drho / 2)
+    r.init_fields(rho=rho)
+    g.step_fv(600)
+    r.step_fv(600)
+    assert rel_l2_u(g, r) < 1e-5
+    with pytest.raises(lb.LBError) as e:
+        g.step_st(1)
+    assert e.value.status == lb.LB_ERR_ARG
+    with pytest.raises(lb.LBError):
+        lb.Grid(8, 8, bcx=lb.LB_BC_DENSITY, thermal=True)
+
+
+def test_euler_grid_semantics(lbgpu, oracle):
+    """An Euler grid holds plain populations: its initial state and moments
+    match the oracle's Euler grid (no dt/2 shifts), ST refuses it, and
+    switching the scheme asks for lb_init again."""
+    lb = lbgpu
+    kw = dict(tau=0.4, dt=0.2, ax=1e-3)
+    g = lb.Grid(4, 32, lx=4.0, ly=32.0, store=lb.LB_STORE_F64).set_fv_scheme(lb.LB_FV_EULER)
+    assert g.fv_scheme() == lb.LB_FV_EULER
+    g.init(kind=lb.LB_INIT_SHEAR, amp=0.01, **kw)
+    r = oracle.RefGrid(4, 32, lx=4.0, ly=32.0).set_scheme(oracle.FV_EULER).set_params(**kw)
+    r.init_preset(oracle.INIT_SHEAR, amp=0.01)
+    assert np.abs(g.get_pops()[0] - r.get_pops()[0]).max() < 1e-15
+    g.step_fv(50)
+    r.step_fv(50)
+    assert rel_l2_u(g, r) < 1e-12
+    with pytest.raises(lb.LBError) as e:
+        g.step_st(1)
+    assert e.value.status == lb.LB_ERR_STATE
+    g.set_fv_scheme(lb.LB_FV_HEUN)
+    with pytest.raises(lb.LBError) as e:
+        g.step_fv(1)
+    assert e.value.status == lb.LB_ERR_STATE
+    with pytest.raises(lb.LBError) as e:
+        g.set_fv_scheme(9)
+    assert e.value.status == lb.LB_ERR_ARG
 
 
 @pytest.mark.parametrize("store", ["f32"])

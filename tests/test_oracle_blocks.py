@@ -100,6 +100,19 @@ def test_faces_sinh(oracle):
         assert np.all(np.diff(xi) > 0)
 
 
+def test_faces_chebyshev(oracle):
+    """Chebyshev faces xi_i = L/2 (1 - cos(i pi / N)) (Eq. (grids), read with
+    i in place of i - 1/2 so the faces reach both walls): the cell widths
+    have the closed form L sin((2i + 1) pi / (2N)) sin(pi / (2N))."""
+    for n in (8, 11, 64):
+        xi = oracle.faces(n, 64.0, oracle.CHEB, 0.0)
+        assert xi[0] == 0.0 and xi[-1] == 64.0
+        assert np.allclose(xi + xi[::-1], 64.0, atol=1e-12)
+        i = np.arange(n)
+        d = 64.0 * np.sin((2 * i + 1) * np.pi / (2 * n)) * np.sin(np.pi / (2 * n))
+        assert np.allclose(np.diff(xi), d, rtol=1e-12, atol=1e-13)
+
+
 def test_quick_uniform_weights(oracle):
     """Leonard's QUICK coefficients on a uniform grid (Sec. II B 3)."""
     ref = np.array([float(v) for v in _golden("quick_uniform.txt")[0]])
