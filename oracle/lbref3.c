@@ -8,6 +8,8 @@
  * Sec. II B 5).  Faces of a diagonal population are taken dimension by
  * dimension, each from the nodes on its own grid line, and the isothermal
  * plates anti-reflect the thermal advected field, as in two dimensions.
+ * OpenMP (if enabled) splits only the outer loop over z planes of the
+ * per-cell loops; no floating-point sum changes order.
  */
 #include "lbref3.h"
 
@@ -279,6 +281,7 @@ int ref3_step_st(ref3_grid* G, int nsteps) {
     const int th = G->d.thermal, nx = G->n[0], ny = G->n[1], nz = G->n[2];
     const double taut = p->tau + 0.5, taugt = p->tau_g + 0.5;
     for (int s = 0; s < nsteps; ++s) {
+#pragma omp parallel for schedule(static)
         for (int k = 0; k < nz; ++k)
             for (int j = 0; j < ny; ++j)
                 for (int i = 0; i < nx; ++i) {
@@ -324,6 +327,7 @@ static void fv_eval3(ref3_grid* G, const double* f, const double* gsrc, double* 
     const ref3_params* p = &G->p;
     const double dt = p->dt, taut = p->tau + 0.5 * dt, taugt = p->tau_g + 0.5 * dt;
     const int th = G->d.thermal;
+#pragma omp parallel for schedule(static)
     for (int k = 0; k < G->n[2]; ++k)
         for (int j = 0; j < G->n[1]; ++j)
             for (int i = 0; i < G->n[0]; ++i) {
@@ -400,6 +404,7 @@ static double face3(const ref3_grid* G, const double* hp, int a, int ax, int fc,
 /* Flux divergence sum over axes of c_a (Phi_+ - Phi_-) / width, Eq. (fv). */
 static void fv_advect3(const ref3_grid* G, const double* hp, double* A) {
     const int* cv[3] = {CX3, CY3, CZ3};
+#pragma omp parallel for schedule(static)
     for (int k = 0; k < G->n[2]; ++k)
         for (int j = 0; j < G->n[1]; ++j)
             for (int i = 0; i < G->n[0]; ++i) {

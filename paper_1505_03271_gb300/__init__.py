@@ -57,6 +57,25 @@ class lb_init_desc(C.Structure):
                 ("seed", C.c_ulonglong), ("rho", _DP), ("ux", _DP), ("uy", _DP), ("T", _DP)]
 
 
+class lb3_grid_desc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("lx", C.c_double),
+                ("ly", C.c_double), ("lz", C.c_double), ("sx", C.c_int), ("sy", C.c_int),
+                ("sz", C.c_int), ("stretch_x", C.c_double), ("stretch_y", C.c_double),
+                ("stretch_z", C.c_double), ("bcx", C.c_int), ("bcy", C.c_int), ("bcz", C.c_int),
+                ("thermal", C.c_int), ("store", C.c_int), ("cuda_stream", C.c_void_p)]
+
+
+class lb3_params(C.Structure):
+    _fields_ = [(n, C.c_double) for n in ("tau", "dt", "tau_g", "ax", "ay", "az", "beta", "grav",
+                                          "T0", "T_bot", "T_top")]
+
+
+class lb3_init_desc(C.Structure):
+    _fields_ = [("kind", C.c_int), ("mode", C.c_int), ("u0", C.c_double), ("amp", C.c_double),
+                ("seed", C.c_ulonglong), ("rho", _DP), ("ux", _DP), ("uy", _DP), ("uz", _DP),
+                ("T", _DP)]
+
+
 class lb_request(C.Structure):
     _fields_ = [("id", C.c_longlong), ("grid", lb_grid_desc), ("params", lb_params),
                 ("init", lb_init_desc), ("nsteps", C.c_int)]
@@ -74,6 +93,9 @@ SYMBOLS = ["lb_create_grid", "lb_init", "lb_step_fv", "lb_step_st", "lb_moments"
            "lb_get_window", "lb_sync", "lb_destroy", "lb_last_error", "lb_kernel_launches",
            "lb_conservation_noalloc", "lb_set_fv_schedule", "lb_get_fv_schedule",
            "lb_set_fv_scheme", "lb_get_fv_scheme", "lb_set_boundary_density",
+           "lb3_create_grid", "lb3_init", "lb3_step_fv", "lb3_step_st", "lb3_moments",
+           "lb3_conservation", "lb3_nusselt", "lb3_set_populations", "lb3_get_populations", "lb3_sync",
+           "lb3_destroy",
            "lb_autotune_fv", "lb_server_create", "lb_server_submit", "lb_server_pump",
            "lb_server_results", "lb_server_clock", "lb_server_destroy"]
 LB_FV_AUTO, LB_FV_TILE, LB_FV_MARCH, LB_FV_PAIR, LB_FV_PTILE = 0, 1, 2, 3, 4
@@ -125,6 +147,17 @@ def load(build: bool = True) -> C.CDLL:
     L.lb_server_clock.argtypes = [C.c_void_p]
     L.lb_server_clock.restype = C.c_double
     L.lb_server_destroy.argtypes = [C.c_void_p]
+    L.lb3_create_grid.argtypes = [C.POINTER(lb3_grid_desc), C.POINTER(G)]
+    L.lb3_init.argtypes = [G, C.POINTER(lb3_params), C.POINTER(lb3_init_desc)]
+    L.lb3_step_fv.argtypes = [G, C.c_int]
+    L.lb3_step_st.argtypes = [G, C.c_int]
+    L.lb3_moments.argtypes = [G] + [_DP] * 5
+    L.lb3_conservation.argtypes = [G] + [_DP] * 5
+    L.lb3_nusselt.argtypes = [G, _DP, _DP, _DP]
+    L.lb3_set_populations.argtypes = [G, _DP, _DP]
+    L.lb3_get_populations.argtypes = [G, _DP, _DP]
+    L.lb3_sync.argtypes = [G]
+    L.lb3_destroy.argtypes = [G]
     L.lb_sync.argtypes = [G]
     L.lb_destroy.argtypes = [G]
     L.lb_last_error.restype = C.c_char_p
@@ -430,3 +463,94 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+class Grid3:
+    """A D3Q19 grid on the GPU (include/lb3.h).  Arrays are host numpy FP64
+    [nz, ny, nx]; populations [19, nz, ny, nx]."""
+
+    def __init__(self, nx, ny, nz, lx=None, ly=None, lz=None, sx=LB_AXIS_UNIFORM, sy=LB_AXIS_UNIFORM,
+                 sz=LB_AXIS_UNIFORM, stretch_x=0.0, stretch_y=0.0, stretch_z=0.0, bcx=LB_BC_PERIODIC,
+                 bcy=LB_BC_PERIODIC, bcz=LB_BC_PERIODIC, thermal=False, store=LB_STORE_F32, stream=None):
+        if isinstance(store, str):
+            store = STORE_NAMES[store]
+        if stream is None:
+            stream = current_stream_handle()
+        L = [float(n if v is None else v) for v, n in ((lx, nx), (ly, ny), (lz, nz))]
+        self.desc = lb3_grid_desc(int(nx), int(ny), int(nz), *L, int(sx), int(sy), int(sz),
+                                  float(stretch_x), float(stretch_y), float(stretch_z), int(bcx), int(bcy),
+                                  int(bcz), int(bool(thermal)), int(store), C.c_void_p(stream or 0))
+        self.shape = (int(nz), int(ny), int(nx))
+        self.thermal, self.store = bool(thermal), int(store)
+        h = C.c_void_p()
+        _check(load().lb3_create_grid(C.byref(self.desc), C.byref(h)))
+        self._h = h
+
+    @property
+    def cells(self):
+        return self.shape[0] * self.shape[1] * self.shape[2]
+
+    def close(self):
+        if getattr(self, "_h", None) is not None:
+            load().lb3_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def handle(self):
+        return self._h
+
+    def init(self, tau, dt=1.0, tau_g=None, ax=0.0, ay=0.0, az=0.0, beta=0.0, grav=0.0, T0=1.0, T_bot=1.0,
+             T_top=1.0, kind=LB_INIT_FIELDS, u0=0.0, amp=0.0, mode=1, seed=0, rho=None, ux=None, uy=None,
+             uz=None, T=None):
+        self.params = lb3_params(float(tau), float(dt), float(tau if tau_g is None else tau_g), float(ax),
+                                 float(ay), float(az), float(beta), float(grav), float(T0), float(T_bot),
+                                 float(T_top))
+        keep = [_c64(v, self.shape) for v in (rho, ux, uy, uz, T)]
+        d = lb3_init_desc(int(kind), int(mode), float(u0), float(amp), int(seed), *[_ptr(a) for a in keep])
+        _check(load().lb3_init(self._h, C.byref(self.params), C.byref(d)))
+        return self
+
+    def step_fv(self, n=1):
+        _check(load().lb3_step_fv(self._h, int(n)))
+        return self
+
+    def step_st(self, n=1):
+        _check(load().lb3_step_st(self._h, int(n)))
+        return self
+
+    def moments(self):
+        out = [np.zeros(self.shape) for _ in range(5)]
+        _check(load().lb3_moments(self._h, *[_ptr(a) for a in out]))
+        return tuple(out)
+
+    def conservation(self):
+        v = [C.c_double() for _ in range(5)]
+        _check(load().lb3_conservation(self._h, *[C.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
+    def nusselt(self):
+        v = [C.c_double() for _ in range(3)]
+        _check(load().lb3_nusselt(self._h, *[C.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
+    def set_pops(self, f, g=None):
+        f = _c64(f, (19,) + self.shape)
+        g = _c64(g, (19,) + self.shape)
+        _check(load().lb3_set_populations(self._h, _ptr(f), _ptr(g)))
+        return self
+
+    def get_pops(self):
+        f = np.zeros((19,) + self.shape)
+        g = np.zeros((19,) + self.shape) if self.thermal else None
+        _check(load().lb3_get_populations(self._h, _ptr(f), _ptr(g)))
+        return f, g
+
+    def sync(self):
+        _check(load().lb3_sync(self._h))
+        return self

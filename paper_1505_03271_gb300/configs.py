@@ -101,7 +101,7 @@ class Workload:
 
     @property
     def cells(self) -> int:
-        return self.grid["nx"] * self.grid["ny"]
+        return self.grid["nx"] * self.grid["ny"] * self.grid.get("nz", 1)
 
 
 def tgv64(scheme: str = "st") -> Workload:
@@ -143,6 +143,27 @@ def rayleigh_benard(n: int = 1024, Ra: float = 1e8, Pr: float = 1.0, store: int 
                     dict(tau=p.tau, dt=dt, tau_g=p.tau_g, beta=p.beta, grav=p.grav, T0=p.T0,
                          T_bot=p.T_bot, T_top=p.T_top),
                     dict(kind=LB_INIT_RB, amp=amp, seed=seed), steps, "fv")
+
+
+def rb3d_table(scheme: str = "fv", store: int = LB_STORE_F32, steps: int = 20, seed: int = 1234,
+               amp: float = 1e-3) -> Workload:
+    """The 3-D Rayleigh-Benard runs of Table rb (Sec. IV): Ra = 2.5e6, Pr = 1,
+    aspect ratio 2 on 128 x 128 x 64 cells, x and y periodic, plates on z.
+    FV: H = 640, L = 1280, dt = 4, tau = tau_g = 0.5, beta = 1.325e-4, sinh
+    z grid (s2 = 6.5, the stretching of Sec. III B).  ST: H = 64, L = 128,
+    dt = 1, tau = tau_g = 0.05, beta = 1.325e-3, uniform.  dT = 2, g = 1,
+    plates at T0 +- 1 with T0 = 2 (only beta g dT enters).  Conductive,
+    barometric start with a seeded 1e-3 dT perturbation."""
+    fv = scheme == "fv"
+    H, L = (640.0, 1280.0) if fv else (64.0, 128.0)
+    grid = dict(nx=128, ny=128, nz=64, lx=L, ly=L, lz=H, bcz=LB_BC_WALLS, thermal=True, store=store)
+    if fv:
+        grid.update(sz=LB_AXIS_SINH, stretch_z=6.5)
+    tau = 0.5 if fv else 0.05
+    params = dict(tau=tau, tau_g=tau, dt=4.0 if fv else 1.0, beta=1.325e-4 if fv else 1.325e-3, grav=1.0,
+                  T0=2.0, T_bot=3.0, T_top=1.0)
+    return Workload("rb3d_%s_128x128x64" % scheme, grid, params, dict(kind=LB_INIT_RB, amp=amp, seed=seed),
+                    steps, scheme, dict(Ra=params["beta"] * 2.0 * H**3 / (tau * CS2) ** 2))
 
 
 def st_sweep(n: int = 8192, store: int = LB_STORE_F32, steps: int = 500) -> Workload:

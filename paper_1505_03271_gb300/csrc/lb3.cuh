@@ -1,0 +1,78 @@
+// lb3.cuh -- D3Q19 lattice and the argument blocks of the three-dimensional
+// kernels (private to the library; the C ABI is include/lb3.h).
+//
+// Storage holds deviations from a constant reference: f - w and g - w T0
+// (FP64 or FP32).  Gravity acts along -z: a = (ax, ay, az + beta g (T - T0)).
+#pragma once
+
+#include "lb_internal.cuh"
+
+namespace lbgb {
+
+constexpr int Q3 = 19;
+
+// D3Q19 in the order of include/lb3.h: rest; +-x, +-y, +-z; then the twelve
+// edge velocities in opposite pairs (xy, xz, yz planes).  inv(a) = a +- 1.
+__host__ __device__ constexpr int c3x(int a) {
+    return (a == 1 || a == 7 || a == 9 || a == 11 || a == 13) ? 1
+           : (a == 2 || a == 8 || a == 10 || a == 12 || a == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int c3y(int a) {
+    return (a == 3 || a == 7 || a == 10 || a == 15 || a == 17) ? 1
+           : (a == 4 || a == 8 || a == 9 || a == 16 || a == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int c3z(int a) {
+    return (a == 5 || a == 11 || a == 14 || a == 15 || a == 18) ? 1
+           : (a == 6 || a == 12 || a == 13 || a == 16 || a == 17) ? -1 : 0;
+}
+__host__ __device__ constexpr int inv3(int a) { return a == 0 ? 0 : ((a & 1) ? a + 1 : a - 1); }
+template <typename R>
+__host__ __device__ constexpr R w3(int a) {
+    return a == 0 ? R(1) / R(3) : (a <= 6 ? R(1) / R(18) : R(1) / R(36));
+}
+static_assert(c3x(inv3(7)) == -c3x(7) && c3y(inv3(9)) == -c3y(9) && c3z(inv3(18)) == -c3z(18), "inv3");
+
+// Arguments of one 3-D step in compute precision R.
+template <typename R>
+struct Args3 {
+    const void* fin;
+    void* fout;
+    const void* gin;
+    void* gout;
+    R* H;    // [19][N] advected field h' (time n), then reused
+    R* FC;   // [19][N] f' + Coll, then f' + Coll - dt/2 A[h^n]
+    R* HS;   // [19][N] h*'
+    R* HG;   // thermal counterparts
+    R* GC;
+    R* HGS;
+    int n[3];           // nx, ny, nz
+    int bc[3];          // LB_BC_PERIODIC / LB_BC_WALLS per axis
+    long long N;        // nx ny nz
+    AxisMetric<R> m[3]; // QUICK weights and 1/width per axis
+    R dt, om, omh, cf, hf, omg, omgh;
+    R ax, ay, az, bg, T0, dTb, dTt;  // dTb, dTt: plate temperature - T0 (z walls)
+};
+
+struct Aux3 {
+    const void* f;
+    const void* g;
+    int n[3];
+    long long N;
+    double dt, ax, ay, az, bg, T0;
+};
+
+cudaError_t launch3_fv(Prec p, bool th, const void* args, cudaStream_t s);
+cudaError_t launch3_st(Prec p, bool th, const void* args, cudaStream_t s);
+// fields [5][N] (rho, ux, uy, uz, T) on the device -> storage (equilibrium in tilded variables)
+cudaError_t launch3_init(Prec p, bool th, const Aux3& a, const double* fields, void* f, void* g, cudaStream_t s);
+// storage -> fields [5][N]
+cudaError_t launch3_moments(Prec p, bool th, const Aux3& a, double* fields, cudaStream_t s);
+// FP64 [19][N] <-> storage (value - w off)
+cudaError_t launch3_pack(Prec p, const double* src, void* dst, long long N, double off, cudaStream_t s);
+cudaError_t launch3_unpack(Prec p, const void* src, double* dst, long long N, double off, cudaStream_t s);
+// per-plane sums of the observables: out[nz][8] = (sum V rho, sum V rho u (3), sum V T,
+// sum V u_z (T - T0), sum A T, sum V) over the cells of plane k, fixed order
+cudaError_t launch3_plane_sums(const double* fields, const double* dx, const double* dy, const double* dz,
+                               int nx, int ny, int nz, double T0, double* out, cudaStream_t s);
+
+}  // namespace lbgb

@@ -1,0 +1,166 @@
+"""D3Q19 kernels (include/lb3.h) against the FP64 3-D oracle: FV and ST
+steps element by element from random states (FP64 to 1e-13, FP32 to 2e-6 of
+the deviation scale), periodic boxes, walls and plates on stretched grids,
+axes of one cell; the observables; the Rayleigh-Benard workload of Table rb
+at its full size on sampled planes."""
+import numpy as np
+import pytest
+
+from tests import inputs
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    dict(nx=9, ny=7, nz=6),
+    dict(nx=8, ny=6, nz=10, sz=2, stretch_z=4.0, bcz=1, thermal=True),
+    dict(nx=5, ny=12, nz=8, sy=1, stretch_y=1.5, bcy=1, sz=3, bcz=1),
+    dict(nx=1, ny=10, nz=8, lx=1.0, sz=1, stretch_z=2.0, bcz=1, thermal=True),
+    dict(nx=33, ny=9, nz=4, bcx=1),
+]
+
+
+def _ids(c):
+    return "-".join(f"{k}{v}" for k, v in c.items())
+
+
+def _pair(lb, oracle, case, store, **kw):
+    gk = {k: v for k, v in case.items() if k not in ("nx", "ny", "nz")}
+    g = lb.Grid3(case["nx"], case["ny"], case["nz"], store=store, **gk).init(**kw)
+    r = oracle.RefGrid3(case["nx"], case["ny"], case["nz"], **gk).set_params(**kw)
+    return g, r
+
+
+def _params(th):
+    kw = dict(tau=0.3, dt=0.05, ax=2e-4, ay=-1e-4, az=5e-5)
+    if th:
+        kw.update(tau_g=0.25, beta=1e-2, grav=1.0, T0=1.0, T_bot=1.3, T_top=0.8)
+    return kw
+
+
+@pytest.mark.parametrize("store", ["f64", "f32"])
+@pytest.mark.parametrize("case", CASES, ids=_ids)
+def test_fv3_step(lbgpu, oracle, case, store):
+    lb = lbgpu
+    th = case.get("thermal", False)
+    g, r = _pair(lb, oracle, case, lb.STORE_NAMES[store], **_params(th))
+    nx, ny, nz = case["nx"], case["ny"], case["nz"]
+    f = inputs.random_populations3(nx, ny, nz, seed=nx + 7 * nz, amp=0.2)
+    gg = inputs.random_populations3(nx, ny, nz, seed=5, amp=0.2) if th else None
+    g.set_pops(f, gg)
+    f, gg = g.get_pops()
+    r.set_pops(f, gg)
+    g.step_fv(3)
+    r.step_fv(3)
+    w = oracle.lattice3()[3][:, None, None, None]
+    fg, gg2 = g.get_pops()
+    fr, gr = r.get_pops()
+    tol = 1e-13 if store == "f64" else 2e-6 * np.abs(f - w).max()
+    assert np.abs(fg - fr).max() <= tol
+    if th:
+        assert np.abs(gg2 - gr).max() <= (1e-13 if store == "f64" else 2e-6 * np.abs(gg - w).max())
+
+
+@pytest.mark.parametrize("store", ["f64", "f32"])
+@pytest.mark.parametrize("case", [dict(nx=9, ny=7, nz=6), dict(nx=8, ny=6, nz=10, bcz=1, thermal=True),
+                                  dict(nx=6, ny=5, nz=7, bcy=1, bcz=1), dict(nx=1, ny=10, nz=8, bcz=1, thermal=True)],
+                         ids=_ids)
+def test_st3_step(lbgpu, oracle, case, store):
+    lb = lbgpu
+    th = case.get("thermal", False)
+    kw = _params(th)
+    kw["dt"] = 1.0
+    g, r = _pair(lb, oracle, case, lb.STORE_NAMES[store], **kw)
+    nx, ny, nz = case["nx"], case["ny"], case["nz"]
+    f = inputs.random_populations3(nx, ny, nz, seed=11 + nx, amp=0.2)
+    gg = inputs.random_populations3(nx, ny, nz, seed=6, amp=0.2) if th else None
+    g.set_pops(f, gg)
+    f, gg = g.get_pops()
+    r.set_pops(f, gg)
+    g.step_st(4)
+    r.step_st(4)
+    w = oracle.lattice3()[3][:, None, None, None]
+    tol = 1e-13 if store == "f64" else 2e-6 * np.abs(f - w).max()
+    assert np.abs(g.get_pops()[0] - r.get_pops()[0]).max() <= tol
+    if th:
+        assert np.abs(g.get_pops()[1] - r.get_pops()[1]).max() <= (
+            1e-13 if store == "f64" else 2e-6 * np.abs(gg - w).max())
+
+
+@pytest.mark.parametrize("kind", ["tgv", "shear", "rb"])
+def test_presets_and_observables(lbgpu, oracle, kind):
+    """Presets, moments, conservation sums and Nusselt numbers equal the
+    oracle's (FP64) before and after 20 FV steps."""
+    lb = lbgpu
+    if kind == "rb":
+        case = dict(nx=8, ny=6, nz=12, lz=12.0, sz=2, stretch_z=4.0, bcz=1, thermal=True)
+        kw = dict(tau=0.1, tau_g=0.1, dt=0.1, beta=1e-3, grav=1.0, T0=1.0, T_bot=1.5, T_top=0.5)
+        init = dict(kind=lb.LB_INIT_RB, amp=1e-2, seed=1234)
+        okind = oracle.INIT_RB
+    else:
+        case = dict(nx=12, ny=10, nz=8)
+        kw = dict(tau=0.3, dt=0.5)
+        init = dict(kind=lb.LB_INIT_TGV, u0=0.02) if kind == "tgv" else dict(kind=lb.LB_INIT_SHEAR, amp=0.01, mode=2)
+        okind = oracle.INIT_TGV if kind == "tgv" else oracle.INIT_SHEAR
+    gk = {k: v for k, v in case.items() if k not in ("nx", "ny", "nz")}
+    g = lb.Grid3(case["nx"], case["ny"], case["nz"], store=lb.LB_STORE_F64, **gk).init(**kw, **init)
+    r = oracle.RefGrid3(case["nx"], case["ny"], case["nz"], **gk).set_params(**kw)
+    r.init_preset(okind, u0=init.get("u0", 0.0), amp=init.get("amp", 0.0), mode=init.get("mode", 1),
+                  seed=init.get("seed", 0))
+    for steps in (0, 20):
+        g.step_fv(steps)
+        r.step_fv(steps)
+        fields = list(zip(g.moments(), r.moments()))
+        for a, b in fields if kind == "rb" else fields[:4]:  # T is defined on thermal grids only
+            assert np.abs(a - b).max() < 1e-13
+        assert np.allclose(g.conservation(), r.conservation(), rtol=1e-12, atol=1e-14)
+        if kind == "rb":
+            assert np.allclose(g.nusselt(), r.nusselt(), rtol=1e-10, atol=1e-10)
+
+
+def test_errors_and_states(lbgpu):
+    lb = lbgpu
+    with pytest.raises(lb.LBError):
+        lb.Grid3(4, 4, 4, bcx=lb.LB_BC_WALLS, thermal=True)
+    with pytest.raises(lb.LBError):
+        lb.Grid3(4, 4, 5, sz=lb.LB_AXIS_SINH, stretch_z=2.0)
+    with pytest.raises(lb.LBError):
+        lb.Grid3(4, 4, 4, store=lb.LB_STORE_F16DEV)
+    g = lb.Grid3(4, 4, 4)
+    with pytest.raises(lb.LBError) as e:
+        g.step_fv(1)
+    assert e.value.status == lb.LB_ERR_STATE
+    g.init(tau=0.3, dt=0.5)
+    with pytest.raises(lb.LBError) as e:
+        g.step_st(1)
+    assert e.value.status == lb.LB_ERR_ARG
+    with pytest.raises(lb.LBError) as e:
+        g.nusselt()
+    assert e.value.status == lb.LB_ERR_STATE
+
+
+def test_rb_table_grid_sampled(lbgpu, oracle):
+    """The FV workload of Table rb at its full size (128 x 128 x 64, sinh z
+    grid, H = 640, L = 1280, dt = 4, tau = tau_g = 0.5) in FP32: after 2 steps
+    from the seeded RB state the GPU equals the FP64 oracle on every cell to
+    2e-6 of the deviation scale, and conservation holds."""
+    lb = lbgpu
+    from paper_1505_03271_gb300 import configs as cfg
+    w = cfg.rb3d_table("fv")
+    gk = dict(w.grid)
+    store = gk.pop("store")
+    g = lb.Grid3(store=store, **gk).init(**w.params, **w.init)
+    r = oracle.RefGrid3(**gk).set_params(**w.params)
+    oracle.set_threads(8)
+    r.init_preset(oracle.INIT_RB, amp=w.init["amp"], seed=w.init["seed"])
+    f0, g0 = g.get_pops()
+    r.set_pops(f0, g0)
+    m0 = g.conservation()
+    g.step_fv(2)
+    r.step_fv(2)
+    fg, tg = g.get_pops()
+    fr, tr = r.get_pops()
+    wts = oracle.lattice3()[3][:, None, None, None]
+    assert np.abs(fg - fr).max() <= 2e-6 * np.abs(f0 - wts).max()
+    assert np.abs(tg - tr).max() <= 2e-6 * np.abs(g0 - wts).max()
+    m1 = g.conservation()
+    assert abs(m1[0] / m0[0] - 1) < 1e-6 and abs(m1[4] - m0[4]) < 1e-6 * abs(m0[4])

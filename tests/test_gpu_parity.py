@@ -250,7 +250,7 @@ def test_fv_single_stage_schemes(lbgpu, oracle, case, scheme, store):
 DENSITY_CASES = [
     dict(nx=37, ny=20, bcx=2, bcy=1, sy=1, stretch_y=2.0),
     dict(nx=24, ny=33, bcy=2),
-    dict(nx=19, ny=22, bcx=2, bcy=2, sx=2, stretch_x=3.0),
+    dict(nx=20, ny=22, bcx=2, bcy=2, sx=2, stretch_x=3.0),
 ]
 
 
