@@ -110,6 +110,8 @@ def make_grid(lb, w, stream, tune=True):
     unless --fv-schedule fixes one."""
     grid = dict(w.grid)
     store = grid.pop("store")
+    if "nz" in grid:  # D3Q19 grid (include/lb3.h): one schedule
+        return lb.Grid3(store=store, stream=stream, **grid).init(**w.params, **w.init)
     g = lb.Grid(store=store, stream=stream, **grid)
     g.init(**w.params, **w.init)
     if w.scheme == "fv":
@@ -126,6 +128,8 @@ def make_grid(lb, w, stream, tune=True):
 
 
 def schedule_name(lb, g, scheme):
+    if isinstance(g, lb.Grid3):
+        return "3-D fv three passes (collision; predictor; corrector)" if scheme == "fv" else "3-D st push"
     if scheme != "fv":
         if g.store == lb.LB_STORE_F64:
             return "st push, one thread per cell"
@@ -140,7 +144,10 @@ def schedule_name(lb, g, scheme):
 
 def time_steps(lb, torch, g, scheme, steps, warmup, flush=None):
     """Per-step CUDA-event durations (ms) of `steps` single-step launches."""
-    step = lb.lb_step_fv if scheme == "fv" else lb.lb_step_st
+    if isinstance(g, lb.Grid3):
+        step = (lambda h, n: g.step_fv(n)) if scheme == "fv" else (lambda h, n: g.step_st(n))
+    else:
+        step = lb.lb_step_fv if scheme == "fv" else lb.lb_step_st
     for _ in range(warmup):
         step(g.handle, 1)
     torch.cuda.synchronize()
@@ -216,18 +223,20 @@ def extra_lines(lb, torch, cfg, stream, peak, peak_kind, flush):
              ("st8192_f16dev", cfg.st_sweep(8192, lb.LB_STORE_F16DEV), 20, None, None),
              ("fv4096_f32", _fv_big(cfg, 4096), 10, None, None),
              ("fv_rb1024_f16dev", cfg.rayleigh_benard(1024, 1e8), 20, flush, "rb1024"),
-             ("fv_rb1024_f32", cfg.rayleigh_benard(1024, 1e8, store=lb.LB_STORE_F32), 20, flush, None)]
+             ("fv_rb1024_f32", cfg.rayleigh_benard(1024, 1e8, store=lb.LB_STORE_F32), 20, flush, None),
+             ("rb3d_fv_f32", cfg.rb3d_table("fv"), 10, None, "rb3d_fv"),
+             ("rb3d_st_f32", cfg.rb3d_table("st"), 20, None, "rb3d_st")]
     for name, w, k, fl, case in specs:
         g = make_grid(lb, w, stream)
         ms, _ = time_steps(lb, torch, g, w.scheme, k, 3, fl)
         mean = sum(ms) / len(ms)
-        bpc = cfg.bytes_per_cell(w.grid["store"], w.grid.get("thermal", False))
+        bpc = cfg.bytes_per_cell(w.grid["store"], w.grid.get("thermal", False), 19 if "nz" in w.grid else 9)
         sched = schedule_name(lb, g, w.scheme)
         out[name] = {"mlups": round(w.cells / (mean * 1e-3) / 1e6, 1), "ms_per_step": round(mean, 5),
                      "bytes_per_cell": bpc, "schedule": sched,
                      "roofline": roofline(bpc * w.cells, mean, peak, peak_kind,
                                           measured_traffic(sched, case) if case else None),
-                     "roofline_alu": alu_roofline(cfg, w, mean, None),
+                     "roofline_alu": None if "nz" in w.grid else alu_roofline(cfg, w, mean, None),
                      "cells": w.cells, "l2": "flushed" if fl is not None else "state > L2"}
         g.close()
         torch.cuda.empty_cache()
@@ -365,6 +374,8 @@ def case_workload(cfg, name):
         "fv4096": lambda: _fv_big(cfg, 4096),
         "fv2048": lambda: _fv_big(cfg, 2048),
         "rb1024": lambda: cfg.rayleigh_benard(1024, 1e8),
+        "rb3d_fv": lambda: cfg.rb3d_table("fv"),
+        "rb3d_st": lambda: cfg.rb3d_table("st"),
     }
     return table[name]()
 
@@ -375,7 +386,7 @@ def _config(w, case="channel"):
                 "store": w.grid["store"], "thermal": bool(w.grid.get("thermal", False)),
                 "l2": "flushed: 256 MiB write between timed steps"}
     return {"workload": "FV channel %dx%d, tanh delta=2 walls on y, tau=0.2 (ST tau~=0.7), Re=10, "
-                        "FP32 math on f-w storage (BASELINE configs[1])" % (w.grid["nx"], w.grid["ny"]),
+                        "FP32 math on f-w storage" % (w.grid["nx"], w.grid["ny"]),
             "cells": w.cells, "scheme": "fv semi-implicit + Heun + QUICK",
             "dt": round(w.params["dt"], 6), "l2": "flushed: 256 MiB write between timed steps"}
 
@@ -390,7 +401,7 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
     ap.add_argument("--case", default="channel",
                     help="workload to time: channel (headline), st8192, st4096, st4096_f16dev, "
-                         "fv4096, fv2048, rb1024")
+                         "fv4096, fv2048, rb1024, rb3d_fv, rb3d_st (3-D Table rb grids)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving stream")
     ap.add_argument("--serving-requests", type=int, default=160)
     ap.add_argument("--serving-rate", type=float, default=60.0, help="Poisson arrivals per second")
@@ -436,7 +447,7 @@ def main():
     barrier()
     total_s, value = aggregate(sum(ms) * 1e-3, w.cells, args.steps, world, dist, "cuda")
     mean_ms = total_s * 1e3 / args.steps
-    bpc = cfg.bytes_per_cell(w.grid["store"], w.grid.get("thermal", False))
+    bpc = cfg.bytes_per_cell(w.grid["store"], w.grid.get("thermal", False), 19 if "nz" in w.grid else 9)
     dtype = "f64" if w.grid["store"] == lb.LB_STORE_F64 else "f32"
     line = {"metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(mean_ms, 5),
@@ -445,7 +456,7 @@ def main():
             "roofline": roofline(bpc * w.cells, mean_ms, peak, peak_kind,
                                  measured_traffic(schedule_name(lb, g, w.scheme), args.case)),
             "clocks": clk.summary()}
-    line["roofline_alu"] = alu_roofline(cfg, w, mean_ms, line["clocks"])
+    line["roofline_alu"] = None if "nz" in w.grid else alu_roofline(cfg, w, mean_ms, line["clocks"])
     line["config"]["parallelism"] = "replicas" if world > 1 else "single"
     line["config"]["schedule"] = schedule_name(lb, g, w.scheme)
     if not args.no_extra and args.case == "channel":

@@ -54,14 +54,27 @@ struct Cell3 {
         uy = jy * ir + A.hf * A.ay;
         uz = jz * ir + A.hf * az;
     }
+    // the same from the sums sum d, sum c d (3) and sum e
+    __device__ __forceinline__ void from_sums(R r, R jx, R jy, R jz, R td, const Args3<R>& A) {
+        Td = TH ? td : R(0);
+        rp = r;
+        rho = R(1) + r;
+        T = A.T0 + Td;
+        az = A.az + (TH ? A.bg * Td : R(0));
+        const R ir = R(1) / rho;
+        ux = jx * ir + A.hf * A.ax;
+        uy = jy * ir + A.hf * A.ay;
+        uz = jz * ir + A.hf * az;
+    }
     // f_eq - w, Guo force F (Eq. (F2)) and g_eq - w T0
     __device__ __forceinline__ void eq(int a, const Args3<R>& A, R& feqd, R& F, R& geqd) const {
         const R w = w3<R>(a);
-        const R cu = R(c3x(a)) * ux + R(c3y(a)) * uy + R(c3z(a)) * uz;
+        const R cxa = R(c3comp(a, 0)), cya = R(c3comp(a, 1)), cza = R(c3comp(a, 2));
+        const R cu = cxa * ux + cya * uy + cza * uz;
         const R uu = ux * ux + uy * uy + uz * uz;
         const R poly = R(3) * cu + R(4.5) * cu * cu - R(1.5) * uu;
         feqd = w * (rp + rho * poly);
-        const R ca = R(c3x(a)) * A.ax + R(c3y(a)) * A.ay + R(c3z(a)) * az;
+        const R ca = cxa * A.ax + cya * A.ay + cza * az;
         const R ua = ux * A.ax + uy * A.ay + uz * az;
         F = w * rho * (R(3) * (ca - ua) + R(9) * cu * ca);
         geqd = TH ? w * (Td + T * poly) : R(0);
@@ -144,6 +157,89 @@ __device__ __forceinline__ void advect_all(const R* P, int i, int j, int k, cons
     if constexpr (a + 1 < Q3) advect_all<R, G, a + 1>(P, i, j, k, A, out);
 }
 
+
+// Offsets (in cells) of the stencil nodes s = -2..2 along each axis,
+// wrapped once on periodic axes.  `inside` is false when a node falls past
+// a wall, i.e. when the ghost rules are needed.
+struct Nbr3 {
+    int off[3][5];
+    bool inside;
+};
+
+__device__ __forceinline__ Nbr3 neighbours3(const int* n, const int* bc, int i, int j, int k) {
+    Nbr3 nb;
+    nb.inside = true;
+    const int pos[3] = {i, j, k};
+    const int stride[3] = {1, n[0], n[0] * n[1]};
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+#pragma unroll
+        for (int s = -2; s <= 2; ++s) {
+            int p = pos[ax] + s;
+            if (p < 0 || p >= n[ax]) {
+                if (bc[ax] == LB_BC_PERIODIC) {
+                    p = ((p % n[ax]) + n[ax]) % n[ax];
+                } else {
+                    nb.inside = false;
+                    p = pos[ax];
+                }
+            }
+            nb.off[ax][s + 2] = (p - pos[ax]) * stride[ax];
+        }
+    }
+    return nb;
+}
+
+// Flux divergence of population a from in-grid nodes only (Eq. (fv)).
+template <typename R, int a>
+__device__ __forceinline__ R advect3_in(const R* P, long long c, const Nbr3& nb, const int* pos,
+                                        const Args3<R>& A) {
+    const R* base = P + (long long)a * A.N + c;
+    const int cc[3] = {c3x(a), c3y(a), c3z(a)};
+    R v = 0;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        if (cc[ax] == 0) continue;
+        const int m = pos[ax], sh = cc[ax] > 0 ? 0 : 1;
+        R h[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) h[s] = __ldg(base + nb.off[ax][s + sh]);
+        const AxisMetric<R>& M = A.m[ax];
+        if (cc[ax] > 0) {
+            const R pw = M.wp(0, m) * h[0] + M.wp(1, m) * h[1] + M.wp(2, m) * h[2];
+            const R pe = M.wp(0, m + 1) * h[1] + M.wp(1, m + 1) * h[2] + M.wp(2, m + 1) * h[3];
+            v += (pe - pw) * M.invd(m);
+        } else {
+            const R pw = M.wm(0, m) * h[0] + M.wm(1, m) * h[1] + M.wm(2, m) * h[2];
+            const R pe = M.wm(0, m + 1) * h[1] + M.wm(1, m + 1) * h[2] + M.wm(2, m + 1) * h[3];
+            v -= (pe - pw) * M.invd(m);
+        }
+    }
+    return v;
+}
+
+template <typename R, int a>
+__device__ __forceinline__ void advect_all_in(const R* P, long long c, const Nbr3& nb, const int* pos,
+                                              const Args3<R>& A, R* out) {
+    out[a] = advect3_in<R, a>(P, c, nb, pos, A);
+    if constexpr (a + 1 < Q3) advect_all_in<R, a + 1>(P, c, nb, pos, A, out);
+}
+
+// All 19 flux divergences of one cell: direct offsets when the whole
+// stencil is in the grid, the ghost rules otherwise.  A warp shares its z
+// plane, so with plates on z only the two planes next to each plate take
+// the general path and the rest never fetch its instructions.
+template <typename R, bool G>
+__device__ __forceinline__ void advect_cell(const R* P, int i, int j, int k, long long c, const Nbr3& nb,
+                                            const Args3<R>& A, R* out) {
+    if (nb.inside) {
+        const int pos[3] = {i, j, k};
+        advect_all_in<R, 0>(P, c, nb, pos, A, out);
+    } else {
+        advect_all<R, G, 0>(P, i, j, k, A, out);
+    }
+}
+
 __device__ __forceinline__ bool cell_index(const int* n, int& i, int& j, int& k) {
     i = blockIdx.x * blockDim.x + threadIdx.x;
     j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -177,41 +273,89 @@ __global__ void __launch_bounds__(256) k3_pre(const Args3<R> A) {
     }
 }
 
+// Flux divergence of population a (a runtime index: the passes below loop
+// over the populations so that neither their code nor their registers grow
+// with 19 or 38 populations).
+template <typename R, bool G>
+__device__ __forceinline__ R advect_pop(const R* P, int a, int i, int j, int k, long long c, const Nbr3& nb,
+                                        const Args3<R>& A) {
+    const int pos[3] = {i, j, k};
+    const R* base = P + (long long)a * A.N + c;
+    R v = 0;
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        const int cv = c3comp(a, ax);
+        if (cv == 0) continue;
+        const int m = pos[ax];
+        const bool up = cv > 0;  // upwind nodes (m-2, m-1, m, m+1) or (m-1, m, m+1, m+2)
+        R h[4];
+        if (nb.inside) {
+#pragma unroll
+            for (int s = 0; s < 4; ++s) h[s] = __ldg(base + (up ? nb.off[ax][s] : nb.off[ax][s + 1]));
+        } else {
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                int id[3] = {i, j, k};
+                id[ax] = m + s + (up ? -2 : -1);
+                h[s] = hval<R, G>(P, a, id[0], id[1], id[2], A);
+            }
+        }
+        // weights of faces m and m + 1 from the face-major table
+        const R* fw = A.ft[ax] + kFaceRow * m + (up ? 0 : 3);
+        const R* fe = fw + kFaceRow;
+        const R pw = __ldg(fw) * h[0] + __ldg(fw + 1) * h[1] + __ldg(fw + 2) * h[2];
+        const R pe = __ldg(fe) * h[1] + __ldg(fe + 1) * h[2] + __ldg(fe + 2) * h[3];
+        const R invd = __ldg(A.ft[ax] + kFaceRow * m + 6);
+        v += R(cv) * (pe - pw) * invd;
+    }
+    return v;
+}
+
 // ---- FV pass 2: predictor f~* = f~ + Coll - dt A[h^n], then h* ----
+// f~* is parked in the h* buffer while its moments accumulate, then
+// overwritten there by h* (same thread, same addresses).
 template <typename R, bool TH>
 __global__ void __launch_bounds__(256) k3_mid(const Args3<R> A) {
     int i, j, k;
     if (!cell_index(A.n, i, j, k)) return;
     const long long c = cell3(A.n, i, j, k), N = A.N;
-    R fs[Q3], es[Q3];
-    {
-        R adv[Q3];
-        advect_all<R, false, 0>(A.H, i, j, k, A, adv);
-#pragma unroll
-        for (int a = 0; a < Q3; ++a) {
-            const R fc = A.FC[a * N + c];
-            fs[a] = fc - A.dt * adv[a];
-            A.FC[a * N + c] = fc - A.hf * adv[a];
-        }
+    const Nbr3 nb = neighbours3(A.n, A.bc, i, j, k);
+    R r = 0, jx = 0, jy = 0, jz = 0, td = 0;
+#pragma unroll 1
+    for (int a = 0; a < Q3; ++a) {
+        const R adv = advect_pop<R, false>(A.H, a, i, j, k, c, nb, A);
+        const R fc = A.FC[a * N + c];
+        const R fs = fc - A.dt * adv;
+        A.FC[a * N + c] = fc - A.hf * adv;
+        A.HS[a * N + c] = fs;
+        r += fs;
+        jx += R(c3comp(a, 0)) * fs;
+        jy += R(c3comp(a, 1)) * fs;
+        jz += R(c3comp(a, 2)) * fs;
     }
     if constexpr (TH) {
-        R adv[Q3];
-        advect_all<R, true, 0>(A.HG, i, j, k, A, adv);
-#pragma unroll
+#pragma unroll 1
         for (int a = 0; a < Q3; ++a) {
+            const R adv = advect_pop<R, true>(A.HG, a, i, j, k, c, nb, A);
             const R gc = A.GC[a * N + c];
-            es[a] = gc - A.dt * adv[a];
-            A.GC[a * N + c] = gc - A.hf * adv[a];
+            const R es = gc - A.dt * adv;
+            A.GC[a * N + c] = gc - A.hf * adv;
+            A.HGS[a * N + c] = es;
+            td += es;
         }
     }
     Cell3<R, TH> m;
-    m.moments(fs, es, A);
-#pragma unroll
+    m.from_sums(r, jx, jy, jz, td, A);
+#pragma unroll 1
     for (int a = 0; a < Q3; ++a) {
         R feqd, F, geqd;
         m.eq(a, A, feqd, F, geqd);
-        A.HS[a * N + c] = fs[a] + A.omh * (feqd - fs[a]) + A.hf * F;
-        if constexpr (TH) A.HGS[a * N + c] = es[a] + A.omgh * (geqd - es[a]);
+        const R fs = A.HS[a * N + c];
+        A.HS[a * N + c] = fs + A.omh * (feqd - fs) + A.hf * F;
+        if constexpr (TH) {
+            const R es = A.HGS[a * N + c];
+            A.HGS[a * N + c] = es + A.omgh * (geqd - es);
+        }
     }
 }
 
@@ -221,19 +365,17 @@ __global__ void __launch_bounds__(256) k3_post(const Args3<R> A) {
     int i, j, k;
     if (!cell_index(A.n, i, j, k)) return;
     const long long c = cell3(A.n, i, j, k), N = A.N;
-    {
-        R adv[Q3];
-        advect_all<R, false, 0>(A.HS, i, j, k, A, adv);
-        S* out = static_cast<S*>(A.fout);
-#pragma unroll
-        for (int a = 0; a < Q3; ++a) Store<S>::st(out + a * N + c, A.FC[a * N + c] - A.hf * adv[a]);
-    }
+    const Nbr3 nb = neighbours3(A.n, A.bc, i, j, k);
+    S* out = static_cast<S*>(A.fout);
+#pragma unroll 1
+    for (int a = 0; a < Q3; ++a)
+        Store<S>::st(out + a * N + c, A.FC[a * N + c] - A.hf * advect_pop<R, false>(A.HS, a, i, j, k, c, nb, A));
     if constexpr (TH) {
-        R adv[Q3];
-        advect_all<R, true, 0>(A.HGS, i, j, k, A, adv);
-        S* out = static_cast<S*>(A.gout);
-#pragma unroll
-        for (int a = 0; a < Q3; ++a) Store<S>::st(out + a * N + c, A.GC[a * N + c] - A.hf * adv[a]);
+        S* gout = static_cast<S*>(A.gout);
+#pragma unroll 1
+        for (int a = 0; a < Q3; ++a)
+            Store<S>::st(gout + a * N + c,
+                         A.GC[a * N + c] - A.hf * advect_pop<R, true>(A.HGS, a, i, j, k, c, nb, A));
     }
 }
 

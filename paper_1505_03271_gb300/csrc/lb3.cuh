@@ -32,6 +32,23 @@ __host__ __device__ constexpr R w3(int a) {
 }
 static_assert(c3x(inv3(7)) == -c3x(7) && c3y(inv3(9)) == -c3y(9) && c3z(inv3(18)) == -c3z(18), "inv3");
 
+// The same velocities packed 2 bits per population (value c + 1), one word
+// per component, for loops over a runtime population index.
+__host__ __device__ constexpr unsigned long long pack3(int ax, int a) {
+    return a < 0 ? 0ULL
+                 : pack3(ax, a - 1) |
+                       ((unsigned long long)((ax == 0 ? c3x(a) : ax == 1 ? c3y(a) : c3z(a)) + 1) << (2 * a));
+}
+__host__ __device__ constexpr int c3comp(int a, int ax) {
+    return (int)(((ax == 0 ? pack3(0, Q3 - 1) : ax == 1 ? pack3(1, Q3 - 1) : pack3(2, Q3 - 1)) >> (2 * a)) & 3ULL) - 1;
+}
+static_assert(c3comp(13, 0) == 1 && c3comp(13, 2) == -1 && c3comp(10, 1) == 1 && c3comp(0, 2) == 0, "pack");
+
+// Face-major metric of one axis: for face k (k = 0..n) eight values
+// [wp0 wp1 wp2 wm0 wm1 wm2 1/dx_k 0] (1/dx of cell k; 0 for k = n), so that a
+// thread reads the weights of its two faces at fixed offsets.
+constexpr int kFaceRow = 8;
+
 // Arguments of one 3-D step in compute precision R.
 template <typename R>
 struct Args3 {
@@ -49,6 +66,7 @@ struct Args3 {
     int bc[3];          // LB_BC_PERIODIC / LB_BC_WALLS per axis
     long long N;        // nx ny nz
     AxisMetric<R> m[3]; // QUICK weights and 1/width per axis
+    const R* ft[3];     // the same, face-major (kFaceRow values per face)
     R dt, om, omh, cf, hf, omg, omgh;
     R ax, ay, az, bg, T0, dTb, dTt;  // dTb, dTt: plate temperature - T0 (z walls)
 };

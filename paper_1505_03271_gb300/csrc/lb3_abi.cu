@@ -30,6 +30,7 @@ struct lb3_grid {
     int cur = 0;
     void* work[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};  // H, FC, HS, HG, GC, HGS
     void* metric[3] = {nullptr, nullptr, nullptr};
+    void* faces[3] = {nullptr, nullptr, nullptr};  // face-major metric
     double* width[3] = {nullptr, nullptr, nullptr};
     double* fields = nullptr;  // [5][N] staging
     double* plane = nullptr;   // [nz][8] plane sums
@@ -67,6 +68,7 @@ void release3(lb3_grid* G) {
         if (q) cudaFree(q);
     for (int a = 0; a < 3; ++a) {
         if (G->metric[a]) cudaFree(G->metric[a]);
+        if (G->faces[a]) cudaFree(G->faces[a]);
         if (G->width[a]) cudaFree(G->width[a]);
     }
     if (G->fields) cudaFree(G->fields);
@@ -90,6 +92,7 @@ Args3<R> args3(const lb3_grid* G, bool st) {
         A.n[a] = G->n[a];
         A.bc[a] = G->ax[a].bc;
         A.m[a] = AxisMetric<R>{static_cast<const R*>(G->metric[a]), G->n[a] + 1};
+        A.ft[a] = static_cast<const R*>(G->faces[a]);
     }
     A.N = G->N;
     const lb3_params& p = G->p;
@@ -194,13 +197,23 @@ lb_status lb3_create_grid(const lb3_grid_desc* d, lb3_grid** out) {
     for (int w = 0; w < 3 * sets && e == cudaSuccess; ++w) e = cudaMalloc(&G->work[w], pop);
     for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
         const std::vector<double> m = G->ax[a].metric();
+        const int n1 = n[a] + 1;
+        std::vector<double> fm((size_t)kFaceRow * n1, 0.0);
+        for (int k = 0; k < n1; ++k) {
+            for (int r = 0; r < 6; ++r) fm[(size_t)kFaceRow * k + r] = m[(size_t)r * n1 + k];
+            if (k < n[a]) fm[(size_t)kFaceRow * k + 6] = m[(size_t)6 * n1 + k];
+        }
         if (G->prec == Prec::F64) {
             e = cudaMalloc(&G->metric[a], sizeof(double) * m.size());
             if (e == cudaSuccess) e = cudaMemcpy(G->metric[a], m.data(), sizeof(double) * m.size(), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMalloc(&G->faces[a], sizeof(double) * fm.size());
+            if (e == cudaSuccess) e = cudaMemcpy(G->faces[a], fm.data(), sizeof(double) * fm.size(), cudaMemcpyHostToDevice);
         } else {
-            std::vector<float> mf(m.begin(), m.end());
+            std::vector<float> mf(m.begin(), m.end()), ff(fm.begin(), fm.end());
             e = cudaMalloc(&G->metric[a], sizeof(float) * mf.size());
             if (e == cudaSuccess) e = cudaMemcpy(G->metric[a], mf.data(), sizeof(float) * mf.size(), cudaMemcpyHostToDevice);
+            if (e == cudaSuccess) e = cudaMalloc(&G->faces[a], sizeof(float) * ff.size());
+            if (e == cudaSuccess) e = cudaMemcpy(G->faces[a], ff.data(), sizeof(float) * ff.size(), cudaMemcpyHostToDevice);
         }
         if (e == cudaSuccess) e = cudaMalloc(&G->width[a], sizeof(double) * n[a]);
         if (e == cudaSuccess)

@@ -78,6 +78,7 @@ struct AxisMetric {
     __device__ R wp(int r, int k) const { return __ldg(m + r * n1 + k); }
     __device__ R wm(int r, int k) const { return __ldg(m + (3 + r) * n1 + k); }
     __device__ R invd(int i) const { return __ldg(m + 6 * n1 + i); }
+    __device__ R row(int r, int k) const { return __ldg(m + r * n1 + k); }  // r = 0..2 wp, 3..5 wm
 };
 
 // Parameters of one step, in compute precision R.

@@ -112,7 +112,9 @@ def test_presets_and_observables(lbgpu, oracle, kind):
         fields = list(zip(g.moments(), r.moments()))
         for a, b in fields if kind == "rb" else fields[:4]:  # T is defined on thermal grids only
             assert np.abs(a - b).max() < 1e-13
-        assert np.allclose(g.conservation(), r.conservation(), rtol=1e-12, atol=1e-14)
+        nc = 5 if kind == "rb" else 4  # heat is defined on thermal grids only
+        # momenta cancel to rounding (~1e-14) on these symmetric states
+        assert np.allclose(g.conservation()[:nc], r.conservation()[:nc], rtol=1e-12, atol=1e-12)
         if kind == "rb":
             assert np.allclose(g.nusselt(), r.nusselt(), rtol=1e-10, atol=1e-10)
 
@@ -142,7 +144,8 @@ def test_rb_table_grid_sampled(lbgpu, oracle):
     """The FV workload of Table rb at its full size (128 x 128 x 64, sinh z
     grid, H = 640, L = 1280, dt = 4, tau = tau_g = 0.5) in FP32: after 2 steps
     from the seeded RB state the GPU equals the FP64 oracle on every cell to
-    2e-6 of the deviation scale, and conservation holds."""
+    2e-6 of the deviation scale, and mass is conserved (heat is not: it
+    crosses the isothermal plates)."""
     lb = lbgpu
     from paper_1505_03271_gb300 import configs as cfg
     w = cfg.rb3d_table("fv")
@@ -163,4 +166,4 @@ def test_rb_table_grid_sampled(lbgpu, oracle):
     assert np.abs(fg - fr).max() <= 2e-6 * np.abs(f0 - wts).max()
     assert np.abs(tg - tr).max() <= 2e-6 * np.abs(g0 - wts).max()
     m1 = g.conservation()
-    assert abs(m1[0] / m0[0] - 1) < 1e-6 and abs(m1[4] - m0[4]) < 1e-6 * abs(m0[4])
+    assert abs(m1[0] / m0[0] - 1) < 1e-8
