@@ -4,17 +4,20 @@
 // ST, Eq. (ST): one fused collide-and-push kernel, one thread per cell;
 // half-way bounce-back at walls, anti-bounce-back of g at the z plates.
 //
-// FV, Eqs. (semi) and (semi-heun): three passes over the grid, each a plain
-// per-cell kernel, with the intermediate fields in HBM:
-//   k3_pre   f~ -> h^n and f~ + Coll^n                       (local)
-//   k3_mid   A[h^n] (QUICK on the cross stencil, ghosts formed on the fly)
-//            -> f~* = f~ + Coll - dt A, h*, and f~ + Coll - dt/2 A
-//   k3_post  A[h*] -> f~^(n+1) = f~ + Coll - dt/2 (A[h^n] + A[h*])
+// FV, Eqs. (semi) and (semi-heun): four passes over the grid with the
+// intermediate fields in HBM, plus two small ghost-plane fills:
+//   k3_pre          f~ -> h^n and f~ + Coll^n                           (local)
+//   k3_ghostz       z ghost planes of h^n (walls: Sec. II B 5)
+//   k3_adv (pred.)  A[h^n] per population (QUICK on its own stencil)
+//                   -> f~* (parked), f~ + Coll - dt/2 A
+//   k3_star         moments of f~* -> h*                                (local)
+//   k3_ghostz       z ghost planes of h*
+//   k3_adv (corr.)  A[h*] -> f~^(n+1) = f~ + Coll - dt/2 (A[h^n] + A[h*])
 // A fused 3-D tile would recompute a 4-cell halo on all six faces, or hold
-// 19 (38) populations of several halo planes in shared memory; three passes
-// recompute nothing and move 5x the compulsory bytes, which keeps the step
-// on the HBM roof.  Faces are taken dimension by dimension from the nodes of
-// their own grid line (Sec. II B 3), so only face ghosts are ever read.
+// 19 (38) populations of several halo planes in shared memory; these passes
+// recompute nothing and stream about 6x the compulsory bytes.  Faces are
+// taken dimension by dimension from the nodes of their own grid line
+// (Sec. II B 3), so only face ghosts are ever read.
 #include "lb3.cuh"
 
 namespace lbgb {
@@ -88,156 +91,36 @@ __device__ __forceinline__ void load19(const void* src, long long N, long long c
     for (int a = 0; a < Q3; ++a) d[a] = (R)Store<S>::ld(p + a * N + c);
 }
 
-// Advected-field value of population a at (i, j, k), where at most one
-// index lies outside the grid: periodic axes wrap, walls mirror the node and
-// reflect the population, h_a(ghost) = h_inv(a)(node) (Sec. II B 5); the
-// thermal field is anti-reflected at the z plates,
-// hg'_a(ghost) = 2 w_a (T_wall - T0) - hg'_inv(a)(node).
-template <typename R, bool G>
-__device__ __forceinline__ R hval(const R* P, int a, int i, int j, int k, const Args3<R>& A) {
-    int idx[3] = {i, j, k};
+// Padded layout of the advected fields h, h* (and hg, hg*): two ghost
+// planes below and above the grid in z, [pop][nz + 4][ny][nx], so that the
+// z stencil never leaves the array.  k3_ghostz fills the ghost planes:
+// periodic copies, or the wall rules of Sec. II B 5 (double reflection,
+// h_a(ghost) = h_inv(a)(mirror); the thermal field anti-reflected,
+// hg'_a(ghost) = 2 w_a (T_wall - T0) - hg'_inv(a)(mirror)).
+__device__ __forceinline__ long long padded3(const int* n, int i, int j, int k) {
+    return ((long long)(k + 2) * n[1] + j) * n[0] + i;
+}
+
+// Advected-field value at (i, j, padded plane k + 2) when i or j lies
+// outside the grid (never both: the stencil is a cross): periodic wrap or
+// wall mirror with the reflected population.  Thermal grids are periodic in
+// x and y, so only the flow field meets these walls.
+template <typename R>
+__device__ __forceinline__ R hval_xy(const R* P, int a, int i, int j, int k, const Args3<R>& A) {
+    int idx[2] = {i, j};
     int b = a;
-    bool flip = false;
-    R wallv = 0;
 #pragma unroll
-    for (int ax = 0; ax < 3; ++ax) {
+    for (int ax = 0; ax < 2; ++ax) {
         const int n = A.n[ax];
         if (idx[ax] >= 0 && idx[ax] < n) continue;
         if (A.bc[ax] == LB_BC_PERIODIC) {
-            idx[ax] = ((idx[ax] % n) + n) % n;  // axes of 1 or 2 cells wrap more than once
+            idx[ax] = ((idx[ax] % n) + n) % n;
         } else {
-            const bool lo = idx[ax] < 0;
-            idx[ax] = lo ? -idx[ax] - 1 : 2 * n - 1 - idx[ax];
+            idx[ax] = idx[ax] < 0 ? -idx[ax] - 1 : 2 * n - 1 - idx[ax];
             b = inv3(a);
-            if (G) {
-                flip = true;
-                wallv = R(2) * w3<R>(a) * (lo ? A.dTb : A.dTt);
-            }
         }
     }
-    const R v = __ldg(P + (long long)b * A.N + cell3(A.n, idx[0], idx[1], idx[2]));
-    return flip ? wallv - v : v;
-}
-
-// Flux divergence of population a at (i, j, k), Eq. (fv): for each axis
-// with c != 0, c (Phi_+ - Phi_-) / width with QUICK faces.
-template <typename R, bool G, int a>
-__device__ __forceinline__ R advect3(const R* P, int i, int j, int k, const Args3<R>& A) {
-    R v = 0;
-    const int cc[3] = {c3x(a), c3y(a), c3z(a)};
-    const int pos[3] = {i, j, k};
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax) {
-        if (cc[ax] == 0) continue;
-        const int m = pos[ax];
-        R h[4];
-#pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            int id[3] = {i, j, k};
-            id[ax] = m + s + (cc[ax] > 0 ? -2 : -1);
-            h[s] = hval<R, G>(P, a, id[0], id[1], id[2], A);
-        }
-        const AxisMetric<R>& M = A.m[ax];
-        if (cc[ax] > 0) {
-            const R pw = M.wp(0, m) * h[0] + M.wp(1, m) * h[1] + M.wp(2, m) * h[2];
-            const R pe = M.wp(0, m + 1) * h[1] + M.wp(1, m + 1) * h[2] + M.wp(2, m + 1) * h[3];
-            v += (pe - pw) * M.invd(m);
-        } else {
-            const R pw = M.wm(0, m) * h[0] + M.wm(1, m) * h[1] + M.wm(2, m) * h[2];
-            const R pe = M.wm(0, m + 1) * h[1] + M.wm(1, m + 1) * h[2] + M.wm(2, m + 1) * h[3];
-            v -= (pe - pw) * M.invd(m);
-        }
-    }
-    return v;
-}
-
-template <typename R, bool G, int a>
-__device__ __forceinline__ void advect_all(const R* P, int i, int j, int k, const Args3<R>& A, R* out) {
-    out[a] = advect3<R, G, a>(P, i, j, k, A);
-    if constexpr (a + 1 < Q3) advect_all<R, G, a + 1>(P, i, j, k, A, out);
-}
-
-
-// Offsets (in cells) of the stencil nodes s = -2..2 along each axis,
-// wrapped once on periodic axes.  `inside` is false when a node falls past
-// a wall, i.e. when the ghost rules are needed.
-struct Nbr3 {
-    int off[3][5];
-    bool inside;
-};
-
-__device__ __forceinline__ Nbr3 neighbours3(const int* n, const int* bc, int i, int j, int k) {
-    Nbr3 nb;
-    nb.inside = true;
-    const int pos[3] = {i, j, k};
-    const int stride[3] = {1, n[0], n[0] * n[1]};
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax) {
-#pragma unroll
-        for (int s = -2; s <= 2; ++s) {
-            int p = pos[ax] + s;
-            if (p < 0 || p >= n[ax]) {
-                if (bc[ax] == LB_BC_PERIODIC) {
-                    p = ((p % n[ax]) + n[ax]) % n[ax];
-                } else {
-                    nb.inside = false;
-                    p = pos[ax];
-                }
-            }
-            nb.off[ax][s + 2] = (p - pos[ax]) * stride[ax];
-        }
-    }
-    return nb;
-}
-
-// Flux divergence of population a from in-grid nodes only (Eq. (fv)).
-template <typename R, int a>
-__device__ __forceinline__ R advect3_in(const R* P, long long c, const Nbr3& nb, const int* pos,
-                                        const Args3<R>& A) {
-    const R* base = P + (long long)a * A.N + c;
-    const int cc[3] = {c3x(a), c3y(a), c3z(a)};
-    R v = 0;
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax) {
-        if (cc[ax] == 0) continue;
-        const int m = pos[ax], sh = cc[ax] > 0 ? 0 : 1;
-        R h[4];
-#pragma unroll
-        for (int s = 0; s < 4; ++s) h[s] = __ldg(base + nb.off[ax][s + sh]);
-        const AxisMetric<R>& M = A.m[ax];
-        if (cc[ax] > 0) {
-            const R pw = M.wp(0, m) * h[0] + M.wp(1, m) * h[1] + M.wp(2, m) * h[2];
-            const R pe = M.wp(0, m + 1) * h[1] + M.wp(1, m + 1) * h[2] + M.wp(2, m + 1) * h[3];
-            v += (pe - pw) * M.invd(m);
-        } else {
-            const R pw = M.wm(0, m) * h[0] + M.wm(1, m) * h[1] + M.wm(2, m) * h[2];
-            const R pe = M.wm(0, m + 1) * h[1] + M.wm(1, m + 1) * h[2] + M.wm(2, m + 1) * h[3];
-            v -= (pe - pw) * M.invd(m);
-        }
-    }
-    return v;
-}
-
-template <typename R, int a>
-__device__ __forceinline__ void advect_all_in(const R* P, long long c, const Nbr3& nb, const int* pos,
-                                              const Args3<R>& A, R* out) {
-    out[a] = advect3_in<R, a>(P, c, nb, pos, A);
-    if constexpr (a + 1 < Q3) advect_all_in<R, a + 1>(P, c, nb, pos, A, out);
-}
-
-// All 19 flux divergences of one cell: direct offsets when the whole
-// stencil is in the grid, the ghost rules otherwise.  A warp shares its z
-// plane, so with plates on z only the two planes next to each plate take
-// the general path and the rest never fetch its instructions.
-template <typename R, bool G>
-__device__ __forceinline__ void advect_cell(const R* P, int i, int j, int k, long long c, const Nbr3& nb,
-                                            const Args3<R>& A, R* out) {
-    if (nb.inside) {
-        const int pos[3] = {i, j, k};
-        advect_all_in<R, 0>(P, c, nb, pos, A, out);
-    } else {
-        advect_all<R, G, 0>(P, i, j, k, A, out);
-    }
+    return __ldg(P + (long long)b * A.NP + padded3(A.n, idx[0], idx[1], k));
 }
 
 __device__ __forceinline__ bool cell_index(const int* n, int& i, int& j, int& k) {
@@ -252,7 +135,7 @@ template <typename R, typename S, bool TH>
 __global__ void __launch_bounds__(256) k3_pre(const Args3<R> A) {
     int i, j, k;
     if (!cell_index(A.n, i, j, k)) return;
-    const long long c = cell3(A.n, i, j, k), N = A.N;
+    const long long c = cell3(A.n, i, j, k), N = A.N, cp = padded3(A.n, i, j, k), NP = A.NP;
     R d[Q3], e[Q3];
     load19<S>(A.fin, N, c, d);
     if constexpr (TH) load19<S>(A.gin, N, c, e);
@@ -263,119 +146,210 @@ __global__ void __launch_bounds__(256) k3_pre(const Args3<R> A) {
         R feqd, F, geqd;
         m.eq(a, A, feqd, F, geqd);
         const R neq = feqd - d[a];
-        A.H[a * N + c] = d[a] + A.omh * neq + A.hf * F;
+        A.H[a * NP + cp] = d[a] + A.omh * neq + A.hf * F;
         A.FC[a * N + c] = d[a] + A.om * neq + A.cf * F;
         if constexpr (TH) {
             const R neqg = geqd - e[a];
-            A.HG[a * N + c] = e[a] + A.omgh * neqg;
+            A.HG[a * NP + cp] = e[a] + A.omgh * neqg;
             A.GC[a * N + c] = e[a] + A.omg * neqg;
         }
     }
 }
 
-// Flux divergence of population a (a runtime index: the passes below loop
-// over the populations so that neither their code nor their registers grow
-// with 19 or 38 populations).
-template <typename R, bool G>
-__device__ __forceinline__ R advect_pop(const R* P, int a, int i, int j, int k, long long c, const Nbr3& nb,
-                                        const Args3<R>& A) {
-    const int pos[3] = {i, j, k};
-    const R* base = P + (long long)a * A.N + c;
-    R v = 0;
-#pragma unroll
-    for (int ax = 0; ax < 3; ++ax) {
-        const int cv = c3comp(a, ax);
-        if (cv == 0) continue;
-        const int m = pos[ax];
-        const bool up = cv > 0;  // upwind nodes (m-2, m-1, m, m+1) or (m-1, m, m+1, m+2)
-        R h[4];
-        if (nb.inside) {
-#pragma unroll
-            for (int s = 0; s < 4; ++s) h[s] = __ldg(base + (up ? nb.off[ax][s] : nb.off[ax][s + 1]));
-        } else {
-#pragma unroll
-            for (int s = 0; s < 4; ++s) {
-                int id[3] = {i, j, k};
-                id[ax] = m + s + (up ? -2 : -1);
-                h[s] = hval<R, G>(P, a, id[0], id[1], id[2], A);
-            }
-        }
-        // weights of faces m and m + 1 from the face-major table
-        const R* fw = A.ft[ax] + kFaceRow * m + (up ? 0 : 3);
-        const R* fe = fw + kFaceRow;
-        const R pw = __ldg(fw) * h[0] + __ldg(fw + 1) * h[1] + __ldg(fw + 2) * h[2];
-        const R pe = __ldg(fe) * h[1] + __ldg(fe + 1) * h[2] + __ldg(fe + 2) * h[3];
-        const R invd = __ldg(A.ft[ax] + kFaceRow * m + 6);
-        v += R(cv) * (pe - pw) * invd;
+// ---- z ghost planes of h (star = 0) or h* (star = 1) ----
+// blockIdx.z = ghost * np + p, ghost 0..3 -> planes -2, -1, nz, nz + 1.
+template <typename R>
+__global__ void __launch_bounds__(256) k3_ghostz(const Args3<R> A, int star, int np) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= A.n[0] || j >= A.n[1]) return;
+    const int p = blockIdx.z % np, gh = blockIdx.z / np;
+    const bool th = p >= Q3;
+    const int a = th ? p - Q3 : p, nz = A.n[2];
+    const int gk = gh < 2 ? gh - 2 : nz + gh - 2;
+    R* P = th ? (star ? A.HGS : A.HG) : (star ? A.HS : A.H);
+    R v;
+    if (A.bc[2] == LB_BC_PERIODIC) {
+        const int src = ((gk % nz) + nz) % nz;
+        v = P[(long long)a * A.NP + padded3(A.n, i, j, src)];
+    } else {
+        const bool lo = gk < 0;
+        const int src = lo ? -gk - 1 : 2 * nz - 1 - gk;
+        v = P[(long long)inv3(a) * A.NP + padded3(A.n, i, j, src)];
+        if (th) v = R(2) * w3<R>(a) * (lo ? A.dTb : A.dTt) - v;
     }
-    return v;
+    P[(long long)a * A.NP + padded3(A.n, i, j, gk)] = v;
 }
 
-// ---- FV pass 2: predictor f~* = f~ + Coll - dt A[h^n], then h* ----
-// f~* is parked in the h* buffer while its moments accumulate, then
-// overwritten there by h* (same thread, same addresses).
+// ---- FV flux passes, one population per CTA ----
+// The flux of population a reads only population a's own advected field,
+// so the predictor's and the corrector's flux passes run one population per
+// CTA: a 32 x 8 block of columns marches up a chunk of z planes, keeping
+// the four z-stencil nodes of its column in registers (one new value per
+// plane; the padded ghost planes make every z node a plain load).  The x
+// and y node offsets and weights of a column are set once.
+//   predictor (CORR = false): f~* = f~ + Coll - dt A[h^n] into the h* buffer
+//                             (parked until k3_star), f~ + Coll -= dt/2 A
+//   corrector (CORR = true):  f~^(n+1) = (f~ + Coll - dt/2 A[h^n]) - dt/2 A[h*]
+// blockIdx.z = chunk * np + p; p < 19 flow, p >= 19 thermal population p - 19.
+
+// x or y stencil offsets of a column: nodes s = -2..2 (wrapped once on
+// periodic axes); `in` is false when a node lies past a wall.
+struct Line5 {
+    int off[5];
+    bool in;
+};
+
+__device__ __forceinline__ Line5 line5(int pos, int n, int bc, int stride) {
+    Line5 L;
+    L.in = true;
+#pragma unroll
+    for (int s = -2; s <= 2; ++s) {
+        int p = pos + s;
+        if (p < 0 || p >= n) {
+            if (bc == LB_BC_PERIODIC) p = ((p % n) + n) % n;
+            else { L.in = false; p = pos; }
+        }
+        L.off[s + 2] = (p - pos) * stride;
+    }
+    return L;
+}
+
+// QUICK weights of one axis at cell m for the sign of c: west-face and
+// east-face triples and 1/width (row-major metric).
+template <typename R>
+struct AxisW {
+    R w[3], e[3], inv;
+    __device__ __forceinline__ void load(const AxisMetric<R>& M, int m, int cv) {
+        const int r0 = cv > 0 ? 0 : 3;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            w[r] = M.row(r0 + r, m);
+            e[r] = M.row(r0 + r, m + 1);
+        }
+        inv = M.invd(m);
+    }
+    __device__ __forceinline__ R div(int cv, const R* h) const {
+        const R pw = w[0] * h[0] + w[1] * h[1] + w[2] * h[2];
+        const R pe = e[0] * h[1] + e[1] * h[2] + e[2] * h[3];
+        return R(cv) * (pe - pw) * inv;
+    }
+};
+
+template <typename R, typename S, bool CORR, bool G, bool FAST>
+__device__ __forceinline__ void adv_pop_column(const Args3<R>& A, int a, int i, int j, int k0, int k1,
+                                               const Line5& lx, const Line5& ly) {
+    const long long N = A.N, NP = A.NP;
+    const int nx = A.n[0], ny = A.n[1];
+    const long long plane = (long long)nx * ny;
+    const R* P = G ? (CORR ? A.HGS : A.HG) : (CORR ? A.HS : A.H);
+    R* FCp = G ? A.GC : A.FC;
+    R* park = G ? A.HGS : A.HS;
+    const int cx = c3comp(a, 0), cy = c3comp(a, 1), cz = c3comp(a, 2);
+    const R* col = P + (long long)a * NP + (long long)j * nx + i;  // padded plane 0 of this column
+    AxisW<R> WX, WY;
+    int ox[4] = {0, 0, 0, 0}, oy[4] = {0, 0, 0, 0};
+    if (cx != 0) {
+        WX.load(A.m[0], i, cx);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) ox[s] = cx > 0 ? lx.off[s] : lx.off[s + 1];
+    }
+    if (cy != 0) {
+        WY.load(A.m[1], j, cy);
+#pragma unroll
+        for (int s = 0; s < 4; ++s) oy[s] = cy > 0 ? ly.off[s] : ly.off[s + 1];
+    }
+    const int zs = cz > 0 ? -2 : -1;  // z nodes (k-2..k+1) or (k-1..k+2)
+    R zr[4] = {0, 0, 0, 0};
+    if (cz != 0) {
+#pragma unroll
+        for (int s = 0; s < 3; ++s) zr[s] = __ldg(col + (long long)(k0 + zs + s + 2) * plane);
+    }
+    for (int k = k0; k < k1; ++k) {
+        const R* cp = col + (long long)(k + 2) * plane;
+        R v = 0;
+        if (cx != 0) {
+            R h[4];
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                h[s] = FAST ? __ldg(cp + ox[s]) : hval_xy<R>(P, a, i + s + (cx > 0 ? -2 : -1), j, k, A);
+            v += WX.div(cx, h);
+        }
+        if (cy != 0) {
+            R h[4];
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+                h[s] = FAST ? __ldg(cp + oy[s]) : hval_xy<R>(P, a, i, j + s + (cy > 0 ? -2 : -1), k, A);
+            v += WY.div(cy, h);
+        }
+        if (cz != 0) {
+            zr[3] = __ldg(cp + (long long)(zs + 3) * plane);
+            const R* fz = A.ft[2] + kFaceRow * k + (cz > 0 ? 0 : 3);  // uniform over the block
+            const R pw = __ldg(fz) * zr[0] + __ldg(fz + 1) * zr[1] + __ldg(fz + 2) * zr[2];
+            const R pe = __ldg(fz + kFaceRow) * zr[1] + __ldg(fz + kFaceRow + 1) * zr[2] +
+                         __ldg(fz + kFaceRow + 2) * zr[3];
+            v += R(cz) * (pe - pw) * __ldg(A.ft[2] + kFaceRow * k + 6);
+            zr[0] = zr[1];
+            zr[1] = zr[2];
+            zr[2] = zr[3];
+        }
+        const long long q = (long long)a * N + (long long)k * plane + (long long)j * nx + i;
+        const R fc = FCp[q];
+        if constexpr (CORR) {
+            S* out = static_cast<S*>(G ? A.gout : A.fout);
+            Store<S>::st(out + q, fc - A.hf * v);
+        } else {
+            FCp[q] = fc - A.hf * v;
+            park[(long long)a * NP + (long long)(k + 2) * plane + (long long)j * nx + i] = fc - A.dt * v;
+        }
+    }
+}
+
+template <typename R, typename S, bool CORR>
+__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) k3_adv(const Args3<R> A, int np, int kc) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int j = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= A.n[0] || j >= A.n[1]) return;
+    const int p = blockIdx.z % np, chunk = blockIdx.z / np;
+    const int k0 = chunk * kc, k1 = min(k0 + kc, A.n[2]);
+    const Line5 lx = line5(i, A.n[0], A.bc[0], 1), ly = line5(j, A.n[1], A.bc[1], A.n[0]);
+    const bool fast = lx.in && ly.in;
+    if (p < Q3) {
+        if (fast) adv_pop_column<R, S, CORR, false, true>(A, p, i, j, k0, k1, lx, ly);
+        else adv_pop_column<R, S, CORR, false, false>(A, p, i, j, k0, k1, lx, ly);
+    } else {
+        // thermal grids are periodic in x and y: always the plain path
+        adv_pop_column<R, S, CORR, true, true>(A, p - Q3, i, j, k0, k1, lx, ly);
+    }
+}
+
+// ---- FV: moments of f~* (parked in the h* buffers) and h* ----
 template <typename R, bool TH>
-__global__ void __launch_bounds__(256) k3_mid(const Args3<R> A) {
+__global__ void __launch_bounds__(256) k3_star(const Args3<R> A) {
     int i, j, k;
     if (!cell_index(A.n, i, j, k)) return;
-    const long long c = cell3(A.n, i, j, k), N = A.N;
-    const Nbr3 nb = neighbours3(A.n, A.bc, i, j, k);
+    const long long cp = padded3(A.n, i, j, k), NP = A.NP;
     R r = 0, jx = 0, jy = 0, jz = 0, td = 0;
-#pragma unroll 1
+#pragma unroll
     for (int a = 0; a < Q3; ++a) {
-        const R adv = advect_pop<R, false>(A.H, a, i, j, k, c, nb, A);
-        const R fc = A.FC[a * N + c];
-        const R fs = fc - A.dt * adv;
-        A.FC[a * N + c] = fc - A.hf * adv;
-        A.HS[a * N + c] = fs;
+        const R fs = A.HS[a * NP + cp];
         r += fs;
-        jx += R(c3comp(a, 0)) * fs;
-        jy += R(c3comp(a, 1)) * fs;
-        jz += R(c3comp(a, 2)) * fs;
-    }
-    if constexpr (TH) {
-#pragma unroll 1
-        for (int a = 0; a < Q3; ++a) {
-            const R adv = advect_pop<R, true>(A.HG, a, i, j, k, c, nb, A);
-            const R gc = A.GC[a * N + c];
-            const R es = gc - A.dt * adv;
-            A.GC[a * N + c] = gc - A.hf * adv;
-            A.HGS[a * N + c] = es;
-            td += es;
-        }
+        jx += R(c3x(a)) * fs;
+        jy += R(c3y(a)) * fs;
+        jz += R(c3z(a)) * fs;
+        if constexpr (TH) td += A.HGS[a * NP + cp];
     }
     Cell3<R, TH> m;
     m.from_sums(r, jx, jy, jz, td, A);
-#pragma unroll 1
+#pragma unroll
     for (int a = 0; a < Q3; ++a) {
         R feqd, F, geqd;
         m.eq(a, A, feqd, F, geqd);
-        const R fs = A.HS[a * N + c];
-        A.HS[a * N + c] = fs + A.omh * (feqd - fs) + A.hf * F;
+        const R fs = A.HS[a * NP + cp];
+        A.HS[a * NP + cp] = fs + A.omh * (feqd - fs) + A.hf * F;
         if constexpr (TH) {
-            const R es = A.HGS[a * N + c];
-            A.HGS[a * N + c] = es + A.omgh * (geqd - es);
+            const R es = A.HGS[a * NP + cp];
+            A.HGS[a * NP + cp] = es + A.omgh * (geqd - es);
         }
-    }
-}
-
-// ---- FV pass 3: corrector, Eq. (semi-heun) ----
-template <typename R, typename S, bool TH>
-__global__ void __launch_bounds__(256) k3_post(const Args3<R> A) {
-    int i, j, k;
-    if (!cell_index(A.n, i, j, k)) return;
-    const long long c = cell3(A.n, i, j, k), N = A.N;
-    const Nbr3 nb = neighbours3(A.n, A.bc, i, j, k);
-    S* out = static_cast<S*>(A.fout);
-#pragma unroll 1
-    for (int a = 0; a < Q3; ++a)
-        Store<S>::st(out + a * N + c, A.FC[a * N + c] - A.hf * advect_pop<R, false>(A.HS, a, i, j, k, c, nb, A));
-    if constexpr (TH) {
-        S* gout = static_cast<S*>(A.gout);
-#pragma unroll 1
-        for (int a = 0; a < Q3; ++a)
-            Store<S>::st(gout + a * N + c,
-                         A.GC[a * N + c] - A.hf * advect_pop<R, true>(A.HGS, a, i, j, k, c, nb, A));
     }
 }
 
@@ -518,15 +492,23 @@ __global__ void __launch_bounds__(256) k3_plane_sums(const double* F, const doub
 
 dim3 grid3(const int* n) { return dim3((n[0] + 31) / 32, (n[1] + 7) / 8, n[2]); }
 
+// z planes per CTA of the flux passes
+constexpr int kZChunk = 16;
+
 template <typename R, typename S, bool TH>
 cudaError_t run_fv3(const Args3<R>& A, cudaStream_t s) {
     const dim3 b(32, 8), g = grid3(A.n);
+    const int np = TH ? 2 * Q3 : Q3;
+    const int chunks = (A.n[2] + kZChunk - 1) / kZChunk;
+    const dim3 gx((A.n[0] + 31) / 32, (A.n[1] + 7) / 8, 1);
+    const dim3 ga(gx.x, gx.y, chunks * np), gz(gx.x, gx.y, 4 * np);
     k3_pre<R, S, TH><<<g, b, 0, s>>>(A);
-    count_launch();
-    k3_mid<R, TH><<<g, b, 0, s>>>(A);
-    count_launch();
-    k3_post<R, S, TH><<<g, b, 0, s>>>(A);
-    count_launch();
+    k3_ghostz<R><<<gz, b, 0, s>>>(A, 0, np);
+    k3_adv<R, S, false><<<ga, b, 0, s>>>(A, np, kZChunk);
+    k3_star<R, TH><<<g, b, 0, s>>>(A);
+    k3_ghostz<R><<<gz, b, 0, s>>>(A, 1, np);
+    k3_adv<R, S, true><<<ga, b, 0, s>>>(A, np, kZChunk);
+    for (int q = 0; q < 6; ++q) count_launch();
     return cudaGetLastError();
 }
 

@@ -56,15 +56,16 @@ struct Args3 {
     void* fout;
     const void* gin;
     void* gout;
-    R* H;    // [19][N] advected field h' (time n), then reused
+    R* H;    // [19][nz + 4][ny][nx] advected field h' (time n), two ghost planes each side in z
     R* FC;   // [19][N] f' + Coll, then f' + Coll - dt/2 A[h^n]
-    R* HS;   // [19][N] h*'
+    R* HS;   // [19][nz + 4][ny][nx] f~*' (parked), then h*'
     R* HG;   // thermal counterparts
     R* GC;
     R* HGS;
     int n[3];           // nx, ny, nz
     int bc[3];          // LB_BC_PERIODIC / LB_BC_WALLS per axis
     long long N;        // nx ny nz
+    long long NP;       // nx ny (nz + 4): population stride of the padded fields
     AxisMetric<R> m[3]; // QUICK weights and 1/width per axis
     const R* ft[3];     // the same, face-major (kFaceRow values per face)
     R dt, om, omh, cf, hf, omg, omgh;

@@ -95,6 +95,7 @@ Args3<R> args3(const lb3_grid* G, bool st) {
         A.ft[a] = static_cast<const R*>(G->faces[a]);
     }
     A.N = G->N;
+    A.NP = (long long)G->n[0] * G->n[1] * (G->n[2] + 4);
     const lb3_params& p = G->p;
     const double dt = st ? 1.0 : p.dt;
     const double taut = p.tau + 0.5 * dt, taugt = p.tau_g + 0.5 * dt;  // tau~ = tau + dt/2
@@ -194,7 +195,9 @@ lb_status lb3_create_grid(const lb3_grid_desc* d, lb3_grid** out) {
         e = cudaMalloc(&G->f[b], pop);
         if (e == cudaSuccess && d->thermal) e = cudaMalloc(&G->g[b], pop);
     }
-    for (int w = 0; w < 3 * sets && e == cudaSuccess; ++w) e = cudaMalloc(&G->work[w], pop);
+    // h, h* (and hg, hg*) carry two ghost planes on each side in z; f + Coll does not
+    const size_t padded = (size_t)Q3 * n[0] * n[1] * (n[2] + 4) * rsize(G->prec);
+    for (int w = 0; w < 3 * sets && e == cudaSuccess; ++w) e = cudaMalloc(&G->work[w], w % 3 == 1 ? pop : padded);
     for (int a = 0; a < 3 && e == cudaSuccess; ++a) {
         const std::vector<double> m = G->ax[a].metric();
         const int n1 = n[a] + 1;
