@@ -129,7 +129,7 @@ def make_grid(lb, w, stream, tune=True):
 
 def schedule_name(lb, g, scheme):
     if isinstance(g, lb.Grid3):
-        return "3-D fv three passes (collision; predictor; corrector)" if scheme == "fv" else "3-D st push"
+        return "3-D fv four passes (collision; predictor; star; corrector)" if scheme == "fv" else "3-D st push"
     if scheme != "fv":
         if g.store == lb.LB_STORE_F64:
             return "st push, one thread per cell"
@@ -262,7 +262,7 @@ def serving_measure(lb, torch, count=120, rate=25.0):
              for r in reqs if srv["results"][r.rid]["status"] == 0 and seq["results"][r.rid]["status"] == 0]
     keep = ("requests", "ok", "unstable", "cell_updates", "wall_s", "mlups", "tts_p50_s", "tts_p99_s")
     return {"workload": "RB FV requests, N in {64..1024}^2 tanh plates, Ra log-uniform 1e4-1e8, Pr=1, "
-                        "steps uniform 50-1000 (config 5 steps / 20), FP16 deviation storage, "
+                        "steps uniform 50-1000 (the 1000-20000 of the full stream divided by 20), FP16 deviation storage, "
                         "Poisson arrivals %.0f/s, %d requests" % (rate, count),
             "server": {k: srv[k] for k in keep}, "server_equal_share": {k: share[k] for k in keep},
             "sequential": {k: seq[k] for k in keep},
