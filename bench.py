@@ -115,7 +115,9 @@ def make_grid(lb, w, stream, tune=True):
     g = lb.Grid(store=store, stream=stream, **grid)
     g.init(**w.params, **w.init)
     if w.scheme == "fv":
-        if FV_SCHEDULE.startswith("ptile"):
+        if FV_SCHEDULE.startswith("split"):
+            g.set_fv_schedule(lb.LB_FV_SPLIT, int(FV_SCHEDULE.split(":")[1]) if ":" in FV_SCHEDULE else 0)
+        elif FV_SCHEDULE.startswith("ptile"):
             g.set_fv_schedule(lb.LB_FV_PTILE, int(FV_SCHEDULE.split(":")[1]) if ":" in FV_SCHEDULE else 0)
         elif FV_SCHEDULE.startswith("tile"):
             g.set_fv_schedule(lb.LB_FV_TILE, int(FV_SCHEDULE.split(":")[1]) if ":" in FV_SCHEDULE else 0)
@@ -137,6 +139,8 @@ def schedule_name(lb, g, scheme):
     k, c = g.fv_schedule()
     if k == lb.LB_FV_TILE:
         return "fv tile %s (halo 4)" % {0: "32x16", 16: "16x16", 8: "16x8"}[c]
+    if k == lb.LB_FV_SPLIT:
+        return "fv split (f32x2) %s: collision+predictor, corrector" % {0: "32x16", 16: "16x16"}[c]
     if k == lb.LB_FV_PTILE:
         return "fv pair-tile (f32x2) %s (halo 4)" % {0: "32x16", 16: "16x16", 512: "32x16, 512 threads"}[c]
     return ("fv pair-march (f32x2)" if k == lb.LB_FV_PAIR else "fv march") + ", %d rows per CTA" % c

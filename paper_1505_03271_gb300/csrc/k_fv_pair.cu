@@ -562,6 +562,201 @@ __global__ void __launch_bounds__(NTH, MINB) k_fv_ptile(const StepArgs<float> A)
     ptile_body<S, TH, TX, TY, NTH>(A, blockIdx.x * TX, blockIdx.y * TY);
 }
 
+// ---- split schedule: two kernels per step ----
+// The fused tile recomputes the collision on tile + 4 and the predictor on
+// tile + 2.  Here the first kernel computes the collision on tile + 2 and the
+// predictor on the tile only, and hands h* and f~ + Coll - dt/2 A[h^n] to
+// the second kernel through global memory (L2 on small grids); the second
+// reads h* on tile + 2 and applies the corrector.  Halo work drops from
+// 1.875x and 1.41x to 1.41x and 1x, and shared memory from three regions
+// to one per kernel, at the price of a second launch and 72 B (144 B with
+// g) per cell through L2.
+template <typename S, bool TH, int TX, int TY, int NTH>
+__global__ void __launch_bounds__(NTH) k_fv_split_a(const StepArgs<float> A) {
+    constexpr int NQ = TH ? 2 * Q : Q;
+    constexpr int BW = (TX + 4) / 2, BH = TY + 4, NB = BW * BH;
+    constexpr int TW = TX / 2, NT = TW * TY;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V2* sH = reinterpret_cast<V2*>(smem_raw);  // [NQ][BH][BW] h^n on tile + 2
+    V2* sFC = sH + NQ * NB;                    // [NQ][TY][TW] f~ + Coll on the tile
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, nx = A.nx;
+    const S* fin = static_cast<const S*>(A.fin);
+    const S* gin = static_cast<const S*>(A.gin);
+    for (int k = threadIdx.x; k < NB; k += NTH) {
+        const int px = k % BW, ey = k / BW;
+        int gy;
+        if (!map_axis(y0 - 2 + ey, A.ny, A.bcy, gy)) continue;
+        const int xu = x0 - 2 + 2 * px;
+        const int gxl = ((xu % nx) + nx) % nx, gxr = ((xu + 1) % nx + nx) % nx;
+        const bool contiguous = xu >= 0 && xu + 1 < nx;
+        const long long row = (long long)gy * A.pitch;
+        V2 d[Q], e[Q];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const S* b = fin + a * A.plane + row;
+            d[a] = contiguous ? PairIO<S>::ld(b + xu) : mk(Store<S>::ld(b + gxl), Store<S>::ld(b + gxr));
+            if constexpr (TH) {
+                const S* bg = gin + a * A.plane + row;
+                e[a] = contiguous ? PairIO<S>::ld(bg + xu) : mk(Store<S>::ld(bg + gxl), Store<S>::ld(bg + gxr));
+            }
+        }
+        const float4 o = __ldg(reinterpret_cast<const float4*>(A.rowtab + 20 * gy) + 3);
+        PairCell<TH> c;
+        c.build(d, e, A, o.y, TH ? o.z : 0.0f);
+        const bool inT = px >= 1 && px < BW - 1 && ey >= 2 && ey < BH - 2;
+        const int kt = (ey - 2) * TW + (px - 1);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const V2 neq = c.feqd[a] - d[a];
+            sH[a * NB + k] = fma2(bc(A.omh), neq, fma2(bc(A.hf), c.F[a], d[a]));
+            if (inT) sFC[a * NT + kt] = fma2(bc(A.om), neq, fma2(bc(A.cf), c.F[a], d[a]));
+            if constexpr (TH) {
+                const V2 neqg = c.geqd[a] - e[a];
+                sH[(Q + a) * NB + k] = fma2(bc(A.omgh), neqg, e[a]);
+                if (inT) sFC[(Q + a) * NT + kt] = fma2(bc(A.omg), neqg, e[a]);
+            }
+        }
+    }
+    __syncthreads();
+    ghost_rows_region<TH, NQ, BH, BW>(sH, y0 - 2, A);
+    __syncthreads();
+    for (int k = threadIdx.x; k < NT; k += NTH) {
+        const int tx = k % TW, ty = k / TW;
+        const int gx = x0 + 2 * tx, gy = y0 + ty;
+        if (gx >= nx || gy >= A.ny) continue;
+        XPair X;
+        load_col(A.coltab, gx, X);
+        YPair Y;
+        load_row(A.rowtab, gy, Y);
+        V2 adv[NQ];
+        advect_region_all<TH, NQ, BH, BW, 0>(sH, tx + 1, ty + 2, X, Y, adv);
+        const long long at = (long long)gy * A.pitch + gx;
+        const bool both = gx + 1 < nx;
+        V2 fs[Q], es[Q];
+#pragma unroll
+        for (int a = 0; a < NQ; ++a) {
+            const V2 fc = sFC[a * NT + k];
+            const V2 fcb = fma2(bc(-A.hf), adv[a], fc);
+            float* p = A.xfc + a * A.plane + at;
+            if (both) PairIO<float>::st(p, fcb);
+            else *p = fcb.v.x;
+            const V2 st = fma2(bc(-A.dt), adv[a], fc);
+            if (a < Q) fs[a] = st;
+            else if constexpr (TH) es[a - Q] = st;
+        }
+        PairCell<TH> c;
+        c.build(fs, es, A, Y.ro, TH ? Y.to : 0.0f);
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const V2 hs = fma2(bc(A.omh), c.feqd[a] - fs[a], fma2(bc(A.hf), c.F[a], fs[a]));
+            float* p = A.xh + a * A.plane + at;
+            if (both) PairIO<float>::st(p, hs);
+            else *p = hs.v.x;
+            if constexpr (TH) {
+                const V2 hg = fma2(bc(A.omgh), c.geqd[a] - es[a], es[a]);
+                float* q = A.xh + (Q + a) * A.plane + at;
+                if (both) PairIO<float>::st(q, hg);
+                else *q = hg.v.x;
+            }
+        }
+    }
+}
+
+template <typename S, bool TH, int TX, int TY, int NTH>
+__global__ void __launch_bounds__(NTH) k_fv_split_c(const StepArgs<float> A) {
+    constexpr int NQ = TH ? 2 * Q : Q;
+    constexpr int BW = (TX + 4) / 2, BH = TY + 4, NB = BW * BH;
+    constexpr int TW = TX / 2, NT = TW * TY;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    V2* sHs = reinterpret_cast<V2*>(smem_raw);  // [NQ][BH][BW] h* on tile + 2
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, nx = A.nx;
+    for (int k = threadIdx.x; k < NB; k += NTH) {
+        const int px = k % BW, ey = k / BW;
+        int gy;
+        if (!map_axis(y0 - 2 + ey, A.ny, A.bcy, gy)) continue;
+        const int xu = x0 - 2 + 2 * px;
+        const int gxl = ((xu % nx) + nx) % nx, gxr = ((xu + 1) % nx + nx) % nx;
+        const bool contiguous = xu >= 0 && xu + 1 < nx;
+        const long long row = (long long)gy * A.pitch;
+#pragma unroll
+        for (int a = 0; a < NQ; ++a) {
+            const float* b = A.xh + a * A.plane + row;
+            sHs[a * NB + k] = contiguous ? PairIO<float>::ld(b + xu) : mk(__ldg(b + gxl), __ldg(b + gxr));
+        }
+    }
+    __syncthreads();
+    ghost_rows_region<TH, NQ, BH, BW>(sHs, y0 - 2, A);
+    __syncthreads();
+    S* fout = static_cast<S*>(A.fout);
+    S* gout = static_cast<S*>(A.gout);
+    for (int k = threadIdx.x; k < NT; k += NTH) {
+        const int tx = k % TW, ty = k / TW;
+        const int gx = x0 + 2 * tx, gy = y0 + ty;
+        if (gx >= nx || gy >= A.ny) continue;
+        XPair X;
+        load_col(A.coltab, gx, X);
+        YPair Y;
+        load_row(A.rowtab, gy, Y);
+        V2 adv[NQ];
+        advect_region_all<TH, NQ, BH, BW, 0>(sHs, tx + 1, ty + 2, X, Y, adv);
+        const long long at = (long long)gy * A.pitch + gx;
+        const bool both = gx + 1 < nx;
+#pragma unroll
+        for (int a = 0; a < NQ; ++a) {
+            const float* p = A.xfc + a * A.plane + at;
+            const V2 fcb = both ? PairIO<float>::ld(p) : mk(__ldg(p), 0.0f);
+            const V2 o = fma2(bc(-A.hf), adv[a], fcb);
+            S* base = (a < Q ? fout + a * A.plane : gout + (a - Q) * A.plane) + at;
+            if (both) PairIO<S>::st(base, o);
+            else Store<S>::st(base, o.v.x);
+        }
+    }
+}
+
+template <typename S, bool TH, int TX, int TY, int NTH>
+static cudaError_t run_split(const void* vargs, cudaStream_t s) {
+    const StepArgs<float>& A = *static_cast<const StepArgs<float>*>(vargs);
+    constexpr int NQ = TH ? 2 * Q : Q;
+    constexpr size_t smem_a = sizeof(V2) * NQ * (((TX + 4) / 2) * (TY + 4) + (TX / 2) * TY);
+    constexpr size_t smem_c = sizeof(V2) * NQ * ((TX + 4) / 2) * (TY + 4);
+    static_assert(smem_a <= 232448, "shared memory per CTA");
+    static bool configured = false;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_fv_split_a<S, TH, TX, TY, NTH>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_fv_split_c<S, TH, TX, TY, NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem_c);
+        if (e != cudaSuccess) return e;
+        configured = true;
+    }
+    dim3 grid((A.nx + TX - 1) / TX, (A.ny + TY - 1) / TY);
+    k_fv_split_a<S, TH, TX, TY, NTH><<<grid, NTH, smem_a, s>>>(A);
+    count_launch();
+    k_fv_split_c<S, TH, TX, TY, NTH><<<grid, NTH, smem_c, s>>>(A);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <typename S, bool TH>
+static cudaError_t run_split_shape(const void* args, int shape, cudaStream_t s) {
+    if (shape == 16) return run_split<S, TH, 16, 16, 128>(args, s);
+    return run_split<S, TH, 32, 16, 256>(args, s);
+}
+
+cudaError_t launch_fv_split(Prec p, bool th, const void* args, int shape, cudaStream_t s) {
+    switch (p) {
+        case Prec::F32:
+            return th ? run_split_shape<float, true>(args, shape, s) : run_split_shape<float, false>(args, shape, s);
+        case Prec::F16:
+            return th ? run_split_shape<__half, true>(args, shape, s) : run_split_shape<__half, false>(args, shape, s);
+        case Prec::BF16:
+            return th ? run_split_shape<__nv_bfloat16, true>(args, shape, s)
+                      : run_split_shape<__nv_bfloat16, false>(args, shape, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
 // Many grids in one launch (the serving path): CTA b steps tile tiles[b] =
 // (request, tile x, tile y) with that request's parameters, picking its
 // input buffer from step k of the launch sequence; requests with fewer than
@@ -582,19 +777,22 @@ k_fv_ptile_batched(const BatchReq<float>* reqs, const int4* tiles, const int* nt
     ptile_body<S, TH, TX, TY, NTH>(A, t.y * TX, t.z * TY);
 }
 
+// Thermal tiles use 512 threads (one CTA per SM by shared memory; the
+// corrector splits f and g over two threads per pair-cell), flow tiles 256.
 template <typename S, bool TH>
 static cudaError_t run_ptile_batched(const void* reqs, const int4* tiles, const int* ntiles, int capacity, int k,
                                      cudaStream_t s) {
     constexpr int NQ = TH ? 2 * Q : Q;
+    constexpr int NTH = TH ? 512 : 256;
     constexpr size_t smem = sizeof(V2) * NQ * (((32 + 8) / 2) * (16 + 8) + 2 * ((32 + 4) / 2) * (16 + 4));
     static bool configured = false;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_fv_ptile_batched<S, TH, 32, 16, 256>,
+        cudaError_t e = cudaFuncSetAttribute(k_fv_ptile_batched<S, TH, 32, 16, NTH>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    k_fv_ptile_batched<S, TH, 32, 16, 256><<<capacity, 256, smem, s>>>(static_cast<const BatchReq<float>*>(reqs),
+    k_fv_ptile_batched<S, TH, 32, 16, NTH><<<capacity, NTH, smem, s>>>(static_cast<const BatchReq<float>*>(reqs),
                                                                       tiles, ntiles, k);
     count_launch();
     return cudaGetLastError();

@@ -49,7 +49,7 @@ namespace {
 void release(lb_grid* G) {
     void* ptrs[] = {G->f[0], G->f[1], G->g[0], G->g[1], G->mx, G->my, G->dxv, G->dyv, G->xc,
                     G->yc, G->toff, G->toff_r, G->roff, G->roff_r, G->dref_r, G->rowtab, G->coltab, G->fields,
-                    G->partial, G->red};
+                    G->partial, G->red, G->xh, G->xfc};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -129,6 +129,20 @@ int resolved_chunk(const lb_grid* G) {
     return ch < 32 ? 32 : ch;
 }
 
+// The split schedule's two FP32 buffers (NQ planes each), allocated on
+// first use.
+cudaError_t ensure_split_buffers(lb_grid* G) {
+    if (G->xh) return cudaSuccess;
+    const size_t bytes = sizeof(float) * (G->d.thermal ? 18 : 9) * (size_t)G->plane;
+    cudaError_t e = cudaMalloc(&G->xh, bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&G->xfc, bytes);
+    if (e != cudaSuccess) {
+        if (G->xh) cudaFree(G->xh);
+        G->xh = G->xfc = nullptr;
+    }
+    return e;
+}
+
 template <typename R>
 cudaError_t launch_fv_step(lb_grid* G) {
     StepArgs<R> A = step_args<R>(G, G->p.dt);
@@ -136,6 +150,13 @@ cudaError_t launch_fv_step(lb_grid* G) {
     if (A.stages == 1 || has_density_axis(G))  // single-stage schemes, density boundaries: scalar tile kernel
         return launch_fv(G->prec, th, &A, G->fv_kernel == LB_FV_TILE ? G->fv_chunk : 0, G->stream);
     const int k = resolved_kernel(G);
+    if (k == LB_FV_SPLIT) {
+        cudaError_t e = ensure_split_buffers(G);
+        if (e != cudaSuccess) return e;
+        A.xh = G->xh;
+        A.xfc = G->xfc;
+        return launch_fv_split(G->prec, th, &A, G->fv_chunk, G->stream);
+    }
     if (k == LB_FV_PAIR) return launch_fv_pair(G->prec, th, &A, resolved_chunk(G), G->stream);
     if (k == LB_FV_PTILE) return launch_fv_ptile(G->prec, th, &A, G->fv_kernel == LB_FV_PTILE ? G->fv_chunk : 0,
                                                  G->stream);
@@ -447,13 +468,15 @@ lb_status lb_step_fv(lb_grid* G, int nsteps) {
 
 lb_status lb_set_fv_schedule(lb_grid* G, int kernel, int chunk) {
     if (!G) return fail(LB_ERR_ARG, "grid is NULL");
-    if (kernel < LB_FV_AUTO || kernel > LB_FV_PTILE) return fail(LB_ERR_ARG, "unknown FV kernel %d", kernel);
+    if (kernel < LB_FV_AUTO || kernel > LB_FV_SPLIT) return fail(LB_ERR_ARG, "unknown FV kernel %d", kernel);
     if (chunk < 0) return fail(LB_ERR_ARG, "chunk must be >= 0");
     if (kernel == LB_FV_TILE && chunk != 0 && chunk != 8 && chunk != 16)
         return fail(LB_ERR_ARG, "tile shape must be 0 (32 x 16), 16 (16 x 16) or 8 (16 x 8)");
     if (kernel == LB_FV_PTILE && chunk != 0 && chunk != 16 && chunk != 512)
         return fail(LB_ERR_ARG, "paired tile shape must be 0 (32 x 16), 16 (16 x 16) or 512 (32 x 16, 512 threads)");
-    if ((kernel == LB_FV_PAIR || kernel == LB_FV_PTILE) && !pair_ok(G))
+    if (kernel == LB_FV_SPLIT && chunk != 0 && chunk != 16)
+        return fail(LB_ERR_ARG, "split tile shape must be 0 (32 x 16) or 16 (16 x 16)");
+    if ((kernel == LB_FV_PAIR || kernel == LB_FV_PTILE || kernel == LB_FV_SPLIT) && !pair_ok(G))
         return fail(LB_ERR_ARG, "the paired FV kernel needs FP32/FP16/BF16 storage and a periodic x axis");
     G->fv_kernel = kernel;
     G->fv_chunk = chunk;
@@ -492,7 +515,8 @@ lb_status lb_get_fv_schedule(lb_grid* G, int* kernel, int* chunk) {
     if (kernel) *kernel = resolved_kernel(G);
     if (chunk) {
         const int k = resolved_kernel(G);
-        *chunk = (k == LB_FV_TILE || k == LB_FV_PTILE) ? (G->fv_kernel == k ? G->fv_chunk : 0) : resolved_chunk(G);
+        *chunk = (k == LB_FV_TILE || k == LB_FV_PTILE || k == LB_FV_SPLIT) ? (G->fv_kernel == k ? G->fv_chunk : 0)
+                                                                            : resolved_chunk(G);
     }
     return LB_OK;
 }
@@ -518,6 +542,10 @@ lb_status lb_autotune_fv(lb_grid* G, int steps) {
         cands.push_back({LB_FV_PTILE, 0});
         cands.push_back({LB_FV_PTILE, 16});
         cands.push_back({LB_FV_PTILE, 512});
+        if (ensure_split_buffers(G) == cudaSuccess) {
+            cands.push_back({LB_FV_SPLIT, 0});
+            cands.push_back({LB_FV_SPLIT, 16});
+        }
     }
     for (int kern : {(int)LB_FV_MARCH, (int)LB_FV_PAIR}) {
         if (kern == LB_FV_PAIR && !pair_ok(G)) continue;

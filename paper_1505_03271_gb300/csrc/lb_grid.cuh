@@ -125,6 +125,8 @@ struct lb_grid {
     void* dref_r = nullptr;     // [4][ny] y flux divergence of the base state, compute precision
     float* rowtab = nullptr;    // [ny][20] y weights, 1/dy, offsets, base-state fluxes (paired kernels)
     float* coltab = nullptr;    // [nx][20] x weights of a column pair and its 1/dx (paired tile kernel)
+    float* xh = nullptr;        // split schedule: h*, [NQ][ny][pitch] FP32 (allocated on first use)
+    float* xfc = nullptr;       // split schedule: f~ + Coll - dt/2 A[h^n]
     double* fields = nullptr;   // [4][ny][nx] staging for init/moments
     double* partial = nullptr;  // reduction partials
     double* red = nullptr;      // reduction totals
@@ -185,6 +187,8 @@ inline StepArgs<R> step_args(const lb_grid* G, double dt) {
     A.dref = static_cast<const R*>(G->dref_r);
     A.rowtab = G->rowtab;
     A.coltab = G->coltab;
+    A.xh = G->xh;
+    A.xfc = G->xfc;
     return A;
 }
 

@@ -104,6 +104,8 @@ struct StepArgs {
     const R* dref;          // [4][ny]: y flux divergence of rho_r (c_y > 0, < 0), of T_r (> 0, < 0)
     const float* rowtab;    // [ny][20] per-row y data of the paired kernels (FP32 grids)
     const float* coltab;    // [nx][20] per-column-pair x data of the paired tile kernel
+    float* xh;              // split schedule: h* of the step, [NQ][ny][pitch] (FP32)
+    float* xfc;             // split schedule: f~ + Coll - dt/2 A[h^n], same layout
 };
 
 // Wrap or reject a global index on one axis: periodic axes wrap, wall axes
@@ -209,6 +211,9 @@ int pair_width();
 size_t pair_smem(bool thermal);
 // paired tile kernel: shape 0 = 32 x 16, 16 = 16 x 16 (x-periodic, FP32 arithmetic)
 cudaError_t launch_fv_ptile(Prec p, bool thermal, const void* args, int shape, cudaStream_t s);
+// split paired schedule: two launches per step (collision + predictor, corrector),
+// h* and f~ + Coll - dt/2 A[h^n] through the xh / xfc buffers
+cudaError_t launch_fv_split(Prec p, bool thermal, const void* args, int shape, cudaStream_t s);
 // batched paired tile (32 x 16) over a request table, as launch_fv_batched
 cudaError_t launch_fv_ptile_batched(Prec p, bool thermal, const void* reqs, const int4* tiles, const int* ntiles,
                                     int capacity, int k, cudaStream_t s);

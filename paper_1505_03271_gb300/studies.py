@@ -9,6 +9,10 @@
   * ``dt_max``: the largest stable FV time step as a function of tau for the
     Euler, semi-implicit and Heun schemes on the decaying [1, 64] shear wave
     (Fig. KOL3).
+  * ``rb3d_stats``: the 3-D Rayleigh-Benard runs of Table rb with FV (sinh z
+    grid) and ST (uniform), time- and plane-averaged profiles T_m(z),
+    T_rms(z), k_m(z) and Nu(z), and the cells inside the thermal boundary
+    layer (Sec. IV, Figs. cfrT, cfrT2, cfrE, cfrLB).
 
 Conventions (readings of the paper):
   * tau = 0.5 (physical) for the Poiseuille studies: the paper puts the best
@@ -232,6 +236,78 @@ def dt_max(lb, torch, taus=(0.03, 0.05, 0.08, 0.125, 0.2, 0.3, 0.5, 0.7, 1.0, 1.
     return [{"scheme": s, "tau": t, "dt_max": round(bounds[(s, t)][0], 4)} for s, t in keys]
 
 
+def _ddz(z, f):
+    """Second-order derivative at the nodes of a stretched grid: the
+    3-point Lagrange derivative, central in the bulk, forward/backward at
+    the first and last node (the post-processing of Sec. IV)."""
+    n = len(z)
+    d = np.zeros(n)
+    for k in range(n):
+        m = min(max(k, 1), n - 2)
+        z0, z1, z2 = z[m - 1], z[m], z[m + 1]
+        x = z[k]
+        d[k] = (f[m - 1] * (2 * x - z1 - z2) / ((z0 - z1) * (z0 - z2)) +
+                f[m] * (2 * x - z0 - z2) / ((z1 - z0) * (z1 - z2)) +
+                f[m + 1] * (2 * x - z0 - z1) / ((z2 - z0) * (z2 - z1)))
+    return d
+
+
+def rb3d_stats(lb, torch, scheme, tff_total=300.0, tff_avg=200.0, samples=100, store=None):
+    """Table rb run with `scheme` ("fv" or "st"): tff_total free-fall times
+    H / sqrt(beta g dT H), statistics over the last tff_avg of them from
+    `samples` equally spaced snapshots.  Nu(z) = (<u_z (T - T0)> - kappa
+    d<T>/dz) / (kappa dT / H); lambda_T = dT / (2 dT_m/dz at the plate)."""
+    w = cfg.rb3d_table(scheme) if store is None else cfg.rb3d_table(scheme, store=store)
+    gk = dict(w.grid)
+    st = gk.pop("store")
+    p = w.params
+    H, dT = gk["lz"], p["T_bot"] - p["T_top"]
+    tff = H / math.sqrt(p["beta"] * p["grav"] * dT * H)
+    dt = p["dt"]
+    steps_total = int(round(tff_total * tff / dt))
+    steps_avg = int(round(tff_avg * tff / dt))
+    every = max(1, steps_avg // samples)
+    g = lb.Grid3(store=st, **gk).init(**p, **w.init)
+    step = g.step_fv if scheme == "fv" else g.step_st
+    xi = cfg.faces(gk["nz"], H, gk.get("sz", 0), gk.get("stretch_z", 0.0))
+    zc = 0.5 * (xi[1:] + xi[:-1])
+    kappa = p["tau_g"] * cfg.CS2
+    acc = {k: np.zeros(gk["nz"]) for k in ("T", "T2", "k", "uzT")}
+    nus = []
+    step(steps_total - steps_avg)
+    n = 0
+    for _ in range(steps_avg // every):
+        step(every)
+        rho, ux, uy, uz, T = g.moments()
+        acc["T"] += T.mean(axis=(1, 2))
+        acc["T2"] += (T * T).mean(axis=(1, 2))
+        acc["k"] += 0.5 * (ux * ux + uy * uy + uz * uz).mean(axis=(1, 2))
+        acc["uzT"] += (uz * (T - p["T0"])).mean(axis=(1, 2))
+        nus.append(g.nusselt())
+        n += 1
+    g.close()
+    Tm = acc["T"] / n
+    Trms = np.sqrt(np.maximum(acc["T2"] / n - Tm * Tm, 0.0))
+    km = acc["k"] / n
+    nu_z = (acc["uzT"] / n - kappa * _ddz(zc, Tm)) / (kappa * dT / H)
+    nus = np.array(nus)
+    nu_bot = float(nus[:, 1].mean())
+    lam = H / (2.0 * nu_bot)
+    lower = zc < 0.1 * H
+    return {"scheme": scheme, "cells": w.cells, "nz": gk["nz"], "H": H, "dt": dt, "tff": tff,
+            "steps": steps_total, "samples": n, "nu_vol": float(nus[:, 0].mean()), "nu_bot": nu_bot,
+            "nu_top": float(nus[:, 2].mean()), "nu_vol_std": float(nus[:, 0].std()),
+            "lambda_T": lam, "cells_in_bl": int((zc < lam).sum()), "z1": float(zc[0]),
+            "nu_z_mean": float(nu_z.mean()), "nu_z_wall_dev": float(np.abs(nu_z[lower] - nu_z.mean()).max()),
+            "zc_over_H": [round(float(v), 5) for v in zc / H], "T_m": [round(float(v), 6) for v in Tm],
+            "T_rms": [round(float(v), 6) for v in Trms], "k_m": [float(f"{v:.4e}") for v in km],
+            "nu_z": [round(float(v), 4) for v in nu_z]}
+
+
+def rb3d(lb, torch, tff_total=300.0, tff_avg=200.0):
+    return [rb3d_stats(lb, torch, s, tff_total, tff_avg) for s in ("fv", "st")]
+
+
 def main(argv=None):
     import time
 
@@ -242,7 +318,8 @@ def main(argv=None):
     argv = sys.argv[1:] if argv is None else argv
     which = set(argv) or {"kol3", "poi2", "poi3"}
     load()
-    for name, fn in (("kol3", dt_max), ("poi2", poiseuille_vs_n), ("poi3", poiseuille_vs_spacing)):
+    for name, fn in (("kol3", dt_max), ("poi2", poiseuille_vs_n), ("poi3", poiseuille_vs_spacing),
+                     ("rb3d", rb3d)):
         if name in which:
             t0 = time.perf_counter()
             rows = fn(lb, torch)
