@@ -195,10 +195,12 @@ lb_status lb_set_boundary_density(lb_grid* grid, double rho_x0, double rho_x1, d
 lb_status lb_set_fv_scheme(lb_grid* grid, int scheme);
 lb_status lb_get_fv_scheme(lb_grid* grid, int* scheme);
 
-/* Autotuner: times `steps` FV steps for each candidate schedule (tile; march
- * and pair with several chunk lengths) on the grid's current state, restores the
- * state after each candidate, and keeps the fastest.  Synchronous; uses a
- * temporary copy of the populations.  LB_ERR_STATE before lb_init. */
+/* Autotuner: times `steps` FV steps for each candidate schedule (the three
+ * tile shapes; march and pair with several chunk lengths; the paired tiles
+ * and the split schedule where they apply) on the grid's current state,
+ * restores the state after each candidate, and keeps the fastest.
+ * Synchronous; uses a temporary copy of the populations (and allocates the
+ * split schedule's buffers).  LB_ERR_STATE before lb_init. */
 lb_status lb_autotune_fv(lb_grid* grid, int steps);
 
 /* Macroscopic fields: rho = sum f~, u = sum c f~ / rho + dt/2 a (Sec. II B 4),

@@ -1,8 +1,12 @@
 // k_fv_pair.cu -- the FV time step (Sec. II B: Eqs. (semi), (semi-heun),
-// QUICK faces of Sec. II B 3, double-reflection walls of Sec. II B 5) as a
-// y-marching strip kernel in which every thread owns two adjacent columns
-// and all arithmetic runs on packed FP32 pairs (Blackwell's f32x2 FMA, ADD
-// and MUL: one instruction for both columns).
+// QUICK faces of Sec. II B 3, double-reflection walls of Sec. II B 5) in
+// kernels where every thread owns two adjacent columns and all arithmetic
+// runs on packed FP32 pairs (Blackwell's f32x2 FMA, ADD and MUL: one
+// instruction for both columns):
+//   k_fv_pair             y-marching strips (below);
+//   k_fv_ptile            the tile step of k_fv.cu on column pairs;
+//   k_fv_split_a / _c     the tile step in two launches;
+//   k_fv_ptile_batched    the paired tile over the server's request table.
 //
 // March structure as in k_fv_march.cu: stage A forms h^n and f~ + Coll^n of
 // row t, stage B forms f~* and h* of row t - 2, stage C writes f~^(n+1) of
