@@ -169,20 +169,30 @@ def time_steps(lb, torch, g, scheme, steps, warmup, flush=None):
     return [a.elapsed_time(b) for a, b in evs], launches
 
 
+def source_hash(files):
+    """Hash of the code of the given csrc files with comments and whitespace
+    removed, so that a comment edit does not count as a kernel change."""
+    import hashlib
+    import re
+    m = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_1505_03271_gb300", "csrc", f)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        m.update(" ".join(text.split()).encode())
+    return m.hexdigest()[:16]
+
+
 def measured_traffic(schedule, case):
     """DRAM bytes per launch from the committed ncu summary of this kernel
-    and workload, or None if there is none or the kernel's sources have
-    changed since it was captured."""
-    import hashlib
+    and workload, or None if there is none or the kernel's code has changed
+    since it was captured."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
             table = json.load(fh)
         e = table["%s|%s" % (schedule, case)]
-        m = hashlib.sha256()
-        for f in e["files"]:
-            with open(os.path.join(ROOT, "paper_1505_03271_gb300", "csrc", f), "rb") as fh:
-                m.update(fh.read())
-        return e["bytes"] if m.hexdigest()[:16] == e["sources"] else None
+        return e["bytes"] if source_hash(e["files"]) == e["sources"] else None
     except (OSError, KeyError, ValueError):
         return None
 

@@ -1,5 +1,11 @@
 """Accuracy and stability studies of Secs. III and V, run through the library.
 
+  * ``viscosity_error``: relative error of the viscosity measured from the
+    decay of the [1, 64] shear wave, nu_num against tau c_s^2, for FV and ST
+    as a function of tau (Fig. KOL; FV with dt = 1 for tau >= 0.13 and 0.1
+    below, ST with dt = 1).
+  * ``poiseuille_unit_dx``: the Re = 10 Poiseuille error at fixed dx = 1
+    (L = N) for FV and ST on uniform grids (Fig. POI).
   * ``poiseuille_vs_n``: relative L2 error of the Re = 10 Poiseuille profile
     against the parabola for a fixed channel width L = 64 and a varying
     number of cells N (Fig. POI2), for FV on uniform, tanh, sinh and
@@ -148,6 +154,47 @@ def run_poiseuille(lb, torch, cases, streams=8):
                 "U": U, "dt": dt, "steps": steps, "err": st.c.error(ux[:, 0], xi, L, U)}
 
     return _run_concurrent(lb, torch, cases, start, advance, finish, streams)
+
+
+def viscosity_error(lb, torch, taus=(0.02, 0.05, 0.08, 0.1, 0.13, 0.2, 0.3, 0.5, 0.7, 1.0, 1.5, 2.0),
+                    n=64, amp=1e-4, periods=0.25):
+    """nu_num from the kinetic energy decay k(t) = k0 exp(-2 nu k^2 t) of the
+    shear wave u_x = A sin(2 pi y / n) (Sec. III A), a least-squares fit of
+    ln k over `periods` energy decay times; error |nu_num / (tau c_s^2) - 1|."""
+    kw2 = (2 * math.pi / n) ** 2
+    rows = []
+    for scheme in ("fv", "st"):
+        for tau in taus:
+            nu = tau * cfg.CS2
+            dt = 1.0 if (scheme == "st" or tau >= 0.13) else 0.1
+            T = periods / (2 * nu * kw2)
+            nsamp = 20
+            steps = max(1, int(round(T / dt / nsamp)))
+            g = lb.Grid(1, n, lx=1.0, ly=float(n), store=LB_STORE_F64)
+            g.init(tau=tau, dt=dt, kind=LB_INIT_SHEAR, amp=amp)
+            ts, ks = [], []
+            for s in range(nsamp + 1):
+                if s:
+                    (g.step_fv if scheme == "fv" else g.step_st)(steps)
+                _, ux, uy, _ = g.moments()
+                ts.append(s * steps * dt)
+                ks.append(0.5 * float((ux * ux + uy * uy).sum()))
+            g.close()
+            slope = np.polyfit(np.array(ts), np.log(np.array(ks)), 1)[0]
+            nu_num = -slope / (2 * kw2)
+            rows.append({"scheme": scheme, "tau": tau, "dt": dt, "nu": nu, "nu_num": nu_num,
+                         "err": abs(nu_num / nu - 1)})
+    return rows
+
+
+def poiseuille_unit_dx(lb, torch, ns=(8, 16, 32, 64, 128, 256)):
+    """Fig. POI: channel width L = N at dx = 1, Re = 10, tau = 0.5."""
+    cases = []
+    for n in ns:
+        cases.append(Poiseuille("st", n, float(n)))
+        cases.append(Poiseuille("fv-uniform", n, float(n)))
+    res = run_poiseuille(lb, torch, cases)
+    return [res[c] for c in cases]
 
 
 def poiseuille_vs_n(lb, torch, ns=(8, 12, 16, 24, 32, 48, 64, 96, 128, 192, 256), cheb_max=128):
@@ -318,8 +365,8 @@ def main(argv=None):
     argv = sys.argv[1:] if argv is None else argv
     which = set(argv) or {"kol3", "poi2", "poi3"}
     load()
-    for name, fn in (("kol3", dt_max), ("poi2", poiseuille_vs_n), ("poi3", poiseuille_vs_spacing),
-                     ("rb3d", rb3d)):
+    for name, fn in (("kol", viscosity_error), ("poi", poiseuille_unit_dx), ("kol3", dt_max),
+                     ("poi2", poiseuille_vs_n), ("poi3", poiseuille_vs_spacing), ("rb3d", rb3d)):
         if name in which:
             t0 = time.perf_counter()
             rows = fn(lb, torch)
