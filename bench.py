@@ -102,6 +102,7 @@ class ClockSampler:
 # --------------------------------------------------------------------- GPU --
 
 FV_SCHEDULE = "tune"
+FV3_SCHEDULE = "auto"
 
 
 def make_grid(lb, w, stream, tune=True):
@@ -110,8 +111,11 @@ def make_grid(lb, w, stream, tune=True):
     unless --fv-schedule fixes one."""
     grid = dict(w.grid)
     store = grid.pop("store")
-    if "nz" in grid:  # D3Q19 grid (include/lb3.h): one schedule
-        return lb.Grid3(store=store, stream=stream, **grid).init(**w.params, **w.init)
+    if "nz" in grid:  # D3Q19 grid (include/lb3.h): plain or staged flux passes
+        g3 = lb.Grid3(store=store, stream=stream, **grid).init(**w.params, **w.init)
+        if w.scheme == "fv" and FV3_SCHEDULE != "auto":
+            g3.set_fv_schedule(lb.LB3_FV_PLAIN if FV3_SCHEDULE == "plain" else lb.LB3_FV_STAGED)
+        return g3
     g = lb.Grid(store=store, stream=stream, **grid)
     g.init(**w.params, **w.init)
     if w.scheme == "fv":
@@ -131,7 +135,11 @@ def make_grid(lb, w, stream, tune=True):
 
 def schedule_name(lb, g, scheme):
     if isinstance(g, lb.Grid3):
-        return "3-D fv four passes (collision; predictor; star; corrector)" if scheme == "fv" else "3-D st push"
+        if scheme != "fv":
+            return "3-D st push"
+        if g.fv_schedule == lb.LB3_FV_STAGED:
+            return "3-D fv four passes (collision; staged predictor; star; staged corrector)"
+        return "3-D fv four passes (collision; predictor; star; corrector)"
     if scheme != "fv":
         if g.store == lb.LB_STORE_F64:
             return "st push, one thread per cell"
@@ -421,10 +429,13 @@ def main():
     ap.add_argument("--serving-rate", type=float, default=60.0, help="Poisson arrivals per second")
     ap.add_argument("--fv-schedule", default="tune",
                     help="tune (autotuner), tile, march[:rows per CTA] or pair[:rows per CTA]")
+    ap.add_argument("--fv3-schedule", default="auto", choices=["auto", "plain", "staged"],
+                    help="flux passes of the 3-D FV step (include/lb3.h)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
-    global FV_SCHEDULE
+    global FV_SCHEDULE, FV3_SCHEDULE
     FV_SCHEDULE = args.fv_schedule
+    FV3_SCHEDULE = args.fv3_schedule
     if args.impl == "reference":
         return run_reference(args)
 

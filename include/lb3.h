@@ -75,8 +75,46 @@ lb_status lb3_create_grid(const lb3_grid_desc* desc, lb3_grid** out);
  * seed ^ ((k ny + j) nx + i). */
 lb_status lb3_init(lb3_grid* grid, const lb3_params* params, const lb3_init_desc* init);
 
-/* nsteps FV steps, Eq. (semi-heun): three kernel launches per step. */
+/* nsteps FV steps, Eq. (semi-heun): six kernel launches per step (the
+ * collision pass, z ghost planes of h, the predictor's flux pass, the moments
+ * of f~* and h*, z ghost planes of h*, the corrector's flux pass). */
 lb_status lb3_step_fv(lb3_grid* grid, int nsteps);
+
+/* Flux passes of lb3_step_fv (the QUICK divergence of Sec. II B 3):
+ *   LB3_FV_PLAIN:  one population per CTA; stencil nodes read through the
+ *                  caches; every grid;
+ *   LB3_FV_STAGED: one population per CTA; its z planes staged in shared
+ *                  memory by bulk asynchronous copies several planes ahead;
+ *                  needs x and y periodic and nx a power of two <= 256 whose
+ *                  rows are a multiple of 16 bytes (nx >= 4 for FP32, >= 2
+ *                  for FP64);
+ *   LB3_FV_AUTO:   STAGED where the grid allows it, else PLAIN (default).
+ * Both give the same step up to the rounding of the folded face weights.
+ * lb3_set_fv_schedule returns LB_ERR_ARG for STAGED on a grid it does not
+ * serve; lb3_get_fv_schedule writes the passes a step runs (PLAIN or
+ * STAGED). */
+#define LB3_FV_AUTO 0
+#define LB3_FV_PLAIN 1
+#define LB3_FV_STAGED 2
+lb_status lb3_set_fv_schedule(lb3_grid* grid, int schedule);
+lb_status lb3_get_fv_schedule(lb3_grid* grid, int* resolved);
+/* Shape of the staged passes: x rows per tile (1 .. 1024 / nx, FP64
+ * 512 / nx), z planes per CTA (1 .. 256) and planes of copies in flight
+ * ahead of the arithmetic (1 .. 12); 0 keeps the default of each (rows
+ * min(16, 1024 / nx), 16 planes, 3 ahead).  LB_ERR_ARG when out of range or
+ * beyond 200 KiB of shared memory per CTA.  Results do not depend on it. */
+lb_status lb3_set_fv_staged_shape(lb3_grid* grid, int rows, int planes, int ahead);
+
+/* Every wait of the staged passes on its copies is bounded (0.5 s).  A pass
+ * whose wait runs out records it on the device, and the next lb3_sync,
+ * lb3_moments, lb3_conservation or lb3_nusselt returns LB_ERR_TIMEOUT; the
+ * grid is then poisoned (LB_ERR_STATE) until lb3_init.
+ * lb3_debug_drop_copies(grid, 1) is the test hook of that path: each CTA of
+ * the staged passes announces its first copy group without starting it, so
+ * its wait runs out after 2 ms and the step reports LB_ERR_TIMEOUT.  No
+ * fault is raised and the context stays usable.  0 restores normal steps. */
+lb_status lb3_debug_drop_copies(lb3_grid* grid, int on);
+
 /* nsteps ST steps, Eq. (ST); needs uniform unit spacing on every axis and
  * dt = 1 (LB_ERR_ARG otherwise).  One launch per step. */
 lb_status lb3_step_st(lb3_grid* grid, int nsteps);

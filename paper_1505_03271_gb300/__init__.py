@@ -95,12 +95,14 @@ SYMBOLS = ["lb_create_grid", "lb_init", "lb_step_fv", "lb_step_st", "lb_moments"
            "lb_set_fv_scheme", "lb_get_fv_scheme", "lb_set_boundary_density",
            "lb3_create_grid", "lb3_init", "lb3_step_fv", "lb3_step_st", "lb3_moments",
            "lb3_conservation", "lb3_nusselt", "lb3_set_populations", "lb3_get_populations", "lb3_sync",
-           "lb3_destroy",
+           "lb3_destroy", "lb3_set_fv_schedule", "lb3_get_fv_schedule", "lb3_debug_drop_copies",
+           "lb3_set_fv_staged_shape",
            "lb_autotune_fv", "lb_server_create", "lb_server_submit", "lb_server_pump",
            "lb_server_results", "lb_server_clock", "lb_server_destroy"]
 LB_FV_AUTO, LB_FV_TILE, LB_FV_MARCH, LB_FV_PAIR, LB_FV_PTILE, LB_FV_SPLIT = 0, 1, 2, 3, 4, 5
 LB_SERVE_SHARE, LB_SERVE_SHORTEST = 0, 1
 LB_FV_HEUN, LB_FV_SEMI, LB_FV_EULER = 0, 1, 2
+LB3_FV_AUTO, LB3_FV_PLAIN, LB3_FV_STAGED = 0, 1, 2
 
 _lib = None
 
@@ -157,6 +159,10 @@ def load(build: bool = True) -> C.CDLL:
     L.lb3_set_populations.argtypes = [G, _DP, _DP]
     L.lb3_get_populations.argtypes = [G, _DP, _DP]
     L.lb3_sync.argtypes = [G]
+    L.lb3_set_fv_schedule.argtypes = [G, C.c_int]
+    L.lb3_get_fv_schedule.argtypes = [G, C.POINTER(C.c_int)]
+    L.lb3_debug_drop_copies.argtypes = [G, C.c_int]
+    L.lb3_set_fv_staged_shape.argtypes = [G, C.c_int, C.c_int, C.c_int]
     L.lb3_destroy.argtypes = [G]
     L.lb_sync.argtypes = [G]
     L.lb_destroy.argtypes = [G]
@@ -553,4 +559,27 @@ class Grid3:
 
     def sync(self):
         _check(load().lb3_sync(self._h))
+        return self
+
+    def set_fv_schedule(self, schedule):
+        """LB3_FV_AUTO, LB3_FV_PLAIN or LB3_FV_STAGED (flux passes of step_fv)."""
+        _check(load().lb3_set_fv_schedule(self._h, int(schedule)))
+        return self
+
+    def set_staged_shape(self, rows=0, planes=0, ahead=0):
+        """Rows per tile, z planes per CTA and planes in flight of the staged
+        flux passes (0: default)."""
+        _check(load().lb3_set_fv_staged_shape(self._h, int(rows), int(planes), int(ahead)))
+        return self
+
+    @property
+    def fv_schedule(self):
+        """The flux passes a step runs: LB3_FV_PLAIN or LB3_FV_STAGED."""
+        v = C.c_int()
+        _check(load().lb3_get_fv_schedule(self._h, C.byref(v)))
+        return v.value
+
+    def drop_copies(self, on=True):
+        """Test hook of the staged passes' bounded waits (include/lb3.h)."""
+        _check(load().lb3_debug_drop_copies(self._h, int(bool(on))))
         return self

@@ -495,20 +495,33 @@ dim3 grid3(const int* n) { return dim3((n[0] + 31) / 32, (n[1] + 7) / 8, n[2]); 
 // z planes per CTA of the flux passes
 constexpr int kZChunk = 16;
 
+// staged: the flux passes of k3_staged.cu instead of k3_adv
 template <typename R, typename S, bool TH>
-cudaError_t run_fv3(const Args3<R>& A, cudaStream_t s) {
+cudaError_t run_fv3(const Args3<R>& A, bool staged, cudaStream_t s) {
     const dim3 b(32, 8), g = grid3(A.n);
     const int np = TH ? 2 * Q3 : Q3;
     const int chunks = (A.n[2] + kZChunk - 1) / kZChunk;
     const dim3 gx((A.n[0] + 31) / 32, (A.n[1] + 7) / 8, 1);
     const dim3 ga(gx.x, gx.y, chunks * np), gz(gx.x, gx.y, 4 * np);
+    const Prec p = sizeof(R) == 8 ? Prec::F64 : Prec::F32;
+    cudaError_t e;
     k3_pre<R, S, TH><<<g, b, 0, s>>>(A);
     k3_ghostz<R><<<gz, b, 0, s>>>(A, 0, np);
-    k3_adv<R, S, false><<<ga, b, 0, s>>>(A, np, kZChunk);
+    if (staged) {
+        if ((e = launch3_adv_staged(p, false, np, &A, s)) != cudaSuccess) return e;
+    } else {
+        k3_adv<R, S, false><<<ga, b, 0, s>>>(A, np, kZChunk);
+        count_launch();
+    }
     k3_star<R, TH><<<g, b, 0, s>>>(A);
     k3_ghostz<R><<<gz, b, 0, s>>>(A, 1, np);
-    k3_adv<R, S, true><<<ga, b, 0, s>>>(A, np, kZChunk);
-    for (int q = 0; q < 6; ++q) count_launch();
+    if (staged) {
+        if ((e = launch3_adv_staged(p, true, np, &A, s)) != cudaSuccess) return e;
+    } else {
+        k3_adv<R, S, true><<<ga, b, 0, s>>>(A, np, kZChunk);
+        count_launch();
+    }
+    for (int q = 0; q < 4; ++q) count_launch();
     return cudaGetLastError();
 }
 
@@ -521,14 +534,14 @@ cudaError_t run_st3(const Args3<R>& A, cudaStream_t s) {
 
 }  // namespace
 
-cudaError_t launch3_fv(Prec p, bool th, const void* args, cudaStream_t s) {
+cudaError_t launch3_fv(Prec p, bool th, bool staged, const void* args, cudaStream_t s) {
     if (p == Prec::F64) {
         const auto& A = *static_cast<const Args3<double>*>(args);
-        return th ? run_fv3<double, double, true>(A, s) : run_fv3<double, double, false>(A, s);
+        return th ? run_fv3<double, double, true>(A, staged, s) : run_fv3<double, double, false>(A, staged, s);
     }
     if (p == Prec::F32) {
         const auto& A = *static_cast<const Args3<float>*>(args);
-        return th ? run_fv3<float, float, true>(A, s) : run_fv3<float, float, false>(A, s);
+        return th ? run_fv3<float, float, true>(A, staged, s) : run_fv3<float, float, false>(A, staged, s);
     }
     return cudaErrorInvalidValue;
 }

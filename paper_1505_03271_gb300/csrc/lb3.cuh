@@ -70,6 +70,13 @@ struct Args3 {
     const R* ft[3];     // the same, face-major (kFaceRow values per face)
     R dt, om, omh, cf, hf, omg, omgh;
     R ax, ay, az, bg, T0, dTb, dTt;  // dTb, dTt: plate temperature - T0 (z walls)
+    // staged flux passes (k3_staged.cu): status word a CTA sets when a bounded
+    // wait runs out, the limit of each wait, and the test hook that leaves
+    // the first copy group of every CTA unstarted
+    int* werr;
+    unsigned long long wait_ns;
+    int drop_copy;
+    int sshape[3];  // requested rows per tile, planes per CTA, planes ahead (0: default)
 };
 
 struct Aux3 {
@@ -80,7 +87,15 @@ struct Aux3 {
     double dt, ax, ay, az, bg, T0;
 };
 
-cudaError_t launch3_fv(Prec p, bool th, const void* args, cudaStream_t s);
+// One FV step.  staged: run the flux passes of k3_staged.cu (the grid must
+// pass adv3_staged_ok).
+cudaError_t launch3_fv(Prec p, bool th, bool staged, const void* args, cudaStream_t s);
+// The staged flux pass (k3_staged.cu): whether it serves a grid, and one launch
+// (corr: the corrector's pass; np: 19 or 38 populations).
+bool adv3_staged_ok(const int* n, const int* bc, Prec p);
+// whether a requested (rows per tile, planes per CTA, planes ahead) fits the grid (0: default)
+bool adv3_staged_shape_ok(const int* n, Prec p, int ty, int kc, int ahead);
+cudaError_t launch3_adv_staged(Prec p, bool corr, int np, const void* args, cudaStream_t s);
 cudaError_t launch3_st(Prec p, bool th, const void* args, cudaStream_t s);
 // fields [5][N] (rho, ux, uy, uz, T) on the device -> storage (equilibrium in tilded variables)
 cudaError_t launch3_init(Prec p, bool th, const Aux3& a, const double* fields, void* f, void* g, cudaStream_t s);

@@ -34,6 +34,10 @@ struct lb3_grid {
     double* width[3] = {nullptr, nullptr, nullptr};
     double* fields = nullptr;  // [5][N] staging
     double* plane = nullptr;   // [nz][8] plane sums
+    int* werr = nullptr;       // set by a staged flux pass whose bounded wait ran out
+    int fv_sched = LB3_FV_AUTO;
+    int sshape[3] = {0, 0, 0};  // staged pass shape: rows per tile, planes per CTA, planes ahead
+    int drop_copy = 0;         // test hook of the bounded waits (lb3_debug_drop_copies)
 };
 
 namespace {
@@ -73,6 +77,36 @@ void release3(lb3_grid* G) {
     }
     if (G->fields) cudaFree(G->fields);
     if (G->plane) cudaFree(G->plane);
+    if (G->werr) cudaFree(G->werr);
+}
+
+// Wait limits of the staged flux passes: generous in production (a copy
+// group takes microseconds), short under the test hook so that the test
+// ends quickly.
+constexpr unsigned long long kWaitNs = 500000000ULL, kWaitTestNs = 2000000ULL;
+
+bool staged_ok3(const lb3_grid* G) {
+    const int bc[3] = {G->ax[0].bc, G->ax[1].bc, G->ax[2].bc};
+    return adv3_staged_ok(G->n, bc, G->prec);
+}
+
+// the flux passes a step runs: staged (k3_staged.cu) or plain (k3_adv)
+bool staged3(const lb3_grid* G) {
+    return G->fv_sched == LB3_FV_STAGED || (G->fv_sched == LB3_FV_AUTO && staged_ok3(G));
+}
+
+// LB_ERR_TIMEOUT (and the grid poisoned) when a staged pass reported a wait
+// that ran out; synchronises the grid's stream.
+lb_status wait_status3(lb3_grid* G) {
+    int flag = 0;
+    CK3(cudaMemcpyAsync(&flag, G->werr, sizeof(int), cudaMemcpyDeviceToHost, G->stream));
+    CK3(cudaStreamSynchronize(G->stream));
+    if (flag) {
+        G->poisoned = true;
+        return fail3(LB_ERR_TIMEOUT, "a bounded wait of a staged flux pass ran out: the step is incomplete and the "
+                                     "grid is poisoned until lb3_init");
+    }
+    return LB_OK;
 }
 
 template <typename R>
@@ -113,6 +147,10 @@ Args3<R> args3(const lb3_grid* G, bool st) {
     A.T0 = (R)p.T0;
     A.dTb = (R)(p.T_bot - p.T0);
     A.dTt = (R)(p.T_top - p.T0);
+    A.werr = G->werr;
+    A.drop_copy = G->drop_copy;
+    A.wait_ns = G->drop_copy ? kWaitTestNs : kWaitNs;
+    for (int q = 0; q < 3; ++q) A.sshape[q] = G->sshape[q];
     return A;
 }
 
@@ -224,6 +262,8 @@ lb_status lb3_create_grid(const lb3_grid_desc* d, lb3_grid** out) {
     }
     if (e == cudaSuccess) e = cudaMalloc(&G->fields, sizeof(double) * 5 * G->N);
     if (e == cudaSuccess) e = cudaMalloc(&G->plane, sizeof(double) * 8 * n[2]);
+    if (e == cudaSuccess) e = cudaMalloc(&G->werr, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(G->werr, 0, sizeof(int));
     if (e != cudaSuccess) return bail(e);
     *out = G;
     return LB_OK;
@@ -286,6 +326,7 @@ lb_status lb3_init(lb3_grid* G, const lb3_params* p, const lb3_init_desc* in) {
     G->cur = 0;
     Aux3 a = aux3(G);
     CK3(launch3_init(G->prec, G->d.thermal != 0, a, G->fields, G->f[0], G->g[0], G->stream));
+    CK3(cudaMemsetAsync(G->werr, 0, sizeof(int), G->stream));
     CK3(cudaStreamSynchronize(G->stream));  // h is released on return
     G->has_params = true;
     G->poisoned = false;
@@ -297,13 +338,14 @@ lb_status lb3_step_fv(lb3_grid* G, int nsteps) {
     if (s != LB_OK) return s;
     if (nsteps < 0) return fail3(LB_ERR_ARG, "nsteps must be >= 0");
     Dev3 dg(G->device);
+    const bool staged = staged3(G);
     for (int k = 0; k < nsteps; ++k) {
         if (G->prec == Prec::F64) {
             Args3<double> A = args3<double>(G, false);
-            CK3(launch3_fv(G->prec, G->d.thermal != 0, &A, G->stream));
+            CK3(launch3_fv(G->prec, G->d.thermal != 0, staged, &A, G->stream));
         } else {
             Args3<float> A = args3<float>(G, false);
-            CK3(launch3_fv(G->prec, G->d.thermal != 0, &A, G->stream));
+            CK3(launch3_fv(G->prec, G->d.thermal != 0, staged, &A, G->stream));
         }
         G->cur ^= 1;
     }
@@ -337,6 +379,7 @@ lb_status lb3_moments(lb3_grid* G, double* rho, double* ux, double* uy, double* 
     lb_status s = ready3(G);
     if (s != LB_OK) return s;
     Dev3 dg(G->device);
+    if ((s = wait_status3(G)) != LB_OK) return s;
     CK3(launch3_moments(G->prec, G->d.thermal != 0, aux3(G), G->fields, G->stream));
     double* outs[5] = {rho, ux, uy, uz, T};
     for (int q = 0; q < 5; ++q)
@@ -350,6 +393,8 @@ lb_status lb3_moments(lb3_grid* G, double* rho, double* ux, double* uy, double* 
 // Per-plane sums on the device, then a fixed-order sum over planes here.
 static lb_status plane_sums3(lb3_grid* G, std::vector<double>& ps) {
     Dev3 dg(G->device);
+    const lb_status s = wait_status3(G);
+    if (s != LB_OK) return s;
     CK3(launch3_moments(G->prec, G->d.thermal != 0, aux3(G), G->fields, G->stream));
     CK3(launch3_plane_sums(G->fields, G->width[0], G->width[1], G->width[2], G->n[0], G->n[1], G->n[2],
                            G->p.T0, G->plane, G->stream));
@@ -460,6 +505,40 @@ lb_status lb3_sync(lb3_grid* G) {
     if (!G) return fail3(LB_ERR_ARG, "NULL grid");
     Dev3 dg(G->device);
     CK3(cudaStreamSynchronize(G->stream));
+    return wait_status3(G);
+}
+
+lb_status lb3_set_fv_schedule(lb3_grid* G, int schedule) {
+    if (!G) return fail3(LB_ERR_ARG, "NULL grid");
+    if (schedule != LB3_FV_AUTO && schedule != LB3_FV_PLAIN && schedule != LB3_FV_STAGED)
+        return fail3(LB_ERR_ARG, "schedule must be LB3_FV_AUTO, LB3_FV_PLAIN or LB3_FV_STAGED");
+    if (schedule == LB3_FV_STAGED && !staged_ok3(G))
+        return fail3(LB_ERR_ARG, "the staged flux passes need x and y periodic and nx a power of two <= 256 "
+                                 "with rows a multiple of 16 bytes");
+    G->fv_sched = schedule;
+    return LB_OK;
+}
+
+lb_status lb3_set_fv_staged_shape(lb3_grid* G, int rows, int planes, int ahead) {
+    if (!G) return fail3(LB_ERR_ARG, "NULL grid");
+    if (!adv3_staged_shape_ok(G->n, G->prec, rows, planes, ahead))
+        return fail3(LB_ERR_ARG, "staged shape out of range: rows per tile 0..(1024 cells / nx, FP64 512), "
+                                 "planes per CTA 0..256, planes ahead 0..12, within the shared memory");
+    G->sshape[0] = rows;
+    G->sshape[1] = planes;
+    G->sshape[2] = ahead;
+    return LB_OK;
+}
+
+lb_status lb3_get_fv_schedule(lb3_grid* G, int* resolved) {
+    if (!G || !resolved) return fail3(LB_ERR_ARG, "NULL argument");
+    *resolved = staged3(G) ? LB3_FV_STAGED : LB3_FV_PLAIN;
+    return LB_OK;
+}
+
+lb_status lb3_debug_drop_copies(lb3_grid* G, int on) {
+    if (!G) return fail3(LB_ERR_ARG, "NULL grid");
+    G->drop_copy = on != 0;
     return LB_OK;
 }
 

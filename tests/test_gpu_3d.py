@@ -30,6 +30,11 @@ def _pair(lb, oracle, case, store, **kw):
     return g, r
 
 
+def oracle_weights3():
+    w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    return w[:, None, None, None]
+
+
 def _params(th):
     kw = dict(tau=0.3, dt=0.05, ax=2e-4, ay=-1e-4, az=5e-5)
     if th:
@@ -167,3 +172,134 @@ def test_rb_table_grid_sampled(lbgpu, oracle):
     assert np.abs(tg - tr).max() <= 2e-6 * np.abs(g0 - wts).max()
     m1 = g.conservation()
     assert abs(m1[0] / m0[0] - 1) < 1e-8
+
+
+# grids the staged flux passes serve: x and y periodic, nx a power of two with
+# 16-byte rows; ragged y tiles (ny not a multiple of the tile), z chunks with
+# a short last chunk, z walls and plates on stretched grids
+STAGED_CASES = [
+    dict(nx=8, ny=6, nz=10, sz=2, stretch_z=4.0, bcz=1, thermal=True),
+    dict(nx=16, ny=12, nz=20),
+    dict(nx=32, ny=10, nz=12, sz=1, stretch_z=1.5, bcz=1, thermal=True),
+    dict(nx=4, ny=3, nz=5, sy=1, stretch_y=1.2),
+    dict(nx=64, ny=20, nz=17, sz=1, stretch_z=2.0, bcz=1),
+]
+
+
+@pytest.mark.parametrize("store", ["f64", "f32"])
+@pytest.mark.parametrize("case", STAGED_CASES, ids=_ids)
+def test_fv3_staged_step(lbgpu, oracle, case, store):
+    """The staged flux passes (shared-memory z-plane ring filled by bulk
+    copies) against the FP64 oracle, 3 steps from a random state."""
+    lb = lbgpu
+    th = case.get("thermal", False)
+    g, r = _pair(lb, oracle, case, lb.STORE_NAMES[store], **_params(th))
+    g.set_fv_schedule(lb.LB3_FV_STAGED)
+    assert g.fv_schedule == lb.LB3_FV_STAGED
+    nx, ny, nz = case["nx"], case["ny"], case["nz"]
+    f = inputs.random_populations3(nx, ny, nz, seed=3 * nx + nz, amp=0.2)
+    gg = inputs.random_populations3(nx, ny, nz, seed=9, amp=0.2) if th else None
+    g.set_pops(f, gg)
+    f, gg = g.get_pops()
+    r.set_pops(f, gg)
+    g.step_fv(3)
+    r.step_fv(3)
+    w = oracle.lattice3()[3][:, None, None, None]
+    fg, tg = g.get_pops()
+    fr, tr = r.get_pops()
+    assert np.abs(fg - fr).max() <= (1e-13 if store == "f64" else 2e-6 * np.abs(f - w).max())
+    if th:
+        assert np.abs(tg - tr).max() <= (1e-13 if store == "f64" else 2e-6 * np.abs(gg - w).max())
+
+
+@pytest.mark.parametrize("store", ["f64", "f32"])
+def test_fv3_staged_matches_plain(lbgpu, store):
+    """Both flux schedules give the same 5 steps on a thermal RB grid, up to
+    the rounding of the folded face weights."""
+    lb = lbgpu
+    case = dict(nx=32, ny=24, nz=18, lz=18.0, sz=2, stretch_z=3.0, bcz=1, thermal=True)
+    kw = dict(tau=0.2, tau_g=0.2, dt=0.2, beta=1e-2, grav=1.0, T0=1.0, T_bot=1.5, T_top=0.5)
+    out = []
+    for sched in (lb.LB3_FV_PLAIN, lb.LB3_FV_STAGED):
+        gk = {k: v for k, v in case.items() if k not in ("nx", "ny", "nz")}
+        g = lb.Grid3(case["nx"], case["ny"], case["nz"], store=lb.STORE_NAMES[store], **gk)
+        g.init(**kw, kind=lb.LB_INIT_RB, amp=1e-2, seed=7).set_fv_schedule(sched)
+        assert g.fv_schedule == sched
+        g.step_fv(5)
+        out.append(g.get_pops())
+    # relative to the deviation scale: FP64 rounding, or a few FP32 ulps per step
+    wts = oracle_weights3()
+    for q in range(2):
+        scale = np.abs(out[0][q] - wts * (1.0 if q == 0 else kw["T0"])).max()
+        assert np.abs(out[0][q] - out[1][q]).max() <= (1e-12 if store == "f64" else 1e-5) * scale
+
+
+def test_fv3_schedule_rules(lbgpu):
+    """AUTO resolves to the staged passes exactly where they serve the grid;
+    asking for them elsewhere is LB_ERR_ARG and leaves the grid as it was."""
+    lb = lbgpu
+    assert lb.Grid3(16, 8, 8).fv_schedule == lb.LB3_FV_STAGED
+    for kw in (dict(nx=12, ny=8, nz=8), dict(nx=16, ny=8, nz=8, bcy=lb.LB_BC_WALLS),
+               dict(nx=2, ny=8, nz=8), dict(nx=512, ny=2, nz=2)):
+        g = lb.Grid3(kw.pop("nx"), kw.pop("ny"), kw.pop("nz"), **kw)
+        assert g.fv_schedule == lb.LB3_FV_PLAIN
+        with pytest.raises(lb.LBError) as e:
+            g.set_fv_schedule(lb.LB3_FV_STAGED)
+        assert e.value.status == lb.LB_ERR_ARG
+        assert g.fv_schedule == lb.LB3_FV_PLAIN
+    g = lb.Grid3(2, 8, 8, store=lb.LB_STORE_F64)  # 16-byte FP64 rows
+    assert g.fv_schedule == lb.LB3_FV_STAGED
+    with pytest.raises(lb.LBError):
+        g.set_fv_schedule(7)
+
+
+def test_fv3_staged_wait_timeout(lbgpu, oracle):
+    """The bounded waits of the staged passes: with the test hook on, each
+    CTA announces a copy group it never starts, its wait runs out (2 ms) and
+    the step reports LB_ERR_TIMEOUT on the next sync; the grid is poisoned
+    until lb3_init, after which the same context steps correctly again."""
+    lb = lbgpu
+    case = dict(nx=16, ny=8, nz=6)
+    kw = dict(tau=0.3, dt=0.25, ax=1e-4)
+    g, r = _pair(lb, oracle, case, lb.LB_STORE_F32, **kw)
+    g.drop_copies(True)
+    g.step_fv(1)
+    with pytest.raises(lb.LBError) as e:
+        g.sync()
+    assert e.value.status == lb.LB_ERR_TIMEOUT
+    with pytest.raises(lb.LBError) as e:
+        g.step_fv(1)
+    assert e.value.status == lb.LB_ERR_STATE
+    g.drop_copies(False)
+    g.init(**kw)
+    f = inputs.random_populations3(16, 8, 6, seed=4, amp=0.2)
+    g.set_pops(f)
+    f, _ = g.get_pops()
+    r.set_pops(f)
+    g.step_fv(2).sync()
+    r.step_fv(2)
+    w = oracle.lattice3()[3][:, None, None, None]
+    assert np.abs(g.get_pops()[0] - r.get_pops()[0]).max() <= 2e-6 * np.abs(f - w).max()
+
+
+def test_fv3_staged_shapes(lbgpu):
+    """Rows per tile, z planes per CTA and copies in flight change the
+    schedule of the staged passes, not their arithmetic: the state after 3
+    steps is bitwise the same for every shape; shapes out of range are
+    LB_ERR_ARG."""
+    lb = lbgpu
+    kw = dict(tau=0.2, tau_g=0.2, dt=0.2, beta=1e-2, grav=1.0, T0=1.0, T_bot=1.5, T_top=0.5)
+    ref = None
+    for shape in ((0, 0, 0), (1, 1, 1), (3, 5, 6), (16, 64, 12), (2, 7, 2)):
+        g = lb.Grid3(16, 12, 20, lz=20.0, sz=lb.LB_AXIS_TANH, stretch_z=1.5, bcz=lb.LB_BC_WALLS, thermal=True)
+        g.init(**kw, kind=lb.LB_INIT_RB, amp=1e-2, seed=3).set_staged_shape(*shape).step_fv(3)
+        f, t = g.get_pops()
+        if ref is None:
+            ref = (f, t)
+        else:
+            assert np.array_equal(f, ref[0]) and np.array_equal(t, ref[1]), shape
+    g = lb.Grid3(16, 12, 20)
+    for bad in ((65, 0, 0), (0, 300, 0), (0, 0, 13), (-1, 0, 0)):
+        with pytest.raises(lb.LBError) as e:
+            g.set_staged_shape(*bad)
+        assert e.value.status == lb.LB_ERR_ARG
