@@ -75,9 +75,10 @@ lb_status lb3_create_grid(const lb3_grid_desc* desc, lb3_grid** out);
  * seed ^ ((k ny + j) nx + i). */
 lb_status lb3_init(lb3_grid* grid, const lb3_params* params, const lb3_init_desc* init);
 
-/* nsteps FV steps, Eq. (semi-heun): six kernel launches per step (the
- * collision pass, z ghost planes of h, the predictor's flux pass, the moments
- * of f~* and h*, z ghost planes of h*, the corrector's flux pass). */
+/* nsteps FV steps, Eq. (semi-heun): four kernel launches per step (the
+ * collision pass with h and its z ghost planes, the predictor's flux pass,
+ * the moments of f~* with h* and its ghost planes, the corrector's flux
+ * pass). */
 lb_status lb3_step_fv(lb3_grid* grid, int nsteps);
 
 /* Flux passes of lb3_step_fv (the QUICK divergence of Sec. II B 3):

@@ -5,14 +5,14 @@
 // half-way bounce-back at walls, anti-bounce-back of g at the z plates.
 //
 // FV, Eqs. (semi) and (semi-heun): four passes over the grid with the
-// intermediate fields in HBM, plus two small ghost-plane fills:
-//   k3_pre          f~ -> h^n and f~ + Coll^n                           (local)
-//   k3_ghostz       z ghost planes of h^n (walls: Sec. II B 5)
+// intermediate fields in HBM:
+//   k3_pre          f~ -> h^n (and its z ghost planes) and f~ + Coll^n  (local)
 //   k3_adv (pred.)  A[h^n] per population (QUICK on its own stencil)
 //                   -> f~* (parked), f~ + Coll - dt/2 A
-//   k3_star         moments of f~* -> h*                                (local)
-//   k3_ghostz       z ghost planes of h*
+//   k3_star         moments of f~* -> h* (and its z ghost planes)       (local)
 //   k3_adv (corr.)  A[h*] -> f~^(n+1) = f~ + Coll - dt/2 (A[h^n] + A[h*])
+// The flux passes are k3_adv below or, where the grid allows it, the staged
+// passes of k3_staged.cu.
 // A fused 3-D tile would recompute a 4-cell halo on all six faces, or hold
 // 19 (38) populations of several halo planes in shared memory; these passes
 // recompute nothing and stream about 6x the compulsory bytes.  Faces are
@@ -93,7 +93,7 @@ __device__ __forceinline__ void load19(const void* src, long long N, long long c
 
 // Padded layout of the advected fields h, h* (and hg, hg*): two ghost
 // planes below and above the grid in z, [pop][nz + 4][ny][nx], so that the
-// z stencil never leaves the array.  k3_ghostz fills the ghost planes:
+// z stencil never leaves the array.  zghost fills the ghost planes:
 // periodic copies, or the wall rules of Sec. II B 5 (double reflection,
 // h_a(ghost) = h_inv(a)(mirror); the thermal field anti-reflected,
 // hg'_a(ghost) = 2 w_a (T_wall - T0) - hg'_inv(a)(mirror)).
@@ -130,6 +130,43 @@ __device__ __forceinline__ bool cell_index(const int* n, int& i, int& j, int& k)
     return i < n[0] && j < n[1];
 }
 
+// z ghost planes of the padded advected field (Sec. II B 5), written by the
+// cells they copy, so that no separate pass fills them.  Periodic z: ghost
+// plane gk in {-2, -1, nz, nz + 1} holds plane gk mod nz.  z walls: the
+// ghost -1 - k (k = 0, 1) and 2 nz - 1 - k (k = nz - 2, nz - 1) of the
+// reflected population inv(a) hold h_a of plane k (double reflection); the
+// thermal field is anti-reflected about the plate: 2 w (T_wall - T0) - h.
+template <typename R>
+__device__ __forceinline__ void zghost(R* P, int a, R v, int i, int j, int k, bool th, const Args3<R>& A) {
+    const int nz = A.n[2];
+    if (A.bc[2] == LB_BC_PERIODIC) {
+#pragma unroll
+        for (int g = 0; g < 4; ++g) {
+            const int gk = g < 2 ? g - 2 : nz + g - 2;
+            const int src = ((gk % nz) + nz) % nz;
+            if (src == k) P[(long long)a * A.NP + padded3(A.n, i, j, gk)] = v;
+        }
+    } else {
+        const int b = inv3(a);
+        if (k <= 1) P[(long long)b * A.NP + padded3(A.n, i, j, -1 - k)] = th ? R(2) * w3<R>(b) * A.dTb - v : v;
+        if (k >= nz - 2)
+            P[(long long)b * A.NP + padded3(A.n, i, j, 2 * nz - 1 - k)] = th ? R(2) * w3<R>(b) * A.dTt - v : v;
+    }
+}
+
+// The ghost images of cell (i, j, k) of h (and hg), from the values this
+// thread has just stored; k is uniform over the CTA, so interior planes
+// skip it at no cost.
+template <typename R, bool TH>
+__device__ __forceinline__ void zghosts(R* P, R* PG, int i, int j, int k, const Args3<R>& A) {
+    if (k >= 2 && k < A.n[2] - 2) return;
+    const long long cp = padded3(A.n, i, j, k);
+    for (int a = 0; a < Q3; ++a) {
+        zghost(P, a, P[a * A.NP + cp], i, j, k, false, A);
+        if constexpr (TH) zghost(PG, a, PG[a * A.NP + cp], i, j, k, true, A);
+    }
+}
+
 // ---- FV pass 1: h^n and f~ + Coll^n (Eq. (semi)) ----
 template <typename R, typename S, bool TH>
 __global__ void __launch_bounds__(256) k3_pre(const Args3<R> A) {
@@ -154,30 +191,7 @@ __global__ void __launch_bounds__(256) k3_pre(const Args3<R> A) {
             A.GC[a * N + c] = e[a] + A.omg * neqg;
         }
     }
-}
-
-// ---- z ghost planes of h (star = 0) or h* (star = 1) ----
-// blockIdx.z = ghost * np + p, ghost 0..3 -> planes -2, -1, nz, nz + 1.
-template <typename R>
-__global__ void __launch_bounds__(256) k3_ghostz(const Args3<R> A, int star, int np) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y * blockDim.y + threadIdx.y;
-    if (i >= A.n[0] || j >= A.n[1]) return;
-    const int p = blockIdx.z % np, gh = blockIdx.z / np;
-    const bool th = p >= Q3;
-    const int a = th ? p - Q3 : p, nz = A.n[2];
-    const int gk = gh < 2 ? gh - 2 : nz + gh - 2;
-    R* P = th ? (star ? A.HGS : A.HG) : (star ? A.HS : A.H);
-    R v;
-    if (A.bc[2] == LB_BC_PERIODIC) {
-        const int src = ((gk % nz) + nz) % nz;
-        v = P[(long long)a * A.NP + padded3(A.n, i, j, src)];
-    } else {
-        const bool lo = gk < 0;
-        const int src = lo ? -gk - 1 : 2 * nz - 1 - gk;
-        v = P[(long long)inv3(a) * A.NP + padded3(A.n, i, j, src)];
-        if (th) v = R(2) * w3<R>(a) * (lo ? A.dTb : A.dTt) - v;
-    }
-    P[(long long)a * A.NP + padded3(A.n, i, j, gk)] = v;
+    zghosts<R, TH>(A.H, A.HG, i, j, k, A);
 }
 
 // ---- FV flux passes, one population per CTA ----
@@ -351,6 +365,7 @@ __global__ void __launch_bounds__(256) k3_star(const Args3<R> A) {
             A.HGS[a * NP + cp] = es + A.omgh * (geqd - es);
         }
     }
+    zghosts<R, TH>(A.HS, A.HGS, i, j, k, A);
 }
 
 // ---- ST: collide and push, Eq. (ST) at dt = dx = 1 ----
@@ -502,11 +517,10 @@ cudaError_t run_fv3(const Args3<R>& A, bool staged, cudaStream_t s) {
     const int np = TH ? 2 * Q3 : Q3;
     const int chunks = (A.n[2] + kZChunk - 1) / kZChunk;
     const dim3 gx((A.n[0] + 31) / 32, (A.n[1] + 7) / 8, 1);
-    const dim3 ga(gx.x, gx.y, chunks * np), gz(gx.x, gx.y, 4 * np);
+    const dim3 ga(gx.x, gx.y, chunks * np);
     const Prec p = sizeof(R) == 8 ? Prec::F64 : Prec::F32;
     cudaError_t e;
     k3_pre<R, S, TH><<<g, b, 0, s>>>(A);
-    k3_ghostz<R><<<gz, b, 0, s>>>(A, 0, np);
     if (staged) {
         if ((e = launch3_adv_staged(p, false, np, &A, s)) != cudaSuccess) return e;
     } else {
@@ -514,14 +528,13 @@ cudaError_t run_fv3(const Args3<R>& A, bool staged, cudaStream_t s) {
         count_launch();
     }
     k3_star<R, TH><<<g, b, 0, s>>>(A);
-    k3_ghostz<R><<<gz, b, 0, s>>>(A, 1, np);
     if (staged) {
         if ((e = launch3_adv_staged(p, true, np, &A, s)) != cudaSuccess) return e;
     } else {
         k3_adv<R, S, true><<<ga, b, 0, s>>>(A, np, kZChunk);
         count_launch();
     }
-    for (int q = 0; q < 4; ++q) count_launch();
+    for (int q = 0; q < 2; ++q) count_launch();
     return cudaGetLastError();
 }
 

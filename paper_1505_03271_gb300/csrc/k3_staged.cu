@@ -17,14 +17,15 @@
 //
 // Grids served (adv3_staged_ok): x and y periodic, and nx a power of two
 // <= 256 whose rows are a multiple of 16 bytes (the bulk-copy granule).  z
-// may be periodic or walls: k3_ghostz fills the padded z ghost planes of h
-// for both passes.
+// may be periodic or walls: the collision and star passes of k3.cu write
+// the padded z ghost planes of h and h*.
 //
 // Every wait on a copy is bounded (Args3::wait_ns).  A CTA whose wait runs
 // out sets *Args3::werr, waits (bounded again) for the copies it has issued,
 // and returns; the host reports LB_ERR_TIMEOUT.
 #include "lb3.cuh"
 #include "lb_async.cuh"
+#include "lb_pair.cuh"
 
 namespace lbgb {
 
@@ -146,28 +147,34 @@ __global__ void __launch_bounds__(kThreads + 32, sizeof(R) == 8 ? 2 : 3)
         const R* P = G ? (CORR ? A.HGS : A.HG) : (CORR ? A.HS : A.H);
         const R* FCp = G ? A.GC : A.FC;
         const int hrows = moving ? (cy != 0 ? rows : ty) : 0, hr0 = cy != 0 ? 0 : 2;
-        int L = 0;
+        int L = 0, slot = 0, round = 0, fslot = 0;  // slot = L % RS, round = L / RS, fslot = (L - Z) % FS
         for (; L < nload; ++L) {
-            const int slot = L % RS, itf = L - Z;
-            if (L >= RS && !async::bar_wait(&empty[slot], (L / RS - 1) & 1, A.wait_ns)) break;
+            const int itf = L - Z;
+            if (round > 0 && !async::bar_wait(&empty[slot], (round - 1) & 1, A.wait_ns)) break;
             const int frows = itf >= 0 ? min(ty, ny - j0) : 0;
             async::fence_async_shared();
             async::bar_arrive_expect(&full[slot], (unsigned)(hrows + frows) * rowb);
-            if (A.drop_copy && L == 0) continue;  // test hook: these copies never start
-            // the h rows j0 - 2 + rr, wrapped in y: one copy per run of consecutive rows
-            const long long hp = (long long)a * NP + (long long)(k0 - zlo + L + 2) * plane;
-            for (int rr = hr0, rend = hr0 + hrows; rr < rend;) {
-                int j = (j0 - 2 + rr) % ny;
-                j = j < 0 ? j + ny : j;
-                const int len = min(rend - rr, ny - j);
-                async::bulk_load(hring + ((size_t)slot * rows + rr) * nx, P + hp + (long long)j * nx,
-                                 (unsigned)len * rowb, &full[slot]);
-                rr += len;
+            if (!(A.drop_copy && L == 0)) {  // test hook: the copies of step 0 never start
+                // the h rows j0 - 2 + rr, wrapped in y: one copy per run of consecutive rows
+                const long long hp = (long long)a * NP + (long long)(k0 - zlo + L + 2) * plane;
+                for (int rr = hr0, rend = hr0 + hrows; rr < rend;) {
+                    int j = (j0 - 2 + rr) % ny;
+                    j = j < 0 ? j + ny : j;
+                    const int len = min(rend - rr, ny - j);
+                    async::bulk_load(hring + ((size_t)slot * rows + rr) * nx, P + hp + (long long)j * nx,
+                                     (unsigned)len * rowb, &full[slot]);
+                    rr += len;
+                }
+                if (frows > 0)
+                    async::bulk_load(fring + (size_t)fslot * ty * nx,
+                                     FCp + (long long)a * N + (long long)(k0 + itf) * plane + (long long)j0 * nx,
+                                     (unsigned)frows * rowb, &full[slot]);
             }
-            if (frows > 0)
-                async::bulk_load(fring + (size_t)(itf % FS) * ty * nx,
-                                 FCp + (long long)a * N + (long long)(k0 + itf) * plane + (long long)j0 * nx,
-                                 (unsigned)frows * rowb, &full[slot]);
+            if (++slot == RS) {
+                slot = 0;
+                ++round;
+            }
+            if (itf >= 0 && ++fslot == FS) fslot = 0;
         }
         if (L < nload) {
             // a wait ran out: report, then let the copies of the last RS
@@ -178,73 +185,161 @@ __global__ void __launch_bounds__(kThreads + 32, sizeof(R) == 8 ? 2 : 3)
         return;
     }
 
-    // the thread's cells: column i, rows r0 + m rstep of the tile
-    const int i = tid % nx, rstep = kThreads / nx, r0 = tid / nx;
-    int xo[4] = {0, 0, 0, 0};
-    R kx[4] = {0, 0, 0, 0};
-    if (cx != 0) {
+    // The computing warps' loop over the chunk's planes.  Ring positions are
+    // kept incrementally: s0 = it % RS (the step the iteration releases),
+    // sw = (it + Z) % RS and its phase (the step it waits for), sf = it % FS
+    // (its f~ + Coll).  body(it, hz, hc, fcp, kz, qb, pb) updates the
+    // thread's cells of plane k0 + it: hz[s] are the planes of the z nodes,
+    // hc the plane itself, fcp its f~ + Coll, kz its folded z weights, qb
+    // and pb the offsets of plane k0 + it of population a in the unpadded
+    // and padded fields.
+    auto planes = [&](auto&& body) {
+        bool ok = true;
+        for (int L = 0; L < Z && ok; ++L) ok = async::bar_wait(&full[L], 0, A.wait_ns);  // Z < RS: first round
+        int s0 = 0, sw = Z, sf = 0;
+        unsigned ph = 0;
+        for (int it = 0; it < nit && ok; ++it) {
+            if (!(ok = async::bar_wait(&full[sw], ph, A.wait_ns))) break;
+            const int k = k0 + it;
+            const R* hz[4];
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            int c = (i + s + (cx > 0 ? -2 : -1)) % nx;
-            xo[s] = c < 0 ? c + nx : c;
+            for (int s = 0; s < 4; ++s) hz[s] = hring + (size_t)(s0 + s < RS ? s0 + s : s0 + s - RS) * rows * nx;
+            const R* hc = zlo == 2 ? hz[2] : (zlo == 1 ? hz[1] : hz[0]);
+            R kz[4] = {0, 0, 0, 0};
+            if (cz != 0) {
+#pragma unroll
+                for (int s = 0; s < 4; ++s) kz[s] = zc[4 * it + s];
+            }
+            body(hz, hc, fring + (size_t)sf * ty * nx, kz, (long long)a * N + (long long)k * plane,
+                 (long long)a * NP + (long long)(k + 2) * plane);
+            __syncwarp();
+            if (lane == 0) async::bar_arrive(&empty[s0]);
+            s0 = s0 + 1 == RS ? 0 : s0 + 1;
+            sf = sf + 1 == FS ? 0 : sf + 1;
+            if (++sw == RS) {
+                sw = 0;
+                ph ^= 1;
+            }
         }
-        axis_fold(A.m[0], i, cx, kx);
-    }
-    R ky[kCells][4];
-#pragma unroll
-    for (int m = 0; m < kCells; ++m) {
-        const int j = j0 + r0 + m * rstep;
-#pragma unroll
-        for (int s = 0; s < 4; ++s) ky[m][s] = 0;
-        if (cy != 0 && r0 + m * rstep < ty && j < ny) axis_fold(A.m[1], j, cy, ky[m]);
-    }
+        return ok;
+    };
 
-    bool ok = true;
-    for (int L = 0; L < Z && ok; ++L) ok = async::bar_wait(&full[L % RS], (L / RS) & 1, A.wait_ns);
-    for (int it = 0; it < nit && ok; ++it) {
-        const int L = it + Z;
-        if (!(ok = async::bar_wait(&full[L % RS], (L / RS) & 1, A.wait_ns))) break;
-        const int k = k0 + it;
-        const R* hc = hring + (size_t)((it + zlo) % RS) * rows * nx;  // plane k
-        const R* fcp = fring + (size_t)(it % FS) * ty * nx;
-        const R* hz[4];
-        R kz[4] = {0, 0, 0, 0};
-#pragma unroll
-        for (int s = 0; s < 4; ++s) hz[s] = hring + (size_t)((it + s) % RS) * rows * nx;
-        if (cz != 0) {
-#pragma unroll
-            for (int s = 0; s < 4; ++s) kz[s] = zc[4 * it + s];
+    bool ok;
+    if constexpr (sizeof(R) == 4) {
+        // FP32: two adjacent x cells per thread (nx is even), packed f32x2
+        // arithmetic on 8-byte shared loads and 8-byte stores
+        using namespace pairmath;
+        const int np2 = nx >> 1, i = 2 * (tid % np2), rstep = kThreads / np2, r0 = tid / np2;
+        int xp[3] = {0, 0, 0};  // pairs (i-2, i-1), (i, i+1), (i+2, i+3), wrapped in x
+        float kl[4] = {0, 0, 0, 0}, kr[4] = {0, 0, 0, 0};
+        if (cx != 0) {
+            xp[0] = (i - 2 + nx) % nx;
+            xp[1] = i;
+            xp[2] = (i + 2) % nx;
+            axis_fold(A.m[0], i, cx, kl);
+            axis_fold(A.m[0], i + 1, cx, kr);
         }
-        const long long qb = (long long)a * N + (long long)k * plane;           // plane k of population a
-        const long long pb = (long long)a * NP + (long long)(k + 2) * plane;    // the same, padded
+        constexpr int kPairs = kCells / 2;
+        float ky[kPairs][4];
+#pragma unroll
+        for (int m = 0; m < kPairs; ++m) {
+            const int j = j0 + r0 + m * rstep;
+#pragma unroll
+            for (int s = 0; s < 4; ++s) ky[m][s] = 0;
+            if (cy != 0 && r0 + m * rstep < ty && j < ny) axis_fold(A.m[1], j, cy, ky[m]);
+        }
+        ok = planes([&](const R* const* hz, const R* hc, const R* fcp, const R* kz, long long qb, long long pb) {
+#pragma unroll
+            for (int m = 0; m < kPairs; ++m) {
+                const int r = r0 + m * rstep, j = j0 + r;
+                if (r >= ty || j >= ny) continue;
+                V2 v = bc(0.0f);
+                if (cx != 0) {
+                    const float* row = hc + (r + 2) * nx;
+                    const float2 p0 = *reinterpret_cast<const float2*>(row + xp[0]);
+                    const float2 p1 = *reinterpret_cast<const float2*>(row + xp[1]);
+                    const float2 p2 = *reinterpret_cast<const float2*>(row + xp[2]);
+                    // nodes of the left cell, then of the right one: (i-2..i+1 | i-1..i+2) for
+                    // c > 0, (i-1..i+2 | i..i+3) for c < 0
+                    const bool pos = cx > 0;
+                    const float n0 = pos ? p0.x : p0.y, n1 = pos ? p0.y : p1.x, n2 = pos ? p1.x : p1.y,
+                                n3 = pos ? p1.y : p2.x, n4 = pos ? p2.x : p2.y;
+                    v = fma2(mk(kl[0], kr[0]), mk(n0, n1), v);
+                    v = fma2(mk(kl[1], kr[1]), mk(n1, n2), v);
+                    v = fma2(mk(kl[2], kr[2]), mk(n2, n3), v);
+                    v = fma2(mk(kl[3], kr[3]), mk(n3, n4), v);
+                }
+                if (cy != 0) {
+                    const float* col = hc + (r + (cy > 0 ? 0 : 1)) * nx + i;
+#pragma unroll
+                    for (int s = 0; s < 4; ++s)
+                        v = fma2(bc(ky[m][s]), V2{*reinterpret_cast<const float2*>(col + s * nx)}, v);
+                }
+                if (cz != 0) {
+                    const int o = (r + 2) * nx + i;
+#pragma unroll
+                    for (int s = 0; s < 4; ++s) v = fma2(bc(kz[s]), V2{*reinterpret_cast<const float2*>(hz[s] + o)}, v);
+                }
+                const V2 f{*reinterpret_cast<const float2*>(fcp + r * nx + i)};
+                const int jo = j * nx + i;
+                if constexpr (CORR) {
+                    *reinterpret_cast<float2*>(static_cast<float*>(G ? A.gout : A.fout) + qb + jo) =
+                        fma2(bc(-A.hf), v, f).v;
+                } else {
+                    *reinterpret_cast<float2*>((G ? A.GC : A.FC) + qb + jo) = fma2(bc(-A.hf), v, f).v;
+                    *reinterpret_cast<float2*>((G ? A.HGS : A.HS) + pb + jo) = fma2(bc(-A.dt), v, f).v;
+                }
+            }
+        });
+    } else {
+        // FP64: one cell per thread-slot, column i, rows r0 + m rstep of the tile
+        const int i = tid % nx, rstep = kThreads / nx, r0 = tid / nx;
+        int xo[4] = {0, 0, 0, 0};
+        R kx[4] = {0, 0, 0, 0};
+        if (cx != 0) {
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                int c = (i + s + (cx > 0 ? -2 : -1)) % nx;
+                xo[s] = c < 0 ? c + nx : c;
+            }
+            axis_fold(A.m[0], i, cx, kx);
+        }
+        R ky[kCells][4];
 #pragma unroll
         for (int m = 0; m < kCells; ++m) {
-            const int r = r0 + m * rstep, j = j0 + r;
-            if (r >= ty || j >= ny) continue;
-            R v = 0;
-            if (cx != 0) {
-                const R* row = hc + (r + 2) * nx;
-                v = kx[0] * row[xo[0]] + kx[1] * row[xo[1]] + kx[2] * row[xo[2]] + kx[3] * row[xo[3]];
-            }
-            if (cy != 0) {
-                const R* col = hc + (r + (cy > 0 ? 0 : 1)) * nx + i;
-                v += ky[m][0] * col[0] + ky[m][1] * col[nx] + ky[m][2] * col[2 * nx] + ky[m][3] * col[3 * nx];
-            }
-            if (cz != 0) {
-                const int o = (r + 2) * nx + i;
-                v += kz[0] * hz[0][o] + kz[1] * hz[1][o] + kz[2] * hz[2][o] + kz[3] * hz[3][o];
-            }
-            const R f = fcp[r * nx + i];
-            const int jo = j * nx + i;
-            if constexpr (CORR) {
-                Store<S>::st(static_cast<S*>(G ? A.gout : A.fout) + qb + jo, f - A.hf * v);
-            } else {
-                (G ? A.GC : A.FC)[qb + jo] = f - A.hf * v;
-                (G ? A.HGS : A.HS)[pb + jo] = f - A.dt * v;
-            }
+            const int j = j0 + r0 + m * rstep;
+#pragma unroll
+            for (int s = 0; s < 4; ++s) ky[m][s] = 0;
+            if (cy != 0 && r0 + m * rstep < ty && j < ny) axis_fold(A.m[1], j, cy, ky[m]);
         }
-        __syncwarp();
-        if (lane == 0) async::bar_arrive(&empty[it % RS]);
+        ok = planes([&](const R* const* hz, const R* hc, const R* fcp, const R* kz, long long qb, long long pb) {
+#pragma unroll
+            for (int m = 0; m < kCells; ++m) {
+                const int r = r0 + m * rstep, j = j0 + r;
+                if (r >= ty || j >= ny) continue;
+                R v = 0;
+                if (cx != 0) {
+                    const R* row = hc + (r + 2) * nx;
+                    v = kx[0] * row[xo[0]] + kx[1] * row[xo[1]] + kx[2] * row[xo[2]] + kx[3] * row[xo[3]];
+                }
+                if (cy != 0) {
+                    const R* col = hc + (r + (cy > 0 ? 0 : 1)) * nx + i;
+                    v += ky[m][0] * col[0] + ky[m][1] * col[nx] + ky[m][2] * col[2 * nx] + ky[m][3] * col[3 * nx];
+                }
+                if (cz != 0) {
+                    const int o = (r + 2) * nx + i;
+                    v += kz[0] * hz[0][o] + kz[1] * hz[1][o] + kz[2] * hz[2][o] + kz[3] * hz[3][o];
+                }
+                const R f = fcp[r * nx + i];
+                const int jo = j * nx + i;
+                if constexpr (CORR) {
+                    Store<S>::st(static_cast<S*>(G ? A.gout : A.fout) + qb + jo, f - A.hf * v);
+                } else {
+                    (G ? A.GC : A.FC)[qb + jo] = f - A.hf * v;
+                    (G ? A.HGS : A.HS)[pb + jo] = f - A.dt * v;
+                }
+            }
+        });
     }
     if (!ok && lane == 0) atomicOr(A.werr, 1);
 }

@@ -40,15 +40,17 @@ __device__ __forceinline__ void bar_arrive(uint64_t* bar) {
 }
 
 // True once the phase of the given parity has completed (acquire: the
-// copied bytes are then visible to the waiting thread).
-__device__ __forceinline__ bool bar_try_wait(uint64_t* bar, unsigned parity) {
+// copied bytes are then visible to the waiting thread).  The thread is
+// suspended in hardware until the phase completes or about `hint_ns`
+// nanoseconds pass, so waiting warps take no issue slots from working ones.
+__device__ __forceinline__ bool bar_try_wait(uint64_t* bar, unsigned parity, unsigned hint_ns) {
     unsigned done;
     asm volatile(
         "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(done)
-        : "r"(smem_addr(bar)), "r"(parity)
+        : "r"(smem_addr(bar)), "r"(parity), "r"(hint_ns)
         : "memory");
     return done != 0;
 }
@@ -61,10 +63,11 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 // Waits for the phase, at most `limit_ns` nanoseconds; false when it ran out.
 __device__ __forceinline__ bool bar_wait(uint64_t* bar, unsigned parity, unsigned long long limit_ns) {
-    if (bar_try_wait(bar, parity)) return true;
+    constexpr unsigned kHintNs = 20000;
+    if (bar_try_wait(bar, parity, kHintNs)) return true;
     const unsigned long long t0 = global_ns();
     for (;;) {
-        if (bar_try_wait(bar, parity)) return true;
+        if (bar_try_wait(bar, parity, kHintNs)) return true;
         if (global_ns() - t0 > limit_ns) return false;
     }
 }
