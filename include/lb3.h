@@ -105,6 +105,16 @@ lb_status lb3_get_fv_schedule(lb3_grid* grid, int* resolved);
  * min(16, 1024 / nx), 16 planes, 3 ahead).  LB_ERR_ARG when out of range or
  * beyond 200 KiB of shared memory per CTA.  Results do not depend on it. */
 lb_status lb3_set_fv_staged_shape(lb3_grid* grid, int rows, int planes, int ahead);
+/* The shape the staged passes use (defaults resolved for this grid). */
+lb_status lb3_get_fv_staged_shape(lb3_grid* grid, int* rows, int* planes, int* ahead);
+/* Times the flux schedules on the grid's current state (one warm-up step and
+ * `steps` timed steps each, CUDA events on the grid's stream), keeps the
+ * fastest and restores the state bit for bit.  Candidates: the plain passes,
+ * and where the grid allows them the staged passes with rows per tile
+ * {default, default / 2}, planes per CTA {16, 32} and planes ahead {2, 3}.
+ * LB_ERR_ARG for steps < 1; LB_ERR_OOM without room for a copy of the
+ * state; LB_ERR_TIMEOUT (grid poisoned) if a timed step's wait ran out. */
+lb_status lb3_autotune_fv(lb3_grid* grid, int steps);
 
 /* Every wait of the staged passes on its copies is bounded (0.5 s).  A pass
  * whose wait runs out records it on the device, and the next lb3_sync,

@@ -96,7 +96,7 @@ SYMBOLS = ["lb_create_grid", "lb_init", "lb_step_fv", "lb_step_st", "lb_moments"
            "lb3_create_grid", "lb3_init", "lb3_step_fv", "lb3_step_st", "lb3_moments",
            "lb3_conservation", "lb3_nusselt", "lb3_set_populations", "lb3_get_populations", "lb3_sync",
            "lb3_destroy", "lb3_set_fv_schedule", "lb3_get_fv_schedule", "lb3_debug_drop_copies",
-           "lb3_set_fv_staged_shape",
+           "lb3_set_fv_staged_shape", "lb3_get_fv_staged_shape", "lb3_autotune_fv",
            "lb_autotune_fv", "lb_server_create", "lb_server_submit", "lb_server_pump",
            "lb_server_results", "lb_server_clock", "lb_server_destroy"]
 LB_FV_AUTO, LB_FV_TILE, LB_FV_MARCH, LB_FV_PAIR, LB_FV_PTILE, LB_FV_SPLIT = 0, 1, 2, 3, 4, 5
@@ -163,6 +163,8 @@ def load(build: bool = True) -> C.CDLL:
     L.lb3_get_fv_schedule.argtypes = [G, C.POINTER(C.c_int)]
     L.lb3_debug_drop_copies.argtypes = [G, C.c_int]
     L.lb3_set_fv_staged_shape.argtypes = [G, C.c_int, C.c_int, C.c_int]
+    L.lb3_get_fv_staged_shape.argtypes = [G] + [C.POINTER(C.c_int)] * 3
+    L.lb3_autotune_fv.argtypes = [G, C.c_int]
     L.lb3_destroy.argtypes = [G]
     L.lb_sync.argtypes = [G]
     L.lb_destroy.argtypes = [G]
@@ -570,6 +572,19 @@ class Grid3:
         """Rows per tile, z planes per CTA and planes in flight of the staged
         flux passes (0: default)."""
         _check(load().lb3_set_fv_staged_shape(self._h, int(rows), int(planes), int(ahead)))
+        return self
+
+    @property
+    def staged_shape(self):
+        """(rows per tile, planes per CTA, planes ahead) of the staged passes."""
+        v = [C.c_int() for _ in range(3)]
+        _check(load().lb3_get_fv_staged_shape(self._h, *[C.byref(x) for x in v]))
+        return tuple(x.value for x in v)
+
+    def autotune_fv(self, steps=3):
+        """Time the flux schedules on the live state, keep the fastest (the
+        state is restored)."""
+        _check(load().lb3_autotune_fv(self._h, int(steps)))
         return self
 
     @property

@@ -370,6 +370,13 @@ bool adv3_staged_shape_ok(const int* n, Prec p, int ty, int kc, int ahead) {
     return staged_shape(n[0], n[2], rs, ty, kc, ahead).bytes <= kMaxSmem;
 }
 
+void adv3_staged_resolve(const int* n, Prec p, int* ty, int* kc, int* ahead) {
+    const Shape sh = staged_shape(n[0], n[2], p == Prec::F64 ? 8 : 4, *ty, *kc, *ahead);
+    *ty = sh.ty;
+    *kc = sh.kc;
+    *ahead = sh.ahead;
+}
+
 bool adv3_staged_ok(const int* n, const int* bc, Prec p) {
     const int nx = n[0];
     const size_t rs = p == Prec::F64 ? 8 : 4;

@@ -95,6 +95,8 @@ cudaError_t launch3_fv(Prec p, bool th, bool staged, const void* args, cudaStrea
 bool adv3_staged_ok(const int* n, const int* bc, Prec p);
 // whether a requested (rows per tile, planes per CTA, planes ahead) fits the grid (0: default)
 bool adv3_staged_shape_ok(const int* n, Prec p, int ty, int kc, int ahead);
+// the shape a launch uses for a request (0 entries: the defaults)
+void adv3_staged_resolve(const int* n, Prec p, int* ty, int* kc, int* ahead);
 cudaError_t launch3_adv_staged(Prec p, bool corr, int np, const void* args, cudaStream_t s);
 cudaError_t launch3_st(Prec p, bool th, const void* args, cudaStream_t s);
 // fields [5][N] (rho, ux, uy, uz, T) on the device -> storage (equilibrium in tilded variables)

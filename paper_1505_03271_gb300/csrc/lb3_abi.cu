@@ -333,22 +333,105 @@ lb_status lb3_init(lb3_grid* G, const lb3_params* p, const lb3_init_desc* in) {
     return LB_OK;
 }
 
+// one FV step on the grid's stream with its current schedule; flips cur
+static cudaError_t fv3_step(lb3_grid* G) {
+    const bool staged = staged3(G);
+    cudaError_t e;
+    if (G->prec == Prec::F64) {
+        Args3<double> A = args3<double>(G, false);
+        e = launch3_fv(G->prec, G->d.thermal != 0, staged, &A, G->stream);
+    } else {
+        Args3<float> A = args3<float>(G, false);
+        e = launch3_fv(G->prec, G->d.thermal != 0, staged, &A, G->stream);
+    }
+    G->cur ^= 1;
+    return e;
+}
+
 lb_status lb3_step_fv(lb3_grid* G, int nsteps) {
     lb_status s = ready3(G);
     if (s != LB_OK) return s;
     if (nsteps < 0) return fail3(LB_ERR_ARG, "nsteps must be >= 0");
     Dev3 dg(G->device);
-    const bool staged = staged3(G);
-    for (int k = 0; k < nsteps; ++k) {
-        if (G->prec == Prec::F64) {
-            Args3<double> A = args3<double>(G, false);
-            CK3(launch3_fv(G->prec, G->d.thermal != 0, staged, &A, G->stream));
-        } else {
-            Args3<float> A = args3<float>(G, false);
-            CK3(launch3_fv(G->prec, G->d.thermal != 0, staged, &A, G->stream));
-        }
-        G->cur ^= 1;
+    for (int k = 0; k < nsteps; ++k) CK3(fv3_step(G));
+    return LB_OK;
+}
+
+lb_status lb3_autotune_fv(lb3_grid* G, int steps) {
+    lb_status s = ready3(G);
+    if (s != LB_OK) return s;
+    if (steps < 1) return fail3(LB_ERR_ARG, "steps must be >= 1");
+    Dev3 dg(G->device);
+    const size_t bytes = (size_t)Q3 * G->N * rsize(G->prec);
+    void *sf = nullptr, *sg = nullptr;
+    CK3(cudaMalloc(&sf, bytes));
+    if (G->d.thermal && cudaMalloc(&sg, bytes) != cudaSuccess) {
+        cudaFree(sf);
+        return fail3(LB_ERR_OOM, "autotune: no memory for the state copy");
     }
+    const int cur0 = G->cur, sched0 = G->fv_sched, shape0[3] = {G->sshape[0], G->sshape[1], G->sshape[2]};
+    cudaMemcpyAsync(sf, G->f[cur0], bytes, cudaMemcpyDeviceToDevice, G->stream);
+    if (sg) cudaMemcpyAsync(sg, G->g[cur0], bytes, cudaMemcpyDeviceToDevice, G->stream);
+    struct Cand {
+        int sched, rows, planes, ahead;
+    };
+    std::vector<Cand> cands = {{LB3_FV_PLAIN, 0, 0, 0}};
+    if (staged_ok3(G)) {
+        int ty = 0, kc = 0, ah = 0;
+        adv3_staged_resolve(G->n, G->prec, &ty, &kc, &ah);
+        for (int rows : {ty, ty / 2})
+            for (int planes : {16, 32})
+                for (int ahead : {2, 3})
+                    if (rows >= 1 && adv3_staged_shape_ok(G->n, G->prec, rows, planes, ahead))
+                        cands.push_back({LB3_FV_STAGED, rows, planes, ahead});
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    Cand pick = cands[0];
+    lb_status st = LB_OK;
+    for (const Cand& c : cands) {
+        G->fv_sched = c.sched;
+        G->sshape[0] = c.rows;
+        G->sshape[1] = c.planes;
+        G->sshape[2] = c.ahead;
+        G->cur = cur0;
+        cudaError_t e = fv3_step(G);  // warm-up, then the timed steps
+        cudaEventRecord(e0, G->stream);
+        for (int k = 0; k < steps && e == cudaSuccess; ++k) e = fv3_step(G);
+        cudaEventRecord(e1, G->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e != cudaSuccess) {
+            st = fail3(LB_ERR_CUDA, cudaGetErrorString(e));
+            break;
+        }
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) {
+            best = ms;
+            pick = c;
+        }
+    }
+    // restore the state into the buffer it started in
+    G->cur = cur0;
+    cudaMemcpyAsync(G->f[cur0], sf, bytes, cudaMemcpyDeviceToDevice, G->stream);
+    if (sg) cudaMemcpyAsync(G->g[cur0], sg, bytes, cudaMemcpyDeviceToDevice, G->stream);
+    cudaStreamSynchronize(G->stream);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(sf);
+    if (sg) cudaFree(sg);
+    if (st == LB_OK) st = wait_status3(G);  // a timed step whose wait ran out
+    if (st != LB_OK) {
+        G->fv_sched = sched0;
+        for (int q = 0; q < 3; ++q) G->sshape[q] = shape0[q];
+        return st;
+    }
+    G->fv_sched = pick.sched;
+    G->sshape[0] = pick.rows;
+    G->sshape[1] = pick.planes;
+    G->sshape[2] = pick.ahead;
     return LB_OK;
 }
 
@@ -533,6 +616,16 @@ lb_status lb3_set_fv_staged_shape(lb3_grid* G, int rows, int planes, int ahead) 
 lb_status lb3_get_fv_schedule(lb3_grid* G, int* resolved) {
     if (!G || !resolved) return fail3(LB_ERR_ARG, "NULL argument");
     *resolved = staged3(G) ? LB3_FV_STAGED : LB3_FV_PLAIN;
+    return LB_OK;
+}
+
+lb_status lb3_get_fv_staged_shape(lb3_grid* G, int* rows, int* planes, int* ahead) {
+    if (!G || !rows || !planes || !ahead) return fail3(LB_ERR_ARG, "NULL argument");
+    int r = G->sshape[0], p = G->sshape[1], a = G->sshape[2];
+    adv3_staged_resolve(G->n, G->prec, &r, &p, &a);
+    *rows = r;
+    *planes = p;
+    *ahead = a;
     return LB_OK;
 }
 

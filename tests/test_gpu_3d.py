@@ -303,3 +303,32 @@ def test_fv3_staged_shapes(lbgpu):
         with pytest.raises(lb.LBError) as e:
             g.set_staged_shape(*bad)
         assert e.value.status == lb.LB_ERR_ARG
+
+
+def test_fv3_autotune(lbgpu):
+    """The 3-D autotuner restores the state bit for bit and keeps one of its
+    candidates: stepping afterwards equals stepping a grid set to the picked
+    schedule and shape by hand."""
+    lb = lbgpu
+    kw = dict(tau=0.2, tau_g=0.2, dt=0.2, beta=1e-2, grav=1.0, T0=1.0, T_bot=1.5, T_top=0.5)
+    geo = dict(lz=20.0, sz=lb.LB_AXIS_TANH, stretch_z=1.5, bcz=lb.LB_BC_WALLS, thermal=True)
+
+    def grid():
+        return lb.Grid3(32, 16, 20, **geo).init(**kw, kind=lb.LB_INIT_RB, amp=1e-2, seed=11)
+
+    g = grid()
+    f0, t0 = g.get_pops()
+    g.autotune_fv(2)
+    f1, t1 = g.get_pops()
+    assert np.array_equal(f0, f1) and np.array_equal(t0, t1)
+    sched, shape = g.fv_schedule, g.staged_shape
+    assert sched in (lb.LB3_FV_PLAIN, lb.LB3_FV_STAGED)
+    g.step_fv(3)
+    h = grid().set_fv_schedule(sched)
+    if sched == lb.LB3_FV_STAGED:
+        h.set_staged_shape(*shape)
+    h.step_fv(3)
+    for a, b in zip(g.get_pops(), h.get_pops()):
+        assert np.array_equal(a, b)
+    with pytest.raises(lb.LBError):
+        g.autotune_fv(0)
