@@ -276,7 +276,8 @@ def serving_measure(lb, torch, count=120, rate=25.0):
     """Scaled config-5 stream through the batching server and one at a time."""
     from paper_1505_03271_gb300 import serving
     reqs = serving.make_requests(count, rate)
-    srv = serving.run_server(lb, reqs, policy=lb.LB_SERVE_SHORTEST)
+    srv = serving.run_server(lb, reqs, policy=lb.LB_SERVE_ARRIVAL)
+    shortest = serving.run_server(lb, reqs, policy=lb.LB_SERVE_SHORTEST)
     share = serving.run_server(lb, reqs, policy=lb.LB_SERVE_SHARE)
     seq = serving.run_sequential(lb, torch, reqs)
     # the same request must give the same Nusselt numbers both ways
@@ -286,7 +287,9 @@ def serving_measure(lb, torch, count=120, rate=25.0):
     return {"workload": "RB FV requests, N in {64..1024}^2 tanh plates, Ra log-uniform 1e4-1e8, Pr=1, "
                         "steps uniform 50-1000 (the 1000-20000 of the full stream divided by 20), FP16 deviation storage, "
                         "Poisson arrivals %.0f/s, %d requests" % (rate, count),
-            "server": {k: srv[k] for k in keep}, "server_equal_share": {k: share[k] for k in keep},
+            "policy": "server: arrival order (LB_SERVE_ARRIVAL); also shortest first and equal share",
+            "server": {k: srv[k] for k in keep}, "server_shortest_first": {k: shortest[k] for k in keep},
+            "server_equal_share": {k: share[k] for k in keep},
             "sequential": {k: seq[k] for k in keep},
             "max_abs_nu_vol_diff_server_vs_sequential": max(diffs) if diffs else None}
 

@@ -297,8 +297,11 @@ typedef struct {
  *   LB_SERVE_SHARE:    all of them (equal steps for everyone);
  *   LB_SERVE_SHORTEST: least remaining work (cells x steps) first, as many as
  *                      fit about two waves of CTAs (at least one); the others
- *                      keep their memory and wait. */
-typedef enum { LB_SERVE_SHARE = 0, LB_SERVE_SHORTEST = 1 } lb_serve_policy;
+ *                      keep their memory and wait;
+ *   LB_SERVE_ARRIVAL:  the earliest submitted first, as many as fit about two
+ *                      waves of CTAs (at least one): first-come first-served
+ *                      for the large requests, batched for the small ones. */
+typedef enum { LB_SERVE_SHARE = 0, LB_SERVE_SHORTEST = 1, LB_SERVE_ARRIVAL = 2 } lb_serve_policy;
 
 /* store/thermal: the one storage type and model all requests use.
  * hbm_budget: bytes of device memory the requests may hold at once.

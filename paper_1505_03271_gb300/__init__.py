@@ -100,7 +100,7 @@ SYMBOLS = ["lb_create_grid", "lb_init", "lb_step_fv", "lb_step_st", "lb_moments"
            "lb_autotune_fv", "lb_server_create", "lb_server_submit", "lb_server_pump",
            "lb_server_results", "lb_server_clock", "lb_server_destroy"]
 LB_FV_AUTO, LB_FV_TILE, LB_FV_MARCH, LB_FV_PAIR, LB_FV_PTILE, LB_FV_SPLIT = 0, 1, 2, 3, 4, 5
-LB_SERVE_SHARE, LB_SERVE_SHORTEST = 0, 1
+LB_SERVE_SHARE, LB_SERVE_SHORTEST, LB_SERVE_ARRIVAL = 0, 1, 2
 LB_FV_HEUN, LB_FV_SEMI, LB_FV_EULER = 0, 1, 2
 LB3_FV_AUTO, LB3_FV_PLAIN, LB3_FV_STAGED = 0, 1, 2
 
@@ -425,7 +425,7 @@ class Server:
             store = STORE_NAMES[store]
         self.store, self.thermal = int(store), bool(thermal)
         h = C.c_void_p()
-        policy = LB_SERVE_SHORTEST if policy is None else int(policy)
+        policy = LB_SERVE_ARRIVAL if policy is None else int(policy)
         _check(load().lb_server_create(self.store, int(self.thermal), int(hbm_budget),
                                        int(steps_per_launch), policy, stream, C.byref(h)))
         self._h = h

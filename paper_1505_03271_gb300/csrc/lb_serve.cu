@@ -202,7 +202,8 @@ extern "C" {
 lb_status lb_server_create(int store, int thermal, unsigned long long hbm_budget, int steps_per_launch,
                            int policy, void* cuda_stream, lb_server** out) {
     if (!out) return fail(LB_ERR_ARG, "NULL output");
-    if (policy != LB_SERVE_SHARE && policy != LB_SERVE_SHORTEST) return fail(LB_ERR_ARG, "unknown policy");
+    if (policy != LB_SERVE_SHARE && policy != LB_SERVE_SHORTEST && policy != LB_SERVE_ARRIVAL)
+        return fail(LB_ERR_ARG, "unknown policy");
     if (store < LB_STORE_F64 || store > LB_STORE_BF16DEV) return fail(LB_ERR_ARG, "bad store");
     if (steps_per_launch < 1) return fail(LB_ERR_ARG, "steps_per_launch must be >= 1");
     lb_server* S = new lb_server();
@@ -308,13 +309,15 @@ lb_status lb_server_pump(lb_server* S, int* n_active, int* n_pending) {
         std::vector<int> order(S->active.size());
         for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
         std::vector<char> run(S->active.size(), 1);
-        if (S->policy == LB_SERVE_SHORTEST) {
-            // least remaining work first, within about two waves of CTAs
-            std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-                const Active &p = S->active[x], &q = S->active[y];
-                return (double)p.req.grid.nx * p.req.grid.ny * p.remaining <
-                       (double)q.req.grid.nx * q.req.grid.ny * q.remaining;
-            });
+        if (S->policy != LB_SERVE_SHARE) {
+            // least remaining work first (SHORTEST) or the active list's
+            // arrival order (ARRIVAL), within about two waves of CTAs
+            if (S->policy == LB_SERVE_SHORTEST)
+                std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+                    const Active &p = S->active[x], &q = S->active[y];
+                    return (double)p.req.grid.nx * p.req.grid.ny * p.remaining <
+                           (double)q.req.grid.nx * q.req.grid.ny * q.remaining;
+                });
             const int target = 2 * S->sms * (S->thermal ? 1 : 2);
             int sum = 0;
             for (size_t j = 0; j < order.size(); ++j) {

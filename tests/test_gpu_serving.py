@@ -49,7 +49,7 @@ def _drain(server):
             return out
 
 
-@pytest.mark.parametrize("policy", [0, 1], ids=["share", "shortest"])
+@pytest.mark.parametrize("policy", [0, 1, 2], ids=["share", "shortest", "arrival"])
 @pytest.mark.parametrize("store", ["f32", "f16dev"])
 def test_alone_equals_mix(lbgpu, store, policy):
     lb = lbgpu
