@@ -150,7 +150,8 @@ def schedule_name(lb, g, scheme):
     if k == lb.LB_FV_SPLIT:
         return "fv split (f32x2) %s: collision+predictor, corrector" % {0: "32x16", 16: "16x16"}[c]
     if k == lb.LB_FV_PTILE:
-        return "fv pair-tile (f32x2) %s (halo 4)" % {0: "32x16", 16: "16x16", 512: "32x16, 512 threads"}[c]
+        return "fv pair-tile (f32x2) %s (halo 4)" % {0: "32x16", 14: "32x14", 16: "16x16", 512: "32x16, 512 threads",
+                                                      526: "32x14, 512 threads"}[c]
     return ("fv pair-march (f32x2)" if k == lb.LB_FV_PAIR else "fv march") + ", %d rows per CTA" % c
 
 

@@ -150,9 +150,10 @@ lb_status lb_step_st(lb_grid* grid, int nsteps);
  *                grids only (LB_ERR_ARG otherwise);
  *   LB_FV_PTILE: the tiles with two columns per thread-cell and packed FP32
  *                pair arithmetic (same restrictions); chunk 0 = 32 x 16,
- *                16 = 16 x 16, 512 = 32 x 16 with 512 threads per CTA
- *                (one pass per stage; the corrector splits each cell's
- *                populations over two threads);
+ *                14 = 32 x 14, 16 = 16 x 16, 512 = 32 x 16 with 512 threads
+ *                per CTA, 526 = 32 x 14 with 512 threads (one pass per
+ *                stage; the corrector splits each cell's populations over
+ *                two threads);
  *   LB_FV_SPLIT: the paired step in two launches: collision on tile + 2 and
  *                the predictor on the tile, then the corrector; h* and
  *                f~ + Coll - dt/2 A[h^n] pass through two library-owned FP32

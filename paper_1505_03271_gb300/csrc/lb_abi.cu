@@ -472,8 +472,9 @@ lb_status lb_set_fv_schedule(lb_grid* G, int kernel, int chunk) {
     if (chunk < 0) return fail(LB_ERR_ARG, "chunk must be >= 0");
     if (kernel == LB_FV_TILE && chunk != 0 && chunk != 8 && chunk != 16)
         return fail(LB_ERR_ARG, "tile shape must be 0 (32 x 16), 16 (16 x 16) or 8 (16 x 8)");
-    if (kernel == LB_FV_PTILE && chunk != 0 && chunk != 16 && chunk != 512)
-        return fail(LB_ERR_ARG, "paired tile shape must be 0 (32 x 16), 16 (16 x 16) or 512 (32 x 16, 512 threads)");
+    if (kernel == LB_FV_PTILE && chunk != 0 && chunk != 14 && chunk != 16 && chunk != 512 && chunk != 526)
+        return fail(LB_ERR_ARG, "paired tile shape must be 0 (32 x 16), 14 (32 x 14), 16 (16 x 16), 512 (32 x 16, "
+                                "512 threads) or 526 (32 x 14, 512 threads)");
     if (kernel == LB_FV_SPLIT && chunk != 0 && chunk != 16)
         return fail(LB_ERR_ARG, "split tile shape must be 0 (32 x 16) or 16 (16 x 16)");
     if ((kernel == LB_FV_PAIR || kernel == LB_FV_PTILE || kernel == LB_FV_SPLIT) && !pair_ok(G))
@@ -542,6 +543,8 @@ lb_status lb_autotune_fv(lb_grid* G, int steps) {
         cands.push_back({LB_FV_PTILE, 0});
         cands.push_back({LB_FV_PTILE, 16});
         cands.push_back({LB_FV_PTILE, 512});
+        cands.push_back({LB_FV_PTILE, 14});
+        cands.push_back({LB_FV_PTILE, 526});
         if (ensure_split_buffers(G) == cudaSuccess) {
             cands.push_back({LB_FV_SPLIT, 0});
             cands.push_back({LB_FV_SPLIT, 16});

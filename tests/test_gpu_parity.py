@@ -173,7 +173,7 @@ def test_fv_step_f64(lbgpu, oracle, case, sched):
         assert np.abs(ggg - ggr).max() < 1e-13
 
 
-@pytest.mark.parametrize("sched", [(1, 0), (2, 16), (3, 8), (3, 16), (3, 0), (4, 0), (4, 16), (4, 512), (5, 0), (5, 16)],
+@pytest.mark.parametrize("sched", [(1, 0), (2, 16), (3, 8), (3, 16), (3, 0), (4, 0), (4, 14), (4, 16), (4, 512), (4, 526), (5, 0), (5, 16)],
                          ids=lambda s: f"k{s[0]}c{s[1]}")
 @pytest.mark.parametrize("case", [c for c in FV_CASES if c.get("bcx", 0) == 0],
                          ids=lambda c: "-".join(f"{k}{v}" for k, v in c.items()))
