@@ -57,6 +57,18 @@ struct Cell3 {
         uy = jy * ir + A.hf * A.ay;
         uz = jz * ir + A.hf * az;
     }
+    // the same from the sums sum d, sum c d (3) and sum e
+    __device__ __forceinline__ void from_sums(R r, R jx, R jy, R jz, R td, const Args3<R>& A) {
+        Td = TH ? td : R(0);
+        rp = r;
+        rho = R(1) + r;
+        T = A.T0 + Td;
+        az = A.az + (TH ? A.bg * Td : R(0));
+        const R ir = R(1) / rho;
+        ux = jx * ir + A.hf * A.ax;
+        uy = jy * ir + A.hf * A.ay;
+        uz = jz * ir + A.hf * az;
+    }
     // f_eq - w, Guo force F (Eq. (F2)) and g_eq - w T0
     __device__ __forceinline__ void eq(int a, const Args3<R>& A, R& feqd, R& F, R& geqd) const {
         const R w = w3<R>(a);
@@ -325,27 +337,37 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 2 : 4) k3_adv(const Args
 }
 
 // ---- FV: moments of f~* (parked in the h* buffers) and h* ----
+// Two CTAs per SM for FP32 (at most 128 registers): the compiler keeps the
+// 38 loaded values live between the moment sums and the h* stores.
 template <typename R, bool TH>
-__global__ void __launch_bounds__(256) k3_star(const Args3<R> A) {
+__global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : 2) k3_star(const Args3<R> A) {
     int i, j, k;
     if (!cell_index(A.n, i, j, k)) return;
     const long long cp = padded3(A.n, i, j, k), NP = A.NP;
-    // every f~* (and g~*) is read once into registers: the h* stores below
-    // overwrite the same locations
-    R d[Q3], e[Q3];
+    // moments of f~* (and g~*) summed as they are read; the h* pass then
+    // reads each value again
+    R r = 0, jx = 0, jy = 0, jz = 0, td = 0;
 #pragma unroll
     for (int a = 0; a < Q3; ++a) {
-        d[a] = A.HS[a * NP + cp];
-        e[a] = TH ? A.HGS[a * NP + cp] : R(0);
+        const R fs = A.HS[a * NP + cp];
+        r += fs;
+        jx += R(c3x(a)) * fs;
+        jy += R(c3y(a)) * fs;
+        jz += R(c3z(a)) * fs;
+        if constexpr (TH) td += A.HGS[a * NP + cp];
     }
     Cell3<R, TH> m;
-    m.moments(d, e, A);
+    m.from_sums(r, jx, jy, jz, td, A);
 #pragma unroll
     for (int a = 0; a < Q3; ++a) {
         R feqd, F, geqd;
         m.eq(a, A, feqd, F, geqd);
-        A.HS[a * NP + cp] = d[a] + A.omh * (feqd - d[a]) + A.hf * F;
-        if constexpr (TH) A.HGS[a * NP + cp] = e[a] + A.omgh * (geqd - e[a]);
+        const R fs = A.HS[a * NP + cp];
+        A.HS[a * NP + cp] = fs + A.omh * (feqd - fs) + A.hf * F;
+        if constexpr (TH) {
+            const R es = A.HGS[a * NP + cp];
+            A.HGS[a * NP + cp] = es + A.omgh * (geqd - es);
+        }
     }
     zghosts<R, TH>(A.HS, A.HGS, i, j, k, A);
 }

@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(256) k_st(const StepArgs<R> A) {
 // are stored as pairs and the others per cell (their neighbour is shifted by
 // one column).
 template <typename S, bool TH>
-__global__ void __launch_bounds__(256) k_st_pair(const StepArgs<float> A) {
+__global__ void __launch_bounds__(256, TH ? 2 : 4) k_st_pair(const StepArgs<float> A) {
     using namespace pairmath;
     const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
     const int y = blockIdx.y;
