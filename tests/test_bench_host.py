@@ -1,0 +1,75 @@
+"""Host logic of bench.py (no GPU): the reference arm's JSON line, the
+comment-insensitive source hashes that decide whether a committed ncu
+traffic figure still describes a kernel, the traffic table itself, and the
+roofline and replica arithmetic."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_reference_arm_line():
+    """`bench.py --impl reference` times the oracle on the headline workload
+    and prints one JSON line in the contract's shape."""
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "2", "--warmup", "3"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr
+    line = json.loads(r.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["unit"] == "MLUPS" and line["value"] > 0 and line["higher_is_better"] is True
+    assert line["steps"] == 2 and line["warmup"] == 3 and line["n_gpus"] == 1
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"] == {"value": line["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
+    assert "channel 256x512" in line["config"]["workload"]
+
+
+def test_source_hash_ignores_comments(tmp_path, monkeypatch):
+    src = tmp_path / "paper_1505_03271_gb300" / "csrc"
+    src.mkdir(parents=True)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (src / "k.cu").write_text("int f(int a) { return a + 1; }  // one\n")
+    h0 = bench.source_hash(["k.cu"])
+    (src / "k.cu").write_text("/* a block\n comment */\nint f(int a) {\n    return a + 1;   // two\n}\n")
+    assert bench.source_hash(["k.cu"]) == h0
+    (src / "k.cu").write_text("int f(int a) { return a + 2; }\n")
+    assert bench.source_hash(["k.cu"]) != h0
+
+
+def test_traffic_table_well_formed():
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+        table = json.load(fh)
+    entries = {k: v for k, v in table.items() if not k.startswith("_")}
+    assert entries
+    for key, e in entries.items():
+        schedule, case = key.split("|")
+        assert schedule and case
+        assert isinstance(e["bytes"], int) and e["bytes"] > 0
+        assert len(e["sources"]) == 16 and e["files"]
+        for f in e["files"]:
+            assert os.path.exists(os.path.join(ROOT, "paper_1505_03271_gb300", "csrc", f)), f
+        assert os.path.exists(os.path.join(ROOT, e["profile"])), e["profile"]
+        # the lookup returns the bytes exactly when the kernel's code is unchanged
+        expect = e["bytes"] if bench.source_hash(e["files"]) == e["sources"] else None
+        assert bench.measured_traffic(schedule, case) == expect
+    assert bench.measured_traffic("no such schedule", "channel") is None
+
+
+def test_roofline_arithmetic():
+    r = bench.roofline(72 * 131072, 0.0144, 6680.2, "measured", traffic=4805120)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["traffic"] == 4805120
+    assert r["achieved"] == pytest.approx(72 * 131072 / 14.4e-6 / 1e9, abs=0.05)
+    assert r["frac"] == pytest.approx(r["achieved"] / 6680.2, abs=1e-4)
+
+
+def test_single_rank_aggregate():
+    t, mlups = bench.aggregate(0.5, 131072, 1000, 1)
+    assert t == 0.5 and mlups == pytest.approx(131072 * 1000 / 0.5 / 1e6)
