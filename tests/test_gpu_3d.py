@@ -16,6 +16,9 @@ CASES = [
     dict(nx=5, ny=12, nz=8, sy=1, stretch_y=1.5, bcy=1, sz=3, bcz=1),
     dict(nx=1, ny=10, nz=8, lx=1.0, sz=1, stretch_z=2.0, bcz=1, thermal=True),
     dict(nx=33, ny=9, nz=4, bcx=1),
+    # the smallest z extents: every plane is a ghost source (walls need two cells)
+    dict(nx=5, ny=4, nz=2, bcx=1, bcz=1),
+    dict(nx=7, ny=3, nz=1),
 ]
 
 
@@ -183,6 +186,11 @@ STAGED_CASES = [
     dict(nx=32, ny=10, nz=12, sz=1, stretch_z=1.5, bcz=1, thermal=True),
     dict(nx=4, ny=3, nz=5, sy=1, stretch_y=1.2),
     dict(nx=64, ny=20, nz=17, sz=1, stretch_z=2.0, bcz=1),
+    # a single z plane (periodic), a single y row, and two and three plates-bounded planes
+    dict(nx=8, ny=6, nz=1),
+    dict(nx=8, ny=1, nz=6, sz=1, stretch_z=1.5, bcz=1),
+    dict(nx=4, ny=5, nz=2, bcz=1, thermal=True),
+    dict(nx=16, ny=3, nz=3, bcz=1, thermal=True),
 ]
 
 
