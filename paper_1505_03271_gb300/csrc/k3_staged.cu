@@ -5,15 +5,19 @@
 // The plain passes of k3.cu read every stencil node through L1/L2 and keep
 // about three cache lines in flight per warp, which holds them near 1.5-1.8
 // TB/s.  Here a CTA owns one population, a tile of ty whole x rows and a
-// chunk of z planes.  Warp 0 keeps `ahead` planes (3 by default) of copies
-// in flight beyond the planes the arithmetic uses:
+// chunk of z planes.  Eight warps compute; one thread of a ninth warp keeps
+// `ahead` planes (3 by default) of copies in flight beyond the planes the
+// arithmetic uses:
 //   - the rows of h (h* in the corrector) of the next plane, with two halo
 //     rows on each side in y when c_y != 0.  The x rows are whole, so the
 //     periodic x wrap is an index wrap in shared memory;
 //   - the rows of f~ + Coll of the plane that the same step completes.
-// Each row is one cp.async.bulk that completes on the plane's mbarrier.
-// Every x, y and z stencil node is then a shared-memory load, and HBM sees
-// each operand once per pass.
+// Consecutive rows are contiguous in memory, so each run of them is one
+// cp.async.bulk (two or three per plane) completing on the plane's
+// mbarrier; a second mbarrier per ring slot tells the copy thread when the
+// computing warps are done with it.  Every x, y and z stencil node is then a
+// shared-memory load, and HBM sees each operand once per pass.  FP32 runs
+// two adjacent x cells per thread in f32x2 arithmetic.
 //
 // Grids served (adv3_staged_ok): x and y periodic, and nx a power of two
 // <= 256 whose rows are a multiple of 16 bytes (the bulk-copy granule).  z
@@ -23,6 +27,8 @@
 // Every wait on a copy is bounded (Args3::wait_ns).  A CTA whose wait runs
 // out sets *Args3::werr, waits (bounded again) for the copies it has issued,
 // and returns; the host reports LB_ERR_TIMEOUT.
+#include <type_traits>
+
 #include "lb3.cuh"
 #include "lb_async.cuh"
 #include "lb_pair.cuh"
@@ -188,8 +194,8 @@ __global__ void __launch_bounds__(kThreads + 32, sizeof(R) == 8 ? 2 : 3)
     // The computing warps' loop over the chunk's planes.  Ring positions are
     // kept incrementally: s0 = it % RS (the step the iteration releases),
     // sw = (it + Z) % RS and its phase (the step it waits for), sf = it % FS
-    // (its f~ + Coll).  body(it, hz, hc, fcp, kz, qb, pb) updates the
-    // thread's cells of plane k0 + it: hz[s] are the planes of the z nodes,
+    // (its f~ + Coll).  body(hz, hc, fcp, kz, qb, pb) updates the thread's
+    // cells of plane k0 + it: hz[s] are the planes of the z nodes,
     // hc the plane itself, fcp its f~ + Coll, kz its folded z weights, qb
     // and pb the offsets of plane k0 + it of population a in the unpadded
     // and padded fields.
@@ -228,6 +234,7 @@ __global__ void __launch_bounds__(kThreads + 32, sizeof(R) == 8 ? 2 : 3)
     if constexpr (sizeof(R) == 4) {
         // FP32: two adjacent x cells per thread (nx is even), packed f32x2
         // arithmetic on 8-byte shared loads and 8-byte stores
+        static_assert(std::is_same<S, float>::value, "the FP32 staged pass stores FP32 populations");
         using namespace pairmath;
         const int np2 = nx >> 1, i = 2 * (tid % np2), rstep = kThreads / np2, r0 = tid / np2;
         int xp[3] = {0, 0, 0};  // pairs (i-2, i-1), (i, i+1), (i+2, i+3), wrapped in x
