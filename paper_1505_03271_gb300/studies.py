@@ -299,17 +299,60 @@ def _ddz(z, f):
     return d
 
 
+def _ddz_weights(z):
+    """Rows (m - 1, m, m + 1) and weights of _ddz at every node, for arrays."""
+    n = len(z)
+    m = np.clip(np.arange(n), 1, n - 2)
+    z0, z1, z2, x = z[m - 1], z[m], z[m + 1], z
+    w = np.stack([(2 * x - z1 - z2) / ((z0 - z1) * (z0 - z2)), (2 * x - z0 - z2) / ((z1 - z0) * (z1 - z2)),
+                  (2 * x - z0 - z1) / ((z2 - z0) * (z2 - z1))], axis=1)
+    return m, w
+
+
+def _grad(f, dx, dy, mz, wz):
+    """Gradient of a field [nz, ny, nx]: central differences in the periodic
+    x and y, the stretched-grid 3-point derivative in z."""
+    gx = (np.roll(f, -1, axis=2) - np.roll(f, 1, axis=2)) / (2.0 * dx)
+    gy = (np.roll(f, -1, axis=1) - np.roll(f, 1, axis=1)) / (2.0 * dy)
+    gz = (wz[:, 0, None, None] * f[mz - 1] + wz[:, 1, None, None] * f[mz] + wz[:, 2, None, None] * f[mz + 1])
+    return gx, gy, gz
+
+
+def _turnover(series, spacing):
+    """Large-eddy turnover time: the first zero crossing of the
+    autocorrelation of a time series sampled every `spacing` (Sec. IV), by
+    linear interpolation; None if it never crosses."""
+    x = np.asarray(series, dtype=float)
+    x = x - x.mean()
+    var = float((x * x).mean())
+    if var <= 0:
+        return None
+    n = len(x)
+    c = np.array([float((x[: n - l] * x[l:]).mean()) / var for l in range(n // 2)])
+    for l in range(1, len(c)):
+        if c[l] <= 0.0:
+            return spacing * (l - 1 + c[l - 1] / (c[l - 1] - c[l]))
+    return None
+
+
 def rb3d_stats(lb, torch, scheme, tff_total=300.0, tff_avg=200.0, samples=100, store=None):
     """Table rb run with `scheme` ("fv" or "st"): tff_total free-fall times
     H / sqrt(beta g dT H), statistics over the last tff_avg of them from
-    `samples` equally spaced snapshots.  Nu(z) = (<u_z (T - T0)> - kappa
-    d<T>/dz) / (kappa dT / H); lambda_T = dT / (2 dT_m/dz at the plate)."""
+    `samples` equally spaced snapshots (Sec. IV, Figs. cfrT, cfrT2, cfrE,
+    cfrLB).
+      Nu(z) = (<u_z (T - T0)> - kappa d<T>/dz) / (kappa dT / H);
+      lambda_T = dT / (2 dT_m/dz at the plate);
+      eps_u = nu sum_ij (d_j u_i)^2, eps_T = kappa sum_j (d_j T)^2 and the
+      Bolgiano length L_B = (beta g)^(-3/2) <eps_u>^(5/4) <eps_T>^(-3/4);
+      the large-eddy turnover time from the zero crossing of the
+      autocorrelation of the total kinetic energy, and t_tot over it."""
     w = cfg.rb3d_table(scheme) if store is None else cfg.rb3d_table(scheme, store=store)
     gk = dict(w.grid)
     st = gk.pop("store")
     p = w.params
     H, dT = gk["lz"], p["T_bot"] - p["T_top"]
-    tff = H / math.sqrt(p["beta"] * p["grav"] * dT * H)
+    bg = p["beta"] * p["grav"]
+    tff = H / math.sqrt(bg * dT * H)
     dt = p["dt"]
     steps_total = int(round(tff_total * tff / dt))
     steps_avg = int(round(tff_avg * tff / dt))
@@ -318,9 +361,13 @@ def rb3d_stats(lb, torch, scheme, tff_total=300.0, tff_avg=200.0, samples=100, s
     step = g.step_fv if scheme == "fv" else g.step_st
     xi = cfg.faces(gk["nz"], H, gk.get("sz", 0), gk.get("stretch_z", 0.0))
     zc = 0.5 * (xi[1:] + xi[:-1])
+    dzc = np.diff(xi)
+    dx, dy = gk["lx"] / gk["nx"], gk["ly"] / gk["ny"]
+    mz, wz = _ddz_weights(zc)
     kappa = p["tau_g"] * cfg.CS2
-    acc = {k: np.zeros(gk["nz"]) for k in ("T", "T2", "k", "uzT")}
-    nus = []
+    nu = p["tau"] * cfg.CS2
+    acc = {k: np.zeros(gk["nz"]) for k in ("T", "T2", "k", "uzT", "eu", "eT")}
+    nus, energy = [], []
     step(steps_total - steps_avg)
     n = 0
     for _ in range(steps_avg // every):
@@ -328,8 +375,17 @@ def rb3d_stats(lb, torch, scheme, tff_total=300.0, tff_avg=200.0, samples=100, s
         rho, ux, uy, uz, T = g.moments()
         acc["T"] += T.mean(axis=(1, 2))
         acc["T2"] += (T * T).mean(axis=(1, 2))
-        acc["k"] += 0.5 * (ux * ux + uy * uy + uz * uz).mean(axis=(1, 2))
+        kz = 0.5 * (ux * ux + uy * uy + uz * uz).mean(axis=(1, 2))
+        acc["k"] += kz
+        energy.append(float((kz * dzc).sum()))
         acc["uzT"] += (uz * (T - p["T0"])).mean(axis=(1, 2))
+        eu = np.zeros_like(T)
+        for comp in (ux, uy, uz):
+            for gcomp in _grad(comp, dx, dy, mz, wz):
+                eu += gcomp * gcomp
+        acc["eu"] += nu * eu.mean(axis=(1, 2))
+        eT = sum(gcomp * gcomp for gcomp in _grad(T, dx, dy, mz, wz))
+        acc["eT"] += kappa * eT.mean(axis=(1, 2))
         nus.append(g.nusselt())
         n += 1
     g.close()
@@ -337,18 +393,25 @@ def rb3d_stats(lb, torch, scheme, tff_total=300.0, tff_avg=200.0, samples=100, s
     Trms = np.sqrt(np.maximum(acc["T2"] / n - Tm * Tm, 0.0))
     km = acc["k"] / n
     nu_z = (acc["uzT"] / n - kappa * _ddz(zc, Tm)) / (kappa * dT / H)
+    eps_u, eps_T = acc["eu"] / n, acc["eT"] / n
+    LB = bg ** -1.5 * eps_u ** 1.25 * eps_T ** -0.75
+    turn = _turnover(energy, every * dt / tff)
     nus = np.array(nus)
     nu_bot = float(nus[:, 1].mean())
     lam = H / (2.0 * nu_bot)
     lower = zc < 0.1 * H
+    mid = int(np.argmin(np.abs(zc - 0.5 * H)))
     return {"scheme": scheme, "cells": w.cells, "nz": gk["nz"], "H": H, "dt": dt, "tff": tff,
             "steps": steps_total, "samples": n, "nu_vol": float(nus[:, 0].mean()), "nu_bot": nu_bot,
             "nu_top": float(nus[:, 2].mean()), "nu_vol_std": float(nus[:, 0].std()),
             "lambda_T": lam, "cells_in_bl": int((zc < lam).sum()), "z1": float(zc[0]),
             "nu_z_mean": float(nu_z.mean()), "nu_z_wall_dev": float(np.abs(nu_z[lower] - nu_z.mean()).max()),
+            "turnover_tff": turn, "t_tot_over_turnover": (tff_total / turn) if turn else None,
+            "LB_over_H_wall": float(LB[0] / H), "LB_over_H_mid": float(LB[mid] / H),
             "zc_over_H": [round(float(v), 5) for v in zc / H], "T_m": [round(float(v), 6) for v in Tm],
             "T_rms": [round(float(v), 6) for v in Trms], "k_m": [float(f"{v:.4e}") for v in km],
-            "nu_z": [round(float(v), 4) for v in nu_z]}
+            "nu_z": [round(float(v), 4) for v in nu_z], "LB_over_H": [float(f"{v:.4e}") for v in LB / H],
+            "eps_u": [float(f"{v:.4e}") for v in eps_u], "eps_T": [float(f"{v:.4e}") for v in eps_T]}
 
 
 def rb3d(lb, torch, tff_total=300.0, tff_avg=200.0):
