@@ -414,8 +414,15 @@ def rb3d_stats(lb, torch, scheme, tff_total=300.0, tff_avg=200.0, samples=100, s
             "eps_u": [float(f"{v:.4e}") for v in eps_u], "eps_T": [float(f"{v:.4e}") for v in eps_T]}
 
 
-def rb3d(lb, torch, tff_total=300.0, tff_avg=200.0):
-    return [rb3d_stats(lb, torch, s, tff_total, tff_avg) for s in ("fv", "st")]
+def rb3d(lb, torch, tff_total=300.0, tff_avg=200.0, samples=100):
+    return [rb3d_stats(lb, torch, s, tff_total, tff_avg, samples) for s in ("fv", "st")]
+
+
+def rb3d_long(lb, torch):
+    """The same comparison over 600 free-fall times (statistics over the
+    last 500, a snapshot every 2): beyond the paper's twelve large-eddy
+    turnover times for both schemes."""
+    return rb3d(lb, torch, 600.0, 500.0, 250)
 
 
 def main(argv=None):
@@ -429,7 +436,8 @@ def main(argv=None):
     which = set(argv) or {"kol3", "poi2", "poi3"}
     load()
     for name, fn in (("kol", viscosity_error), ("poi", poiseuille_unit_dx), ("kol3", dt_max),
-                     ("poi2", poiseuille_vs_n), ("poi3", poiseuille_vs_spacing), ("rb3d", rb3d)):
+                     ("poi2", poiseuille_vs_n), ("poi3", poiseuille_vs_spacing), ("rb3d", rb3d),
+                     ("rb3d_long", rb3d_long)):
         if name in which:
             t0 = time.perf_counter()
             rows = fn(lb, torch)
