@@ -126,3 +126,23 @@ def test_served_request_matches_oracle(lbgpu, oracle):
     ref.step_fv(r["nsteps"])
     for a, b in zip((res["nu_vol"], res["nu_bot"], res["nu_top"]), ref.nusselt()):
         assert abs(a - b) <= 1e-10 * max(1.0, abs(b))
+
+
+def test_arrival_policy_is_first_come_first_served(lbgpu):
+    """LB_SERVE_ARRIVAL: when every request alone fills the GPU (a 1024^2
+    grid is far more than two waves of tiles), they run one at a time in
+    submission order; LB_SERVE_SHORTEST lets a later, smaller one overtake."""
+    lb = lbgpu
+    big = dict(nx=1024, ny=1024, sy=1, stretch_y=2.0, bcy=1, dt=0.1, amp=1e-3, **RB)
+    small = dict(nx=512, ny=512, sy=1, stretch_y=2.0, bcy=1, dt=0.1, amp=1e-3, **RB)
+    order = {}
+    for policy in (lb.LB_SERVE_ARRIVAL, lb.LB_SERVE_SHORTEST):
+        s = lb.Server(store="f16dev", thermal=True, steps_per_launch=4, policy=policy)
+        s.submit(rid=1, nsteps=12, seed=1, **big)
+        s.submit(rid=2, nsteps=12, seed=2, **big)
+        s.submit(rid=3, nsteps=12, seed=3, **small)
+        got = _drain(s)
+        assert all(got[i]["status"] == lb.LB_OK for i in (1, 2, 3))
+        order[policy] = sorted(got, key=lambda i: got[i]["t_done"])
+    assert order[lb.LB_SERVE_ARRIVAL] == [1, 2, 3]
+    assert order[lb.LB_SERVE_SHORTEST][0] == 3
