@@ -143,6 +143,8 @@ def schedule_name(lb, g, scheme):
     if scheme != "fv":
         if g.store == lb.LB_STORE_F64:
             return "st push, one thread per cell"
+        if g.store in (lb.LB_STORE_F16DEV, lb.LB_STORE_BF16DEV) and not g.thermal:
+            return "st pair (f32x2), two cells of two rows per thread"
         return "st pair (f32x2), two cells per thread"
     k, c = g.fv_schedule()
     if k == lb.LB_FV_TILE:

@@ -187,10 +187,132 @@ __global__ void __launch_bounds__(256, TH ? 2 : 4) k_st_pair(const StepArgs<floa
     }
 }
 
+// 16-bit flow grids: the kernel waits on memory latency (about half of its
+// DRAM peak at 32 warps per SM), so each thread takes two rows and issues the
+// second row's loads (kept as packed 16-bit pairs, one register each) before
+// the first row's arithmetic.  The per-row arithmetic and stores are those of
+// k_st_pair without the thermal populations.
+template <typename S>
+__device__ __forceinline__ pairmath::V2 cvt_pair(unsigned u, bool two);
+template <>
+__device__ __forceinline__ pairmath::V2 cvt_pair<__half>(unsigned u, bool two) {
+    const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&u));
+    const pairmath::V2 v{make_float2(f.x * (1.0f / kF16Scale), f.y * (1.0f / kF16Scale))};
+    return two ? v : pairmath::bc(v.v.x);
+}
+template <>
+__device__ __forceinline__ pairmath::V2 cvt_pair<__nv_bfloat16>(unsigned u, bool two) {
+    const pairmath::V2 v{__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u))};
+    return two ? v : pairmath::bc(v.v.x);
+}
+
+template <typename S>
+__device__ __forceinline__ void st_pair_row_flow(const StepArgs<float>& A, const int x, const int y, const bool two,
+                                                 const pairmath::V2* d) {
+    using namespace pairmath;
+    S* fout = static_cast<S*>(A.fout);
+    const long long c = (long long)y * A.pitch + x;
+    const float ro = A.roff[y];
+    PairCell<false> m;
+    m.build(d, d, A, ro, 0.0f);
+    if (x >= 1 && x + 2 < A.nx && y >= 1 && y + 1 < A.ny) {
+        const float rdn = A.roff[y - 1], rup = A.roff[y + 1];
+#pragma unroll
+        for (int a = 0; a < Q; ++a) {
+            const float w = wgt<float>(a);
+            const float rt = cy(a) > 0 ? rup : (cy(a) < 0 ? rdn : ro);
+            const V2 post = fma2(bc(A.om), m.feqd[a] - d[a], fma2(bc(A.cf), m.F[a], d[a])) + bc(w * (ro - rt));
+            const long long o = a * A.plane + c + (long long)cy(a) * A.pitch + cx(a);
+            if (cx(a) == 0) {
+                PairIO<S>::st(fout + o, post);
+            } else {
+                Store<S>::st(fout + o, post.v.x);
+                Store<S>::st(fout + o + 1, post.v.y);
+            }
+        }
+        return;
+    }
+#pragma unroll
+    for (int a = 0; a < Q; ++a) {
+        const V2 post = fma2(bc(A.om), m.feqd[a] - d[a], fma2(bc(A.cf), m.F[a], d[a]));
+        const float w = wgt<float>(a);
+        int ty = y + cy(a);
+        bool outy = false;
+        if (ty < 0 || ty >= A.ny) {
+            if (A.bcy == LB_BC_PERIODIC) ty = ty < 0 ? ty + A.ny : ty - A.ny;
+            else outy = true;
+        }
+        if (cx(a) == 0) {
+            long long o;
+            V2 fv;
+            if (outy) {
+                o = inv(a) * A.plane + c;
+                fv = post;
+            } else {
+                o = a * A.plane + (long long)ty * A.pitch + x;
+                fv = post + bc(w * (ro - A.roff[ty]));
+            }
+            if (two) PairIO<S>::st(fout + o, fv);
+            else Store<S>::st(fout + o, fv.v.x);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                if (i == 1 && !two) break;
+                const float pv = i ? post.v.y : post.v.x;
+                int tx = x + i + cx(a);
+                bool out = outy;
+                if (tx < 0 || tx >= A.nx) {
+                    if (A.bcx == LB_BC_PERIODIC) tx = tx < 0 ? tx + A.nx : tx - A.nx;
+                    else out = true;
+                }
+                if (out) Store<S>::st(fout + inv(a) * A.plane + c + i, pv);
+                else Store<S>::st(fout + a * A.plane + (long long)ty * A.pitch + tx, pv + w * (ro - A.roff[ty]));
+            }
+        }
+    }
+}
+
+// Three CTAs per SM (80 registers): measured faster than four with the
+// 64-register cap, which spills.
+template <typename S>
+__global__ void __launch_bounds__(256, 3) k_st_pair_rows(const StepArgs<float> A) {
+    using namespace pairmath;
+    const int x = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+    const int y = 2 * blockIdx.y;
+    if (x >= A.nx) return;
+    const bool two = x + 1 < A.nx, second = y + 1 < A.ny;
+    // a pair load at an odd last column reads one element of the row's
+    // padding (the pitch is a multiple of 32), which cvt_pair then drops
+    const unsigned* p = reinterpret_cast<const unsigned*>(static_cast<const S*>(A.fin) + (long long)y * A.pitch + x);
+    const long long pl = A.plane / 2, pr = A.pitch / 2;  // in 32-bit words
+    unsigned r0[Q], r1[Q];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) r0[a] = __ldg(p + a * pl);
+    if (second) {
+#pragma unroll
+        for (int a = 0; a < Q; ++a) r1[a] = __ldg(p + a * pl + pr);
+    }
+    V2 d[Q];
+#pragma unroll
+    for (int a = 0; a < Q; ++a) d[a] = cvt_pair<S>(r0[a], two);
+    st_pair_row_flow<S>(A, x, y, two, d);
+    if (second) {
+#pragma unroll
+        for (int a = 0; a < Q; ++a) d[a] = cvt_pair<S>(r1[a], two);
+        st_pair_row_flow<S>(A, x, y + 1, two, d);
+    }
+}
+
 template <typename R, typename S, bool TH>
 static cudaError_t run_st(const void* vargs, cudaStream_t s) {
     const StepArgs<R>& A = *static_cast<const StepArgs<R>*>(vargs);
-    if constexpr (sizeof(R) == 4) {
+    if constexpr (sizeof(R) == 4 && sizeof(S) == 2 && !TH) {
+        // 16-bit flow grids: one thread per two cells of two rows
+        const int half = (A.nx + 1) / 2;
+        int bx = half >= 256 ? 256 : ((half + 31) / 32) * 32;
+        dim3 grid((half + bx - 1) / bx, (A.ny + 1) / 2);
+        k_st_pair_rows<S><<<grid, bx, 0, s>>>(A);
+    } else if constexpr (sizeof(R) == 4) {
         // packed pairs: one thread per two cells
         const int half = (A.nx + 1) / 2;
         int bx = half >= 256 ? 256 : ((half + 31) / 32) * 32;
