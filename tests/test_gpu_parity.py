@@ -133,6 +133,34 @@ def test_st_step_f32_pairs(lbgpu, oracle, case):
         assert np.abs(ggg - ggr).max() <= 2e-6 * np.abs(gg - wts).max()
 
 
+@pytest.mark.parametrize("store,tol", [("bf16dev", 2e-2), ("f16dev", 3e-3)])
+@pytest.mark.parametrize("case", ST_CASES, ids=lambda c: "x".join(map(str, c.values())))
+def test_st_step_16bit(lbgpu, oracle, case, store, tol):
+    """The 16-bit ST paths (two cells of two rows per thread on flow grids,
+    the paired kernel on thermal ones) against the oracle started from the
+    GPU's stored state: odd widths and heights, walls on x and y.  The
+    tolerance is the storage precision relative to the deviation scale,
+    over the three steps (each result is stored in 16 bits again)."""
+    nx, ny = case["nx"], case["ny"]
+    th = case.get("thermal", False)
+    kw = dict(tau=0.3, dt=1.0, ax=2e-4, ay=-1e-4)
+    if th:
+        kw.update(tau_g=0.25, beta=1e-2, grav=1.0, T0=1.0, T_bot=1.3, T_top=0.8)
+    g, r = pair(lbgpu, oracle, store=lbgpu.STORE_NAMES[store], **case, **kw)
+    g.set_pops(inputs.random_populations(nx, ny, seed=nx + 2 * ny, amp=0.2),
+               inputs.random_populations(nx, ny, seed=9, amp=0.2) if th else None)
+    f, gg = g.get_pops()
+    r.set_pops(f, gg)
+    g.step_st(3)
+    r.step_st(3)
+    fg, ggg = g.get_pops()
+    fr, ggr = r.get_pops()
+    wts = oracle.lattice()[2][:, None, None]
+    assert np.abs(fg - fr).max() <= tol * np.abs(f - wts).max()
+    if th:
+        assert np.abs(ggg - ggr).max() <= tol * np.abs(gg - wts * kw["T0"]).max()
+
+
 FV_CASES = [
     dict(nx=70, ny=37),
     dict(nx=18, ny=24, sy=3, bcy=1),
