@@ -72,15 +72,37 @@ __device__ __forceinline__ float row_ref_flux(const YPair& Y, bool thermal) {
     }
 }
 
-// Flux divergence of ring plane p (population a) for the thread's two
-// columns; rows r-2..r+2 sit in slots sl[0..4], x neighbours are the pairs
-// of threads k-1 and k+1.
+// Rows each population's advected field keeps in the marching rings: five
+// for c_y != 0 (the y stencil spans rows r-2..r+2), three for the x-only
+// populations (their row is read two iterations after it is written, by
+// the x stencil), none for the rest population, whose field never moves.
+// Population p >= Q is the thermal population p - Q.
+__host__ __device__ constexpr int ring_depth(int p) {
+    return cy(p % Q) != 0 ? 5 : (cx(p % Q) != 0 ? 3 : 0);
+}
+// First ring row of population p: the depths of the D2Q9 order (0, 3, 5, 3,
+// 5, 5, 5, 5, 5; 36 rows) in closed form, so that every index folds to a
+// constant (a recursive sum is not folded when called with a loop index).
+__host__ __device__ constexpr int ring_off(int p) {
+    const int a = p % Q;
+    return 36 * (p / Q) + (a <= 1 ? 0 : a == 2 ? 3 : a == 3 ? 8 : a == 4 ? 11 : 16 + 5 * (a - 5));
+}
+constexpr int ring_sum(int p) { return p == 0 ? 0 : ring_sum(p - 1) + ring_depth(p - 1); }
+static_assert(ring_off(1) == ring_sum(1) && ring_off(2) == ring_sum(2) && ring_off(3) == ring_sum(3) &&
+                  ring_off(4) == ring_sum(4) && ring_off(5) == ring_sum(5) && ring_off(8) == ring_sum(8) &&
+                  ring_off(9) == ring_sum(9) && ring_off(13) == ring_sum(13) && ring_off(18) == ring_sum(18),
+              "ring offsets");
+
+// Flux divergence of population p (velocity a) for the thread's two
+// columns.  Its ring holds rows r-2..r+2 in slots sl[0..4] (depth 5) or row
+// r in slot c3 (depth 3); x neighbours are the pairs of threads k-1, k+1.
 template <int NQ, int NT, int a>
-__device__ __forceinline__ V2 advect_pair(const V2* ring, const int* sl, int p, int k, const XPair& X,
+__device__ __forceinline__ V2 advect_pair(const V2* ring, const int* sl, int c3, int p, int k, const XPair& X,
                                           const YPair& Y) {
     V2 v = bc(0.0f);
+    const V2* base = ring + ring_off(p) * NT;
     if constexpr (cx(a) != 0) {
-        const V2* row = ring + (sl[2] * NQ + p) * NT;
+        const V2* row = base + (ring_depth(p) == 5 ? sl[2] : c3) * NT;
         const float2 P0 = row[k - 1].v, P1 = row[k].v, P2 = row[k + 1].v;  // columns 2k-2 .. 2k+3
         float fw, fm, fe;
         if constexpr (cx(a) > 0) {
@@ -98,7 +120,7 @@ __device__ __forceinline__ V2 advect_pair(const V2* ring, const int* sl, int p, 
     if constexpr (cy(a) != 0) {
         V2 c[5];
 #pragma unroll
-        for (int i = 0; i < 5; ++i) c[i] = ring[(sl[i] * NQ + p) * NT + k];
+        for (int i = 0; i < 5; ++i) c[i] = base[sl[i] * NT + k];
         V2 fn, fs;
         if constexpr (cy(a) > 0) {
             fn = fma2(Y.pn[0], c[1], fma2(Y.pn[1], c[2], Y.pn[2] * c[3]));
@@ -114,21 +136,26 @@ __device__ __forceinline__ V2 advect_pair(const V2* ring, const int* sl, int p, 
 }
 
 template <bool TH, int NQ, int NT, int a>
-__device__ __forceinline__ void advect_all(const V2* ring, const int* sl, int k, const XPair& X, const YPair& Y,
-                                           const StepArgs<float>& A, int gy, V2* out) {
-    out[a] = advect_pair<NQ, NT, a>(ring, sl, a, k, X, Y) + bc(row_ref_flux<a>(Y, false));
-    if constexpr (TH) out[Q + a] = advect_pair<NQ, NT, a>(ring, sl, Q + a, k, X, Y) + bc(row_ref_flux<a>(Y, true));
-    if constexpr (a + 1 < Q) advect_all<TH, NQ, NT, a + 1>(ring, sl, k, X, Y, A, gy, out);
+__device__ __forceinline__ void advect_all(const V2* ring, const int* sl, int c3, int k, const XPair& X,
+                                           const YPair& Y, const StepArgs<float>& A, int gy, V2* out) {
+    out[a] = advect_pair<NQ, NT, a>(ring, sl, c3, a, k, X, Y) + bc(row_ref_flux<a>(Y, false));
+    if constexpr (TH)
+        out[Q + a] = advect_pair<NQ, NT, a>(ring, sl, c3, Q + a, k, X, Y) + bc(row_ref_flux<a>(Y, true));
+    if constexpr (a + 1 < Q) advect_all<TH, NQ, NT, a + 1>(ring, sl, c3, k, X, Y, A, gy, out);
 }
 
 // Ghost row of a wall on y (own columns), base-state deviations: h'_a =
-// h'_inv(a) for f and -h'_inv(a) for g.
+// h'_inv(a) for f and -h'_inv(a) for g.  Only the populations with c_y != 0
+// read ghost rows (the x stencil runs on fluid rows); a and inv(a) share
+// their ring depth.
 template <bool TH, int NQ, int NT>
 __device__ __forceinline__ void ghost_row(V2* ring, int dst, int src, int k) {
 #pragma unroll
     for (int a = 0; a < Q; ++a) {
-        ring[(dst * NQ + a) * NT + k] = ring[(src * NQ + inv(a)) * NT + k];
-        if constexpr (TH) ring[(dst * NQ + Q + a) * NT + k] = bc(0.0f) - ring[(src * NQ + Q + inv(a)) * NT + k];
+        if (ring_depth(a) != 5) continue;
+        ring[(ring_off(a) + dst) * NT + k] = ring[(ring_off(inv(a)) + src) * NT + k];
+        if constexpr (TH)
+            ring[(ring_off(Q + a) + dst) * NT + k] = bc(0.0f) - ring[(ring_off(Q + inv(a)) + src) * NT + k];
     }
 }
 
@@ -139,9 +166,10 @@ __global__ void __launch_bounds__(NT) k_fv_pair(const StepArgs<float> A, const i
     constexpr int NQ = TH ? 2 * Q : Q;
     constexpr int W = 2 * NT - 8;  // output columns per strip
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    V2* sH = reinterpret_cast<V2*>(smem_raw);  // [5][NQ][NT] h^n
-    V2* sP = sH + 5 * NQ * NT;                 // [5][NQ][NT] f~ + Coll, then - dt/2 A[h^n] (own)
-    V2* sS = sP + 5 * NQ * NT;                 // [5][NQ][NT] h*
+    constexpr int HR = ring_off(NQ);            // rows of the h and h* rings (all populations)
+    V2* sH = reinterpret_cast<V2*>(smem_raw);  // [HR][NT] h^n, ring_depth(p) rows of population p
+    V2* sP = sH + HR * NT;                     // [5][NQ][NT] f~ + Coll, then - dt/2 A[h^n] (own)
+    V2* sS = sP + 5 * NQ * NT;                 // [HR][NT] h*
     const int k = threadIdx.x;
     const int xu = blockIdx.x * W - 4 + 2 * k;  // unwrapped left column of the pair
     const int ys = blockIdx.y * CH;
@@ -201,7 +229,10 @@ __global__ void __launch_bounds__(NT) k_fv_pair(const StepArgs<float> A, const i
     prefetch(ys - 4, b0, e0);
     prefetch(ys - 3, b1, e1);
     int s0 = slot5(ys - 4);  // slot of row t
+    int t3 = ((ys - 4) % 3 + 3) % 3;  // slot of row t in the 3-row rings
     for (int t = ys - 4; t < ye + 4; ++t) {
+        // 3-row ring slots of rows t - 2 and t - 4 (rows three apart share one)
+        const int c3b = t3 == 2 ? 0 : t3 + 1, c3c = t3 == 0 ? 2 : t3 - 1;
         // m[i] = slot of row t - 4 + i (rows t - 4 .. t; m[4] = s0), since
         // rows five apart share a slot
         int m[5];
@@ -232,11 +263,15 @@ __global__ void __launch_bounds__(NT) k_fv_pair(const StepArgs<float> A, const i
 #pragma unroll
                 for (int a = 0; a < Q; ++a) {
                     const V2 neq = c.feqd[a] - d[a];
-                    sH[(s * NQ + a) * NT + k] = fma2(bc(A.omh), neq, fma2(bc(A.hf), c.F[a], d[a]));
+                    if (ring_depth(a) > 0)
+                        sH[(ring_off(a) + (ring_depth(a) == 5 ? s : t3)) * NT + k] =
+                            fma2(bc(A.omh), neq, fma2(bc(A.hf), c.F[a], d[a]));
                     sP[(s * NQ + a) * NT + k] = fma2(bc(A.om), neq, fma2(bc(A.cf), c.F[a], d[a]));
                     if constexpr (TH) {
                         const V2 neqg = c.geqd[a] - e[a];
-                        sH[(s * NQ + Q + a) * NT + k] = fma2(bc(A.omgh), neqg, e[a]);
+                        if (ring_depth(a) > 0)
+                            sH[(ring_off(Q + a) + (ring_depth(a) == 5 ? s : t3)) * NT + k] =
+                                fma2(bc(A.omgh), neqg, e[a]);
                         sP[(s * NQ + Q + a) * NT + k] = fma2(bc(A.omg), neqg, e[a]);
                     }
                 }
@@ -260,7 +295,7 @@ __global__ void __launch_bounds__(NT) k_fv_pair(const StepArgs<float> A, const i
                         load_row(A.rowtab, gy, Y);
                         const int sl[5] = {m[0], m[1], m[2], m[3], m[4]};
                         V2 adv[NQ];
-                        advect_all<TH, NQ, NT, 0>(sH, sl, k, X, Y, A, gy, adv);
+                        advect_all<TH, NQ, NT, 0>(sH, sl, c3b, k, X, Y, A, gy, adv);
                         V2 fs[Q], es[Q];
 #pragma unroll
                         for (int a = 0; a < Q; ++a) {
@@ -277,10 +312,12 @@ __global__ void __launch_bounds__(NT) k_fv_pair(const StepArgs<float> A, const i
                         c.build(fs, es, A, Y.ro, TH ? Y.to : 0.0f);
 #pragma unroll
                         for (int a = 0; a < Q; ++a) {
-                            sS[(s * NQ + a) * NT + k] =
+                            if (ring_depth(a) == 0) continue;
+                            const int sa = ring_depth(a) == 5 ? s : c3b;
+                            sS[(ring_off(a) + sa) * NT + k] =
                                 fma2(bc(A.omh), c.feqd[a] - fs[a], fma2(bc(A.hf), c.F[a], fs[a]));
                             if constexpr (TH)
-                                sS[(s * NQ + Q + a) * NT + k] = fma2(bc(A.omgh), c.geqd[a] - es[a], es[a]);
+                                sS[(ring_off(Q + a) + sa) * NT + k] = fma2(bc(A.omgh), c.geqd[a] - es[a], es[a]);
                         }
                     }
                 } else if (wally && (r == A.ny || r == A.ny + 1)) {
@@ -301,7 +338,7 @@ __global__ void __launch_bounds__(NT) k_fv_pair(const StepArgs<float> A, const i
                 load_row(A.rowtab, r, Y);
                 const int sl[5] = {m[3], m[4], m[0], m[1], m[2]};
                 V2 adv[NQ];
-                advect_all<TH, NQ, NT, 0>(sS, sl, k, X, Y, A, r, adv);
+                advect_all<TH, NQ, NT, 0>(sS, sl, c3c, k, X, Y, A, r, adv);
                 const long long row = (long long)r * A.pitch;
                 const bool both = xu + 1 < nx;
 #pragma unroll
@@ -315,6 +352,7 @@ __global__ void __launch_bounds__(NT) k_fv_pair(const StepArgs<float> A, const i
         }
         __syncthreads();
         s0 = m[0];  // slot of row t + 1 (= slot of row t - 4)
+        t3 = t3 == 2 ? 0 : t3 + 1;
     }
 }
 
@@ -867,7 +905,7 @@ template <typename S, bool TH, int NT>
 static cudaError_t run_pair(const void* vargs, int chunk, cudaStream_t s) {
     const StepArgs<float>& A = *static_cast<const StepArgs<float>*>(vargs);
     constexpr int NQ = TH ? 2 * Q : Q;
-    constexpr size_t smem = sizeof(V2) * 15 * NQ * NT;
+    constexpr size_t smem = sizeof(V2) * (2 * ring_off(NQ) + 5 * NQ) * NT;
     static_assert(smem <= 232448, "shared memory per CTA");
     static bool configured = false;
     if (!configured) {
@@ -886,17 +924,18 @@ static cudaError_t run_pair(const void* vargs, int chunk, cudaStream_t s) {
 
 cudaError_t launch_fv_pair(Prec p, bool th, const void* args, int chunk, cudaStream_t s) {
     switch (p) {
-        case Prec::F32: return th ? run_pair<float, true, 64>(args, chunk, s) : run_pair<float, false, 64>(args, chunk, s);
-        case Prec::F16: return th ? run_pair<__half, true, 64>(args, chunk, s) : run_pair<__half, false, 64>(args, chunk, s);
+        case Prec::F32: return th ? run_pair<float, true, 56>(args, chunk, s) : run_pair<float, false, 56>(args, chunk, s);
+        case Prec::F16: return th ? run_pair<__half, true, 56>(args, chunk, s) : run_pair<__half, false, 56>(args, chunk, s);
         case Prec::BF16:
-            return th ? run_pair<__nv_bfloat16, true, 64>(args, chunk, s)
-                      : run_pair<__nv_bfloat16, false, 64>(args, chunk, s);
+            return th ? run_pair<__nv_bfloat16, true, 56>(args, chunk, s)
+                      : run_pair<__nv_bfloat16, false, 56>(args, chunk, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
-int pair_width() { return 2 * 64 - 8; }
+// 56 threads per strip: with the rings above, four strips fit one SM (52 KB each)
+int pair_width() { return 2 * 56 - 8; }
 
-size_t pair_smem(bool th) { return sizeof(float2) * 15 * (th ? 18 : 9) * 64; }
+size_t pair_smem(bool th) { return sizeof(float2) * (2 * ring_off(th ? 18 : 9) + 5 * (th ? 18 : 9)) * 56; }
 
 }  // namespace lbgb
