@@ -139,6 +139,22 @@ lb_status lb_step_fv(lb_grid* grid, int nsteps);
  * the mesh to the lattice (Sec. II A).  One kernel launch per step. */
 lb_status lb_step_st(lb_grid* grid, int nsteps);
 
+/* Long runs.  A call of lb_step_fv or lb_step_st with more than 2 n steps,
+ * n the grid's graph length, takes its first step with a plain launch,
+ * captures the next n steps once into a CUDA graph (on a private stream of
+ * the grid, created on first use) and replays that graph on the grid's
+ * stream; the steps left over launch one by one.  The replays run the same
+ * kernels with the same arguments, so the state is bitwise that of n plain
+ * launches, and lb_kernel_launches counts each captured kernel once per
+ * replay.  Where capture is unavailable (the grid's stream is itself being
+ * captured) every step launches directly.  n must be even (the state is back
+ * in its buffer after each replay), 0..4096; 0 turns replays off; the
+ * default is 32.  LB_ERR_ARG otherwise.  lb_get_graph_steps returns n and
+ * the number of graph replays this grid has issued (either pointer may be
+ * NULL). */
+lb_status lb_set_graph_steps(lb_grid* grid, int n);
+lb_status lb_get_graph_steps(lb_grid* grid, int* n, unsigned long long* replays);
+
 /* Kernel schedule of lb_step_fv.  All kernels compute the same step
  * (Eq. (semi-heun)); they differ only in how the grid is cut into CTAs:
  *   LB_FV_TILE:  32 x 16 tiles with a 4-cell halo in both axes, three

@@ -93,6 +93,7 @@ SYMBOLS = ["lb_create_grid", "lb_init", "lb_step_fv", "lb_step_st", "lb_moments"
            "lb_get_window", "lb_sync", "lb_destroy", "lb_last_error", "lb_kernel_launches",
            "lb_conservation_noalloc", "lb_set_fv_schedule", "lb_get_fv_schedule",
            "lb_set_fv_scheme", "lb_get_fv_scheme", "lb_set_boundary_density",
+           "lb_set_graph_steps", "lb_get_graph_steps",
            "lb3_create_grid", "lb3_init", "lb3_step_fv", "lb3_step_st", "lb3_moments",
            "lb3_conservation", "lb3_nusselt", "lb3_set_populations", "lb3_get_populations", "lb3_sync",
            "lb3_destroy", "lb3_set_fv_schedule", "lb3_get_fv_schedule", "lb3_debug_drop_copies",
@@ -141,6 +142,8 @@ def load(build: bool = True) -> C.CDLL:
     L.lb_set_fv_scheme.argtypes = [G, C.c_int]
     L.lb_set_boundary_density.argtypes = [G] + [C.c_double] * 4
     L.lb_get_fv_scheme.argtypes = [G, C.POINTER(C.c_int)]
+    L.lb_set_graph_steps.argtypes = [G, C.c_int]
+    L.lb_get_graph_steps.argtypes = [G, C.POINTER(C.c_int), C.POINTER(C.c_ulonglong)]
     L.lb_server_create.argtypes = [C.c_int, C.c_int, C.c_ulonglong, C.c_int, C.c_int, C.c_void_p,
                                    C.POINTER(C.c_void_p)]
     L.lb_server_submit.argtypes = [C.c_void_p, C.POINTER(lb_request)]
@@ -277,6 +280,16 @@ def lb_get_fv_schedule(grid):
     return k.value, c.value
 
 
+def lb_set_graph_steps(grid, n: int) -> None:
+    _check(load().lb_set_graph_steps(grid, int(n)))
+
+
+def lb_get_graph_steps(grid):
+    n, r = C.c_int(), C.c_ulonglong()
+    _check(load().lb_get_graph_steps(grid, C.byref(n), C.byref(r)))
+    return n.value, r.value
+
+
 def lb_autotune_fv(grid, steps: int = 5) -> None:
     _check(load().lb_autotune_fv(grid, int(steps)))
 
@@ -393,6 +406,15 @@ class Grid:
 
     def fv_schedule(self):
         return lb_get_fv_schedule(self._h)
+
+    def set_graph_steps(self, n):
+        """Steps per replayed CUDA graph of long step runs (even; 0: off)."""
+        lb_set_graph_steps(self._h, n)
+        return self
+
+    def graph_steps(self):
+        """(graph length, graph replays issued so far)."""
+        return lb_get_graph_steps(self._h)
 
     def set_fv_scheme(self, scheme):
         """LB_FV_HEUN, LB_FV_SEMI or LB_FV_EULER; a change needs init() again."""

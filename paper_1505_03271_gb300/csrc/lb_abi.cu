@@ -17,6 +17,9 @@ namespace {
 
 thread_local std::string g_err;
 std::atomic<unsigned long long> g_launches{0};
+// While this thread captures a step graph, launches are tallied here: they
+// run (and count) only when the graph is replayed.
+thread_local unsigned long long* t_captured = nullptr;
 
 lb_status fail(lb_status s, const char* fmt, ...) {
     char buf[512];
@@ -39,7 +42,10 @@ lb_status fail(lb_status s, const char* fmt, ...) {
 }  // namespace
 
 namespace lbgb {
-void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+void count_launch() {
+    if (t_captured) ++*t_captured;
+    else g_launches.fetch_add(1, std::memory_order_relaxed);
+}
 // Record a failure message for lb_last_error() from another translation unit.
 lb_status set_last_error(lb_status s, const char* msg) { return fail(s, "%s", msg); }
 }  // namespace lbgb
@@ -52,6 +58,7 @@ void release(lb_grid* G) {
                     G->partial, G->red, G->xh, G->xfc};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (G->cap) cudaStreamDestroy(G->cap);
 }
 
 struct DeviceGuard {
@@ -180,6 +187,89 @@ lb_status reduce(lb_grid* G, double out[kRed]) {
     CK(launch_reduce(G->prec, G->d.thermal != 0, aux_args(G), G->partial, G->nred, G->red, G->stream));
     CK(cudaMemcpyAsync(out, G->red, sizeof(double) * kRed, cudaMemcpyDeviceToHost, G->stream));
     CK(cudaStreamSynchronize(G->stream));
+    return LB_OK;
+}
+
+// Capture n steps of `one` on the grid's private stream into an executable
+// graph.  The state flips buffers n times (n even), so it is back where it
+// started and the captured buffer pointers hold for every replay.  False,
+// with nothing launched, where capture is unavailable: the grid's stream is
+// itself being captured, or a call inside the capture is refused.
+template <typename F>
+bool capture_steps(lb_grid* G, int n, F& one, cudaGraphExec_t* exec, unsigned long long* per) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(G->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+        cudaGetLastError();
+        return false;
+    }
+    if (!G->cap && cudaStreamCreateWithFlags(&G->cap, cudaStreamNonBlocking) != cudaSuccess) {
+        G->cap = nullptr;
+        cudaGetLastError();
+        return false;
+    }
+    const cudaStream_t user = G->stream;
+    const int cur0 = G->cur;
+    unsigned long long count = 0;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(G->cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        G->stream = G->cap;
+        t_captured = &count;
+        for (int j = 0; j < n && e == cudaSuccess; ++j) {
+            e = one();
+            G->cur ^= 1;
+        }
+        t_captured = nullptr;
+        G->stream = user;
+        const cudaError_t e2 = cudaStreamEndCapture(G->cap, &graph);
+        if (e == cudaSuccess) e = e2;
+    }
+    G->cur = cur0;
+    *exec = nullptr;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *exec = nullptr;
+        return false;
+    }
+    *per = count;
+    return true;
+}
+
+// nsteps steps, each one call of `one` on G->stream followed by a buffer
+// flip.  A run of more than 2 graph_steps steps takes its first step
+// directly (first-use function attributes and buffers are set outside any
+// capture), then replays a graph of graph_steps captured steps on the
+// grid's stream and launches the remainder one by one.  The replays run the
+// same kernels with the same arguments as the direct launches; the graph
+// only takes the per-launch host and front-end cost off each step.
+template <typename F>
+lb_status run_steps(lb_grid* G, int nsteps, F one) {
+    int k = 0;
+    const int n = G->graph_steps;
+    if (n > 0 && nsteps > 2 * n) {
+        CK(one());
+        G->cur ^= 1;
+        ++k;
+        cudaGraphExec_t exec = nullptr;
+        unsigned long long per = 0;
+        if (capture_steps(G, n, one, &exec, &per)) {
+            cudaError_t e = cudaSuccess;
+            for (; k + n <= nsteps; k += n) {
+                e = cudaGraphLaunch(exec, G->stream);
+                if (e != cudaSuccess) break;
+                g_launches.fetch_add(per, std::memory_order_relaxed);
+                ++G->graph_replays;
+            }
+            cudaGraphExecDestroy(exec);  // released once its queued replays have run
+            CK(e);
+        }
+    }
+    for (; k < nsteps; ++k) {
+        CK(one());
+        G->cur ^= 1;
+    }
     return LB_OK;
 }
 
@@ -459,10 +549,21 @@ lb_status lb_step_fv(lb_grid* G, int nsteps) {
     if (s != LB_OK) return s;
     if (nsteps < 0) return fail(LB_ERR_ARG, "nsteps must be >= 0");
     DeviceGuard dg(G->device);
-    for (int k = 0; k < nsteps; ++k) {
-        CK(G->prec == Prec::F64 ? launch_fv_step<double>(G) : launch_fv_step<float>(G));
-        G->cur ^= 1;
-    }
+    return run_steps(G, nsteps,
+                     [G] { return G->prec == Prec::F64 ? launch_fv_step<double>(G) : launch_fv_step<float>(G); });
+}
+
+lb_status lb_set_graph_steps(lb_grid* G, int n) {
+    if (!G) return fail(LB_ERR_ARG, "grid is NULL");
+    if (n < 0 || n % 2 != 0 || n > 4096) return fail(LB_ERR_ARG, "graph length must be even, 0..4096 (got %d)", n);
+    G->graph_steps = n;
+    return LB_OK;
+}
+
+lb_status lb_get_graph_steps(lb_grid* G, int* n, unsigned long long* replays) {
+    if (!G) return fail(LB_ERR_ARG, "grid is NULL");
+    if (n) *n = G->graph_steps;
+    if (replays) *replays = G->graph_replays;
     return LB_OK;
 }
 
@@ -624,19 +725,14 @@ lb_status lb_step_st(lb_grid* G, int nsteps) {
     if (std::fabs(G->p.dt - 1.0) > 1e-12) return fail(LB_ERR_ARG, "ST needs dt = 1 (got %g)", G->p.dt);
     DeviceGuard dg(G->device);
     const bool th = G->d.thermal != 0;
-    for (int k = 0; k < nsteps; ++k) {
-        cudaError_t e;
+    return run_steps(G, nsteps, [G, th] {
         if (G->prec == Prec::F64) {
             StepArgs<double> A = step_args<double>(G, 1.0);
-            e = launch_st(G->prec, th, &A, G->stream);
-        } else {
-            StepArgs<float> A = step_args<float>(G, 1.0);
-            e = launch_st(G->prec, th, &A, G->stream);
+            return launch_st(G->prec, th, &A, G->stream);
         }
-        CK(e);
-        G->cur ^= 1;
-    }
-    return LB_OK;
+        StepArgs<float> A = step_args<float>(G, 1.0);
+        return launch_st(G->prec, th, &A, G->stream);
+    });
 }
 
 lb_status lb_moments(lb_grid* G, double* rho, double* ux, double* uy, double* T) {

@@ -136,6 +136,9 @@ struct lb_grid {
     int fv_kernel = LB_FV_AUTO;  // requested schedule
     int fv_chunk = 0;
     int sms = 0;                 // streaming multiprocessors of the device
+    int graph_steps = 32;        // steps per captured graph of long step runs (0: launch step by step)
+    cudaStream_t cap = nullptr;  // private stream the step graphs are captured on (created on first use)
+    unsigned long long graph_replays = 0;
 };
 
 

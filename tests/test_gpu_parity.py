@@ -633,3 +633,69 @@ def test_rb_ra1e4_nusselt_gpu(lbgpu, scheme):
     (g.step_st if scheme == "st" else g.step_fv)(steps)
     for nu in g.nusselt():
         assert abs(nu - Nu_ref) < tol, g.nusselt()
+
+
+# ----------------------------------------------------------- graph replays --
+
+GRAPH_CASES = [
+    # (label, store, thermal, step, schedule)
+    ("fv-ptile-f32", "f32", False, "fv", (4, 0)),
+    ("fv-split-f32-thermal", "f32", True, "fv", (5, 0)),   # two launches per step
+    ("fv-tile-f64-thermal", "f64", True, "fv", (1, 0)),
+    ("fv-pair-f16", "f16dev", False, "fv", (3, 0)),
+    ("st-f32-thermal", "f32", True, "st", None),
+    ("st-bf16", "bf16dev", False, "st", None),
+]
+
+
+@pytest.mark.parametrize("case", GRAPH_CASES, ids=lambda c: c[0])
+def test_graph_replays_match_plain_launches(lbgpu, case):
+    """A long run replays a captured graph of the step; the state is bitwise
+    that of launching every step directly, and each replayed kernel counts
+    as a launch."""
+    lb = lbgpu
+    _, store, th, step, sched = case
+    nx, ny, n = 96, 40, 101
+    outs, launches, replays = [], [], []
+    for graph in (0, 8):
+        kw = dict(bcy=1, thermal=th, store=store)
+        if step == "fv":
+            kw.update(sy=1, stretch_y=2.0)
+        g = lb.Grid(nx, ny, **kw)
+        params = dict(tau=0.12, dt=0.2 if step == "fv" else 1.0, ax=1e-5, kind=lb.LB_INIT_TGV, u0=0.02,
+                      amp=0.01, mode=1)
+        if th:
+            params.update(tau_g=0.1, beta=1e-3, grav=1.0, T0=1.0, T_bot=1.2, T_top=0.8)
+        g.init(**params)
+        if sched:
+            g.set_fv_schedule(*sched)
+        g.set_graph_steps(graph)
+        l0 = lb.lb_kernel_launches()
+        (g.step_fv if step == "fv" else g.step_st)(n)
+        g.sync()
+        launches.append(lb.lb_kernel_launches() - l0)
+        replays.append(g.graph_steps())
+        outs.append(g.get_pops())
+        g.close()
+    assert replays[0] == (0, 0)
+    assert replays[1] == (8, (n - 1) // 8)
+    assert launches[0] == launches[1] and launches[0] % n == 0 and launches[0] >= n
+    assert np.array_equal(outs[0][0], outs[1][0])
+    if th:
+        assert np.array_equal(outs[0][1], outs[1][1])
+
+
+def test_graph_steps_rules(lbgpu):
+    lb = lbgpu
+    g = lb.Grid(32, 16, store="f32")
+    assert g.graph_steps() == (32, 0)
+    for bad in (-2, 3, 4098):
+        with pytest.raises(lb.LBError) as e:
+            g.set_graph_steps(bad)
+        assert e.value.status == lb.LB_ERR_ARG
+    g.init(tau=0.3, dt=0.5, kind=lb.LB_INIT_TGV, u0=0.01)
+    g.step_fv(64)  # not more than 2 n steps: launched one by one
+    assert g.graph_steps() == (32, 0)
+    g.step_fv(65)
+    assert g.graph_steps() == (32, 2)
+    g.close()
