@@ -275,6 +275,29 @@ def extra_lines(lb, torch, cfg, stream, peak, peak_kind, flush):
     return out
 
 
+def roofline_sweep(lb, torch, cfg, stream, peak, flush, sizes):
+    """HBM roofline curve over grid sizes: the ST step with FP32, BF16 and
+    FP16 deviation storage and the FV step (FP32, periodic flow) on n x n
+    grids, each step timed alone after an L2 flush.  One dict per point."""
+    rows = []
+    for n in sizes:
+        for label, w in (("st_f32", cfg.st_sweep(n, lb.LB_STORE_F32)),
+                         ("st_bf16dev", cfg.st_sweep(n, lb.LB_STORE_BF16DEV)),
+                         ("st_f16dev", cfg.st_sweep(n, lb.LB_STORE_F16DEV)),
+                         ("fv_f32", _fv_big(cfg, n))):
+            g = make_grid(lb, w, stream)
+            ms, _ = time_steps(lb, torch, g, w.scheme, 20 if w.scheme == "st" else 10, 3, flush)
+            mean = sum(ms) / len(ms)
+            bpc = cfg.bytes_per_cell(w.grid["store"], False, 9)
+            rows.append({"sweep": label, "n": n, "cells": w.cells, "mlups": round(w.cells / (mean * 1e-3) / 1e6, 1),
+                         "ms_per_step": round(mean, 5), "bytes_per_cell": bpc,
+                         "frac_hbm": round(bpc * w.cells / (mean * 1e-3) / 1e9 / peak, 4),
+                         "schedule": schedule_name(lb, g, w.scheme)})
+            g.close()
+            torch.cuda.empty_cache()
+    return rows
+
+
 def _fv_big(cfg, n):
     """Periodic n x n FV TGV, FP32 (flow only), dt = 0.5: FV kernel at scale."""
     from paper_1505_03271_gb300 import LB_INIT_TGV, LB_STORE_F32
@@ -434,6 +457,13 @@ def _config(w, case="channel"):
             "dt": round(w.params["dt"], 6), "l2": "flushed: 256 MiB write between timed steps"}
 
 
+def visible_gpu_index(local):
+    """nvidia-smi index of this rank's GPU (the first CUDA_VISIBLE_DEVICES
+    entry when it is a number)."""
+    first = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0]
+    return int(first) if first.isdigit() else local
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -446,6 +476,8 @@ def main():
                     help="workload to time: channel (headline), st8192, st4096, st4096_f16dev, "
                          "fv4096, fv2048, rb1024, rb3d_fv, rb3d_st (3-D Table rb grids)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving stream")
+    ap.add_argument("--roofline-sweep", default=None, metavar="N,N,...",
+                    help="print the ST/FV roofline curve over these n x n grid sizes instead of the bench line")
     ap.add_argument("--serving-requests", type=int, default=160)
     ap.add_argument("--serving-rate", type=float, default=60.0, help="Poisson arrivals per second")
     ap.add_argument("--fv-schedule", default="tune",
@@ -475,6 +507,16 @@ def main():
     lb.load()
     stream = torch.cuda.current_stream().cuda_stream
     peak, peak_kind = load_peaks()
+    if args.roofline_sweep:
+        flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+        sizes = [int(v) for v in args.roofline_sweep.split(",")]
+        with ClockSampler(visible_gpu_index(local)) as clk:
+            rows = roofline_sweep(lb, torch, cfg, stream, peak, flush, sizes)
+        for r in rows:
+            r["peak"], r["peak_source"] = peak, f"{peak_kind} hbm_gbs"
+            print(json.dumps(r), flush=True)
+        print(json.dumps({"clocks": clk.summary()}), flush=True)
+        return
     w = case_workload(cfg, args.case)
     g = make_grid(lb, w, stream)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -485,8 +527,7 @@ def main():
             dist.barrier()
         torch.cuda.synchronize()
 
-    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0]) if \
-        os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0].isdigit() else local
+    gpu_index = visible_gpu_index(local)
     barrier()
     with ClockSampler(gpu_index) as clk:
         ms, launches = time_steps(lb, torch, g, w.scheme, args.steps, args.warmup, flush)
