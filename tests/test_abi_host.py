@@ -95,3 +95,45 @@ def test_serving_request_recipe():
         assert r.params["dt"] <= 0.9 * min(np.diff(__import__("paper_1505_03271_gb300.configs",
                                                                fromlist=["x"]).faces(r.n, r.n, 1, 2.0)).min(),
                                            8 * min(r.params["tau"], r.params["tau_g"])) + 1e-15
+
+
+C_CALLER = r"""
+#include <stdio.h>
+#include <string.h>
+#include "lb.h"
+#include "lb3.h"
+
+int main(void) {
+    lb_grid* g = NULL;
+    lb3_grid* g3 = NULL;
+    int n = -1;
+    if (lb_create_grid(NULL, &g) != LB_ERR_ARG || g != NULL) return 1;
+    if (strstr(lb_last_error(), "NULL") == NULL) return 2;
+    if (lb3_create_grid(NULL, &g3) != LB_ERR_ARG) return 3;
+    if (lb_step_fv(NULL, 1) == LB_OK || lb_step_st(NULL, 1) == LB_OK) return 4;
+    if (lb_set_graph_steps(NULL, 32) != LB_ERR_ARG) return 5;
+    if (lb_get_graph_steps(NULL, &n, NULL) != LB_ERR_ARG || n != -1) return 6;
+    if (lb_destroy(NULL) != LB_OK) return 7;
+    printf("launches %llu\n", lb_kernel_launches());
+    return 0;
+}
+"""
+
+
+def test_c_caller_links_and_runs(tmp_path):
+    """A C99 program includes both headers, links the library and calls its
+    argument checks (no device work): the boundary is usable from C."""
+    import subprocess
+    import paper_1505_03271_gb300 as lb
+    lib = lb.library_path()
+    lb.load()
+    src = tmp_path / "caller.c"
+    src.write_text(C_CALLER)
+    exe = tmp_path / "caller"
+    libdir = os.path.dirname(lib)
+    name = os.path.basename(lib)[3:-3]  # libNAME.so -> NAME
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-pedantic", "-I", os.path.join(ROOT, "include"),
+                    str(src), "-L", libdir, "-l" + name, "-Wl,-rpath," + libdir, "-o", str(exe)], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, (r.returncode, r.stderr)
+    assert r.stdout.strip() == "launches 0"
