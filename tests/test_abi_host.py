@@ -137,3 +137,33 @@ def test_c_caller_links_and_runs(tmp_path):
     r = subprocess.run([str(exe)], capture_output=True, text=True)
     assert r.returncode == 0, (r.returncode, r.stderr)
     assert r.stdout.strip() == "launches 0"
+
+
+def test_product_and_oracle_share_no_code():
+    """The CUDA path and the oracle are independent: no file of the package
+    imports or includes anything of oracle/, and no oracle file includes a
+    header or source of the package or include/."""
+    pkg = os.path.join(ROOT, "paper_1505_03271_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        if "_lib" in dirpath or "__pycache__" in dirpath:
+            continue
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                text = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", text, re.M), f
+                assert not re.search(r"#\s*include\s*[<\"][^>\"]*(oracle|lbref)", text), f
+    for f in os.listdir(os.path.join(ROOT, "oracle")):
+        if f.endswith((".c", ".h", ".py")):
+            text = open(os.path.join(ROOT, "oracle", f)).read()
+            assert not re.search(r"#\s*include\s*[<\"][^>\"]*(lb\.h|lb3\.h|\.cuh|csrc)", text), f
+            assert not re.search(r"^\s*(import|from)\s+paper_1505_03271_gb300\b", text, re.M), f
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """With the CUDA library absent the binding raises: there is no CPU path."""
+    import paper_1505_03271_gb300 as lb
+    from paper_1505_03271_gb300 import _build
+    monkeypatch.setattr(lb, "_lib", None)
+    monkeypatch.setattr(_build, "LIB", str(tmp_path / "libmissing.so"))
+    with pytest.raises(RuntimeError, match="CUDA library missing"):
+        lb.load(build=False)
