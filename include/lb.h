@@ -128,7 +128,8 @@ lb_status lb_init(lb_grid* grid, const lb_params* params, const lb_init_desc* in
  * interpolated to the faces by QUICK (Sec. II B 3), walls use the double
  * reflection of Sec. II B 5 on h (thermal field: anti-reflection through
  * T_wall), the predictor f~* is Eq. (semi) and the corrector averages the
- * two flux divergences.  One fused kernel launch per step.
+ * two flux divergences.  One fused kernel launch per step (long runs replay
+ * the launches as a CUDA graph: lb_set_graph_steps).
  * LB_ERR_STATE if the grid has no parameters or is poisoned. */
 lb_status lb_step_fv(lb_grid* grid, int nsteps);
 
@@ -136,7 +137,8 @@ lb_status lb_step_fv(lb_grid* grid, int nsteps);
  * each population to its neighbour; walls use half-way bounce-back (f) and
  * anti-bounce-back through the plate temperature (g).  Requires uniform axes
  * with unit spacing and dt = 1 (LB_ERR_ARG otherwise), since streaming ties
- * the mesh to the lattice (Sec. II A).  One kernel launch per step. */
+ * the mesh to the lattice (Sec. II A).  One kernel launch per step (long
+ * runs replay the launches as a CUDA graph: lb_set_graph_steps). */
 lb_status lb_step_st(lb_grid* grid, int nsteps);
 
 /* Long runs.  A call of lb_step_fv or lb_step_st with more than 2 n steps,

@@ -699,3 +699,18 @@ def test_graph_steps_rules(lbgpu):
     g.step_fv(65)
     assert g.graph_steps() == (32, 2)
     g.close()
+
+
+@pytest.mark.skipif(os.environ.get("LB_FULL_LENGTH_PARITY") != "1",
+                    reason="20000 oracle steps of the full channel take minutes of CPU; "
+                           "set LB_FULL_LENGTH_PARITY=1 to run")
+def test_config_channel_f32_full_length(lbgpu, oracle):
+    """The U = 0.05 FP32 channel over its full 20000 FV steps, through the
+    default schedule and graph replays, against the oracle: relative L2 of
+    u below 1e-5 (the FP32 bar of the channel workload)."""
+    from paper_1505_03271_gb300 import configs as cfg
+    w = cfg.channel(u_max=0.05)
+    g, r = pair(lbgpu, oracle, store=w.grid.pop("store"), **w.grid, **w.params, **w.init)
+    g.step_fv(w.steps)
+    r.step_fv(w.steps)
+    assert rel_l2_u(g, r) < 1e-5
