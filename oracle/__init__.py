@@ -7,8 +7,14 @@ and this package never imports the CUDA library.
 
 Functions with a pin in ``tests/test_oracle_*.py``: lattice constants,
 face generators, Lagrange/QUICK weights, equilibrium, Guo force, the ST step,
-the FV step, the wall rules and the observables.  Parity is unpinned only for
-the thermal isothermal-wall reading beyond the checks listed in those tests.
+the FV step, the wall rules (the isothermal plates through the exactly
+steady conduction state) and the observables.
+
+Parity unpinned: the force part of the FV advected field, h = ... + dt/2 F
+(the literal form of Sec. II B 5).  The exact inverse of the tilde
+transformation would carry (dt/2)(1 - dt/(2 tau~)) F instead; the two differ
+by O(dt^2 F / tau~), below what the Poiseuille pins resolve, so no test
+tells them apart.
 """
 from __future__ import annotations
 

@@ -25,6 +25,12 @@
  *     temperature is 2 T_wall - T(x_k) for the equilibrium and the diffusive
  *     part alike (the FV counterpart of anti-bounce-back).
  *   - Streaming walls use half-way bounce-back (f) and anti-bounce-back (g).
+ *
+ * Parity unpinned: the force part of the FV advected field h is the literal
+ * dt/2 F of Sec. II B 5.  The exact inverse of the tilde transformation would
+ * give (dt/2)(1 - dt/(2 tau~)) F; the difference, O(dt^2 F / tau~), lies below
+ * what the Poiseuille pins resolve.  Every other routine has a pin in the
+ * oracle tests.
  */
 #include "lbref.h"
 
