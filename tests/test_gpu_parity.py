@@ -714,3 +714,21 @@ def test_config_channel_f32_full_length(lbgpu, oracle):
     g.step_fv(w.steps)
     r.step_fv(w.steps)
     assert rel_l2_u(g, r) < 1e-5
+
+
+@pytest.mark.skipif(os.environ.get("LB_FULL_LENGTH_PARITY") != "1",
+                    reason="2000 oracle steps of the 1024^2 RB cell take tens of minutes of CPU; "
+                           "set LB_FULL_LENGTH_PARITY=1 to run")
+def test_config_rb1024_f16_first_2000_steps(lbgpu, oracle):
+    """The 1024^2 Ra = 1e8 RB cell with FP16 deviation storage over its first
+    2000 FV steps, against the FP64 oracle: the volume and plate Nusselt
+    numbers within 1e-3 (the 16-bit storage bar of this workload)."""
+    from paper_1505_03271_gb300 import configs as cfg
+    w = cfg.rayleigh_benard(1024, 1e8)
+    grid = dict(w.grid)
+    grid.pop("store")
+    g, r = pair(lbgpu, oracle, store=lbgpu.LB_STORE_F16DEV, **grid, **w.params, **w.init)
+    g.step_fv(w.steps)
+    r.step_fv(w.steps)
+    for a, b in zip(g.nusselt(), r.nusselt()):
+        assert abs(a / b - 1) < 1e-3
