@@ -73,3 +73,13 @@ def test_roofline_arithmetic():
 def test_single_rank_aggregate():
     t, mlups = bench.aggregate(0.5, 131072, 1000, 1)
     assert t == 0.5 and mlups == pytest.approx(131072 * 1000 / 0.5 / 1e6)
+
+
+def test_reference_arm_other_ranks_do_no_work():
+    """Under torchrun only rank 0 times the oracle; the other ranks exit 0
+    without output."""
+    env = dict(os.environ, RANK="1", WORLD_SIZE="2", LOCAL_RANK="1")
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--gpus", "2", "--steps", "1",
+                        "--warmup", "3"], cwd=ROOT, capture_output=True, text=True, timeout=300, env=env)
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip() == ""
