@@ -371,10 +371,32 @@ def e2e_measure(lb, torch, w, stream, reps=3, inner=1000):
 
 # ------------------------------------------------------------------ oracle --
 
-def oracle_sample(w, budget_s=15.0, steps_cap=None):
-    """Oracle FV/ST steps on the workload for about budget_s seconds."""
+def cpu_model():
+    """CPU model name of this host (lscpu, else /proc/cpuinfo, else the
+    machine type)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
+
+
+def oracle_sample(w, budget_s=15.0, steps_cap=None, threads=None):
+    """Oracle FV/ST steps on the workload for about budget_s seconds, on
+    `threads` OpenMP threads (default: every host core)."""
     import oracle as O
-    threads = os.cpu_count() or 1
+    threads = threads or os.cpu_count() or 1
     O.set_threads(threads)
     grid = dict(w.grid)
     grid.pop("store")
@@ -423,7 +445,8 @@ def run_reference(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": _config(w),
             "cpu_baseline": {"value": round(v, 3), "unit": "MLUPS", "cores": O.get_threads(),
-                             "kind": "oracle", "sample": "%d full FV steps of the channel" % args.steps},
+                             "kind": "oracle", "sample": "%d full FV steps of the channel" % args.steps,
+                             "cpu_model": cpu_model()},
             "e2e": {"value": round(v, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -555,6 +578,7 @@ def main():
         import oracle as O
         O.build()
         r, done, el, thr = oracle_sample(w, budget_s=15.0)
+        _, done1, el1, _ = oracle_sample(w, budget_s=5.0, threads=1)
         # error of the GPU against the oracle after the same number of steps
         g2 = make_grid(lb, w, stream, tune=False)
         g2.set_fv_schedule(*g.fv_schedule())
@@ -564,7 +588,11 @@ def main():
         err = float(np.sqrt(((ux - vx) ** 2 + (uy - vy) ** 2).sum() / (vx**2 + vy**2).sum()))
         line["cpu_baseline"] = {"value": round(w.cells * done / el / 1e6, 3), "unit": "MLUPS",
                                 "cores": thr, "kind": "oracle",
-                                "sample": "%d FV steps of the full channel (%.1f s)" % (done, el)}
+                                "sample": "%d FV steps of the full channel (%.1f s)" % (done, el),
+                                "cpu_model": cpu_model(),
+                                "single_thread": {"value": round(w.cells * done1 / el1 / 1e6, 3),
+                                                  "sample": "%d FV steps of the full channel (%.1f s)"
+                                                            % (done1, el1)}}
         line["oracle_error"] = {"rel_l2_u": err, "steps": done}
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -7,6 +7,7 @@ import os
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -83,3 +84,16 @@ def test_reference_arm_other_ranks_do_no_work():
                         "--warmup", "3"], cwd=ROOT, capture_output=True, text=True, timeout=300, env=env)
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_oracle_sample_threads_and_cpu_model():
+    """The CPU legs of the bench: a bounded oracle sample on the requested
+    thread count, and the host's CPU model for the JSON line."""
+    from paper_1505_03271_gb300 import configs as cfg
+    w = cfg.channel(nx=16, ny=32)
+    r, done, el, thr = bench.oracle_sample(w, budget_s=0.05, threads=1)
+    assert thr == 1 and done >= 1 and el > 0
+    _, ux, _, _ = r.moments()
+    assert ux.shape == (32, 16) and np.isfinite(ux).all()
+    model = bench.cpu_model()
+    assert isinstance(model, str) and model
