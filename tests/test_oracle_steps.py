@@ -309,3 +309,27 @@ def test_rb_ra1e4_nusselt(oracle):
     g.step_st(int(0.9 * H * H / p.kappa))
     for nu in g.nusselt():
         assert abs(nu - Nu_ref) < tol, g.nusselt()
+
+
+@pytest.mark.parametrize("sy,stretch", [(0, 0.0), (1, 2.0)], ids=["uniform", "tanh"])
+def test_plate_nusselt_exact_on_quadratic_profiles(oracle, sy, stretch):
+    """The plate Nusselt numbers (Sec. IV post-processing: the quadratic
+    through the wall value and the first two cell centres) are exact on any
+    temperature profile T(y) = T_bot + b y + c y^2 that meets both plate
+    temperatures, where a first-order one-sided gradient would be off by
+    c y_0.  With the fluid at rest the volume Nusselt number is exactly 1."""
+    nx, ny, H = 3, 12, 12.0
+    T_bot, T_top, c = 1.5, 0.5, 2e-3
+    b = (T_top - T_bot - c * H * H) / H
+    g = oracle.RefGrid(nx, ny, ly=H, sy=sy, stretch_y=stretch, bcy=1, thermal=True)
+    g.set_params(tau=0.2, dt=0.1, tau_g=0.2, beta=1e-3, grav=1.0, T0=1.0, T_bot=T_bot, T_top=T_top)
+    yc = g.centers()[1]
+    T = np.repeat((T_bot + b * yc + c * yc * yc)[:, None], nx, axis=1)
+    g.init_fields(np.ones((ny, nx)), np.zeros((ny, nx)), np.zeros((ny, nx)), T)
+    nu_vol, nu_bot, nu_top = g.nusselt()
+    dT = T_bot - T_top
+    assert nu_vol == pytest.approx(1.0, abs=1e-14)
+    assert nu_bot == pytest.approx(-H * b / dT, rel=1e-12)
+    assert nu_top == pytest.approx(-H * (b + 2 * c * H) / dT, rel=1e-12)
+    # the curvature matters at this size: a first-order gradient would miss it
+    assert abs((T[0, 0] - T_bot) / yc[0] - b) > 1e-3 * abs(b)
