@@ -1,5 +1,7 @@
 """One FV step (Eqs. (semi), (semi-heun)) on a 4 x 5 grid recomputed in exact
-rational arithmetic, independently of the oracle's C code: the same readings,
+rational arithmetic, independently of the oracle's C code, for the Heun
+scheme and for the two single-stage schemes (the predictor alone, and
+explicit Euler on plain populations, Eq. (euler)): the same readings,
 written out again with Python fractions from the equations, and compared with
 the oracle's FP64 step.  This is a cross-check of the implementation details
 (indices, ghost cells, upwind node choice, face weights, signs), not a pin of
@@ -161,6 +163,83 @@ def test_fv_step_exact(oracle, walls, stretch, thermal):
     F = {(i, j): [Fr(f[a, j, i]) for a in range(9)] for i in range(nx) for j in range(ny)}
     G = {(i, j): [Fr(g[a, j, i]) for a in range(9)] for i in range(nx) for j in range(ny)} if thermal else None
     Fn, Gn = ex.step(F, G)
+    r.step_fv(1)
+    fr, gr = r.get_pops()
+    ref = np.array([[[float(Fn[(i, j)][a]) for i in range(nx)] for j in range(ny)] for a in range(9)])
+    assert np.abs(fr - ref).max() < 1e-14
+    if thermal:
+        refg = np.array([[[float(Gn[(i, j)][a]) for i in range(nx)] for j in range(ny)] for a in range(9)])
+        assert np.abs(gr - refg).max() < 1e-14
+
+
+class ExactSingleStage(Exact):
+    """The two single-stage FV schemes of Sec. II B 2 on the same grid."""
+
+    def semi(self, F, G):
+        """Eq. (semi) alone: f~ - dt A[h] + Coll, the Heun predictor."""
+        dt = self.p["dt"]
+        h, hg, co, cog = self.eval(F, G)
+        A = self.advect(h, False)
+        Fn = {c: [F[c][a] - dt * A[c][a] + co[c][a] for a in range(9)] for c in F}
+        if not self.th:
+            return Fn, None
+        Ag = self.advect(hg, True)
+        return Fn, {c: [G[c][a] - dt * Ag[c][a] + cog[c][a] for a in range(9)] for c in F}
+
+    def euler(self, F, G):
+        """Eq. (euler) on plain populations: the advected field is f itself,
+        u = sum c f / rho with no half-step shift, and the source is
+        dt/tau (f_eq - f) + dt F (g: dt/tau_g (g_eq - g))."""
+        p, dt = self.p, self.p["dt"]
+        src, srcg = {}, {}
+        for (i, j), f in F.items():
+            rho = sum(f)
+            T = sum(G[(i, j)]) if self.th else Fr(0)
+            ax, ay = p["ax"], p["ay"] + (p["bg"] * (T - p["T0"]) if self.th else 0)
+            ux = sum(CX[a] * f[a] for a in range(9)) / rho
+            uy = sum(CY[a] * f[a] for a in range(9)) / rho
+            uu = ux * ux + uy * uy
+            s, sg = [], []
+            for a in range(9):
+                cu = CX[a] * ux + CY[a] * uy
+                feq = W[a] * rho * (1 + 3 * cu + Fr(9, 2) * cu * cu - Fr(3, 2) * uu)
+                fa = W[a] * rho * ((3 * (CX[a] - ux) + 9 * cu * CX[a]) * ax + (3 * (CY[a] - uy) + 9 * cu * CY[a]) * ay)
+                s.append(dt / p["tau"] * (feq - f[a]) + dt * fa)
+                if self.th:
+                    sg.append(dt / p["tau_g"] * (T / rho * feq - G[(i, j)][a]))
+            src[(i, j)] = s
+            if self.th:
+                srcg[(i, j)] = sg
+        A = self.advect(F, False)
+        Fn = {c: [F[c][a] - dt * A[c][a] + src[c][a] for a in range(9)] for c in F}
+        if not self.th:
+            return Fn, None
+        Ag = self.advect(G, True)
+        return Fn, {c: [G[c][a] - dt * Ag[c][a] + srcg[c][a] for a in range(9)] for c in F}
+
+
+@pytest.mark.parametrize("scheme", ["semi", "euler"])
+@pytest.mark.parametrize("walls,stretch,thermal", [(False, 0.0, False), (True, 1.5, False), (True, 1.5, True)])
+def test_fv_single_stage_steps_exact(oracle, scheme, walls, stretch, thermal):
+    nx, ny = 4, 5
+    sy = oracle.TANH if stretch else oracle.UNIFORM
+    kw = dict(tau=0.3, dt=0.25, ax=2e-3, ay=-1e-3)
+    if thermal:
+        kw.update(tau_g=0.2, beta=0.05, grav=1.0, T0=1.0, T_bot=1.25, T_top=0.75)
+    r = oracle.RefGrid(nx, ny, ly=5.0, sy=sy, stretch_y=stretch, bcy=oracle.WALLS if walls else oracle.PERIODIC,
+                       thermal=thermal)
+    r.set_scheme(oracle.FV_SEMI if scheme == "semi" else oracle.FV_EULER).set_params(**kw)
+    f = inputs.random_populations(nx, ny, seed=23, amp=0.3)
+    g = inputs.random_populations(nx, ny, seed=24, amp=0.3) if thermal else None
+    r.set_pops(f, g)
+    xi_x, xi_y = r.face_coords()
+    p = {k: Fr(v) for k, v in kw.items()}
+    p.setdefault("tau_g", p["tau"])
+    p["bg"] = p.get("beta", Fr(0)) * p.get("grav", Fr(0))
+    ex = ExactSingleStage([Fr(v) for v in xi_x], [Fr(v) for v in xi_y], walls, thermal, p)
+    F = {(i, j): [Fr(f[a, j, i]) for a in range(9)] for i in range(nx) for j in range(ny)}
+    G = {(i, j): [Fr(g[a, j, i]) for a in range(9)] for i in range(nx) for j in range(ny)} if thermal else None
+    Fn, Gn = ex.semi(F, G) if scheme == "semi" else ex.euler(F, G)
     r.step_fv(1)
     fr, gr = r.get_pops()
     ref = np.array([[[float(Fn[(i, j)][a]) for i in range(nx)] for j in range(ny)] for a in range(9)])
