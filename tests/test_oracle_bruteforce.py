@@ -1,7 +1,8 @@
 """One FV step (Eqs. (semi), (semi-heun)) on a 4 x 5 grid recomputed in exact
 rational arithmetic, independently of the oracle's C code, for the Heun
 scheme and for the two single-stage schemes (the predictor alone, and
-explicit Euler on plain populations, Eq. (euler)): the same readings,
+explicit Euler on plain populations, Eq. (euler)), with periodic axes,
+walls, thermal plates and the fixed-density boundary: the same readings,
 written out again with Python fractions from the equations, and compared with
 the oracle's FP64 step.  This is a cross-check of the implementation details
 (indices, ghost cells, upwind node choice, face weights, signs), not a pin of
@@ -247,3 +248,64 @@ def test_fv_single_stage_steps_exact(oracle, scheme, walls, stretch, thermal):
     if thermal:
         refg = np.array([[[float(Gn[(i, j)][a]) for i in range(nx)] for j in range(ny)] for a in range(9)])
         assert np.abs(gr - refg).max() < 1e-14
+
+
+class ExactBC(ExactSingleStage):
+    """The same steps with each axis periodic, walls, or a fixed-density
+    boundary (Sec. II B 5): a density ghost takes the same population of the
+    node it mirrors, scaled by rho_g / rho_k with rho_g = 2 rho_S - rho_k (the
+    face lies midway between the two centres)."""
+
+    def __init__(self, xi_x, xi_y, kinds, rho_bc, p):
+        super().__init__(xi_x, xi_y, False, False, p)
+        self.kinds = kinds
+        self.walls = [k != "periodic" for k in kinds]  # ghost centres are mirrored
+        self.rho_bc = rho_bc
+
+    def value(self, h, a, i, j, thermal):
+        idx = [i, j]
+        for ax in (0, 1):
+            n, t = self.n[ax], idx[ax]
+            if 0 <= t < n:
+                continue
+            if self.kinds[ax] == "periodic":
+                idx[ax] = t % n
+                return h[tuple(idx)][a]
+            k = -t if t < 0 else t - n + 1
+            idx[ax] = k - 1 if t < 0 else n - k
+            src = h[tuple(idx)]
+            if self.kinds[ax] == "walls":
+                return src[INV[a]]
+            rho_s = self.rho_bc[ax][0 if t < 0 else 1]
+            rho_k = sum(src)
+            return (2 * rho_s - rho_k) / rho_k * src[a]
+        return h[(i, j)][a]
+
+
+@pytest.mark.parametrize("scheme", ["heun", "semi", "euler"])
+@pytest.mark.parametrize("kinds,stretch", [(("density", "periodic"), (1.5, 0.0)),
+                                           (("periodic", "density"), (0.0, 0.0)),
+                                           (("density", "walls"), (0.0, 1.5))],
+                         ids=["x-density-tanh", "y-density", "x-density-y-walls"])
+def test_fv_density_boundary_step_exact(oracle, scheme, kinds, stretch):
+    nx, ny = 5, 4
+    code = {"periodic": oracle.PERIODIC, "walls": oracle.WALLS, "density": oracle.DENSITY}
+    sp = [oracle.TANH if s else oracle.UNIFORM for s in stretch]
+    kw = dict(tau=0.3, dt=0.25, ax=2e-3, ay=-1e-3)
+    r = oracle.RefGrid(nx, ny, lx=5.0, ly=4.0, sx=sp[0], sy=sp[1], stretch_x=stretch[0], stretch_y=stretch[1],
+                       bcx=code[kinds[0]], bcy=code[kinds[1]])
+    r.set_scheme({"heun": oracle.FV_HEUN, "semi": oracle.FV_SEMI, "euler": oracle.FV_EULER}[scheme])
+    r.set_params(**kw).set_boundary_density(rho_x0=1.03, rho_x1=0.98, rho_y0=1.01, rho_y1=0.97)
+    f = inputs.random_populations(nx, ny, seed=25, amp=0.3)
+    r.set_pops(f)
+    xi_x, xi_y = r.face_coords()
+    p = {k: Fr(v) for k, v in kw.items()}
+    p["tau_g"], p["bg"] = p["tau"], Fr(0)
+    rho_bc = [(Fr(1.03), Fr(0.98)), (Fr(1.01), Fr(0.97))]
+    ex = ExactBC([Fr(v) for v in xi_x], [Fr(v) for v in xi_y], kinds, rho_bc, p)
+    F = {(i, j): [Fr(f[a, j, i]) for a in range(9)] for i in range(nx) for j in range(ny)}
+    Fn = {"heun": ex.step, "semi": ex.semi, "euler": ex.euler}[scheme](F, None)[0]
+    r.step_fv(1)
+    fr = r.get_pops()[0]
+    ref = np.array([[[float(Fn[(i, j)][a]) for i in range(nx)] for j in range(ny)] for a in range(9)])
+    assert np.abs(fr - ref).max() < 1e-14
