@@ -175,3 +175,24 @@ def test_conduction_state_3d(oracle):
         zc = 0.5 * (xi[1:] + xi[:-1])
         assert np.allclose(T, (1.0 + (0.5 - zc / 12.0))[:, None, None], atol=1e-12)
         assert np.allclose(g.nusselt(), 1.0, atol=1e-10)
+
+
+def test_plate_nusselt_exact_on_quadratic_profiles_3d(oracle):
+    """As in two dimensions: on T(z) = T_bot + b z + c z^2 meeting both plate
+    temperatures, the plate Nusselt numbers equal -H T'(0)/dT and
+    -H T'(H)/dT to rounding, on a sinh z grid; at rest Nu_vol = 1."""
+    nx, ny, nz, H = 3, 2, 12, 12.0
+    T_bot, T_top, c = 1.5, 0.5, 2e-3
+    b = (T_top - T_bot - c * H * H) / H
+    g = oracle.RefGrid3(nx, ny, nz, lz=H, sz=oracle.SINH, stretch_z=3.0, bcz=oracle.WALLS, thermal=True)
+    g.set_params(tau=0.2, dt=0.1, tau_g=0.2, beta=1e-3, grav=1.0, T0=1.0, T_bot=T_bot, T_top=T_top)
+    xi = oracle.faces(nz, H, oracle.SINH, 3.0)
+    zc = 0.5 * (xi[1:] + xi[:-1])
+    shape = (nz, ny, nx)
+    T = np.broadcast_to((T_bot + b * zc + c * zc * zc)[:, None, None], shape).copy()
+    g.init_fields(np.ones(shape), np.zeros(shape), np.zeros(shape), np.zeros(shape), T)
+    nu_vol, nu_bot, nu_top = g.nusselt()
+    dT = T_bot - T_top
+    assert nu_vol == pytest.approx(1.0, abs=1e-14)
+    assert nu_bot == pytest.approx(-H * b / dT, rel=1e-12)
+    assert nu_top == pytest.approx(-H * (b + 2 * c * H) / dT, rel=1e-12)
