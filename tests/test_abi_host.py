@@ -167,3 +167,65 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(_build, "LIB", str(tmp_path / "libmissing.so"))
     with pytest.raises(RuntimeError, match="CUDA library missing"):
         lb.load(build=False)
+
+
+def _desc2(lb, **kw):
+    d = dict(nx=16, ny=16, lx=16.0, ly=16.0, sx=0, sy=0, stretch_x=0.0, stretch_y=0.0, bcx=0, bcy=0,
+             thermal=0, store=1, cuda_stream=None)
+    d.update(kw)
+    return lb.lb_grid_desc(**d)
+
+
+def _desc3(lb, **kw):
+    d = dict(nx=8, ny=8, nz=8, lx=8.0, ly=8.0, lz=8.0, sx=0, sy=0, sz=0, stretch_x=0.0, stretch_y=0.0,
+             stretch_z=0.0, bcx=0, bcy=0, bcz=0, thermal=0, store=1, cuda_stream=None)
+    d.update(kw)
+    return lb.lb3_grid_desc(**d)
+
+
+BAD_2D = {
+    "empty axis": dict(nx=0),
+    "too many cells": dict(nx=1 << 16, ny=(1 << 15) + 1),
+    "unknown boundary": dict(bcy=7),
+    "wall axis of one cell": dict(ny=1, bcy=1),
+    "thermal with x walls": dict(thermal=1, bcx=1, bcy=1),
+    "thermal with a density axis": dict(thermal=1, bcy=2),
+    "unknown storage": dict(store=9),
+    "unknown spacing": dict(sy=9),
+    "zero length": dict(ly=0.0),
+    "tanh without stretch": dict(sy=1, bcy=1),
+    "sinh on an odd count": dict(ny=15, sy=2, stretch_y=2.0, bcy=1),
+}
+
+BAD_3D = {
+    "empty axis": dict(nz=0),
+    "density axis": dict(bcz=2),
+    "wall axis of one cell": dict(nz=1, bcz=1),
+    "16-bit storage": dict(store=2),
+    "thermal with side walls": dict(thermal=1, bcx=1, bcz=1),
+    "sinh on an odd count": dict(nz=9, sz=2, stretch_z=2.0, bcz=1),
+    "zero length": dict(lx=0.0),
+    "nz too large": dict(nx=1, ny=1, nz=70000),
+}
+
+
+@pytest.mark.parametrize("case", sorted(BAD_2D))
+def test_create_grid_rejects_bad_descriptions(case):
+    """Grid descriptions the method or the kernels cannot take are refused
+    with LB_ERR_ARG and a message, before any device work."""
+    import paper_1505_03271_gb300 as lb
+    L = lb.load()
+    h = ctypes.c_void_p()
+    L.lb_set_graph_steps(None, 2)  # leaves "grid is NULL" as the last message
+    assert L.lb_create_grid(ctypes.byref(_desc2(lb, **BAD_2D[case])), ctypes.byref(h)) == lb.LB_ERR_ARG
+    assert not h.value and lb.lb_last_error() not in ("", "grid is NULL")
+
+
+@pytest.mark.parametrize("case", sorted(BAD_3D))
+def test_create_grid3_rejects_bad_descriptions(case):
+    import paper_1505_03271_gb300 as lb
+    L = lb.load()
+    h = ctypes.c_void_p()
+    L.lb_set_graph_steps(None, 2)
+    assert L.lb3_create_grid(ctypes.byref(_desc3(lb, **BAD_3D[case])), ctypes.byref(h)) == lb.LB_ERR_ARG
+    assert not h.value and lb.lb_last_error() not in ("", "grid is NULL")
