@@ -76,6 +76,7 @@ struct ref_grid {
 /* building blocks                                                     */
 /* ------------------------------------------------------------------ */
 
+/* The D2Q9 velocities, weights and opposite-velocity map (Sec. II). */
 void ref_lattice(int* cx, int* cy, double* w, int* inv) {
     for (int a = 0; a < Q; ++a) {
         if (cx) cx[a] = CX[a];
@@ -114,7 +115,8 @@ void ref_faces(int n, double L, int spacing, double stretch, double* xi) {
     xi[n] = L;
 }
 
-/* Lagrange weights of the parabola through pos[0..2], evaluated at x. */
+/* Lagrange weights of the parabola through pos[0..2], evaluated at x: the
+ * QUICK gamma coefficients of Sec. II B 3 on any node spacing. */
 void ref_lagrange3(const double* pos, double x, double* wts) {
     for (int k = 0; k < 3; ++k) {
         double num = 1.0, den = 1.0;
@@ -328,6 +330,9 @@ int ref_init_fields(ref_grid* G, const double* rho, const double* ux, const doub
     return 0;
 }
 
+/* The workloads' initial fields (Taylor-Green, shear wave, the Poiseuille
+ * parabola of Sec. III B, and the Rayleigh-Benard conduction state with its
+ * seeded perturbation, Sec. IV), set through ref_init_fields. */
 int ref_init_preset(ref_grid* G, int kind, double u0, double amp, int mode,
                     unsigned long long seed) {
     if (!G || !G->has_params) return -1;
@@ -405,6 +410,9 @@ static int axis_uniform_unit(int sp, int n, double L) {
     return sp == REF_UNIFORM && fabs(L / n - 1.0) < 1e-12;
 }
 
+/* nsteps ST steps, Eq. (ST) with dt = dx = 1 (Sec. II A): collide each
+ * cell and push each population to its neighbour; walls use half-way
+ * bounce-back (f) and anti-bounce-back through T_wall (g). */
 int ref_step_st(ref_grid* G, int nsteps) {
     if (!G || !G->has_params || nsteps < 0) return -1;
     const ref_params* p = &G->p;
@@ -656,6 +664,10 @@ int ref_set_scheme(ref_grid* G, int scheme) {
     return 0;
 }
 
+/* nsteps FV steps (Sec. II B 2): Eq. (semi) as the predictor, and the Heun
+ * corrector of Eq. (semi-heun) for the default scheme; the single-stage
+ * schemes stop after the first update (Eq. (semi) alone, or Eq. (euler) on
+ * plain populations). */
 int ref_step_fv(ref_grid* G, int nsteps) {
     if (!G || !G->has_params || nsteps < 0) return -1;
     const double dt = G->p.dt;
@@ -701,6 +713,7 @@ int ref_step_fv(ref_grid* G, int nsteps) {
 /* observables                                                         */
 /* ------------------------------------------------------------------ */
 
+/* Cell moments rho, force-corrected u and T (Sec. II B 4, Eq. (LBg)). */
 int ref_moments(const ref_grid* G, double* rho, double* ux, double* uy, double* T) {
     if (!G || !G->has_params) return -1;
     for (int j = 0; j < G->ny; ++j)
