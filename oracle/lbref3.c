@@ -45,6 +45,7 @@ struct ref3_grid {
 #define P3(G, a, i, j, k) \
     ((((size_t)(a) * ((G)->n[2] + 4) + (k) + 2) * ((G)->n[1] + 4) + (j) + 2) * ((G)->n[0] + 4) + (i) + 2)
 
+/* The D3Q19 velocities, weights and opposite-velocity map (Sec. II). */
 void ref3_lattice(int* cx, int* cy, int* cz, double* w, int* inv) {
     for (int a = 0; a < Q3; ++a) {
         if (cx) cx[a] = CX3[a];
@@ -204,6 +205,9 @@ int ref3_init_fields(ref3_grid* G, const double* rho, const double* ux, const do
     return 0;
 }
 
+/* The 3-D workloads' initial fields (Taylor-Green, shear wave, and the Rayleigh-Benard
+ * conduction state between the z plates with its seeded perturbation,
+ * Sec. IV), set through ref3_init_fields. */
 int ref3_init_preset(ref3_grid* G, int kind, double u0, double amp, int mode, unsigned long long seed) {
     if (!G || !G->has_params) return -1;
     if (kind == REF_INIT_RB && !G->d.thermal) return -1;
@@ -423,6 +427,9 @@ static void fv_advect3(const ref3_grid* G, const double* hp, double* A) {
             }
 }
 
+/* nsteps FV steps: Eq. (semi) as the predictor and the Heun corrector of
+ * Eq. (semi-heun) (Sec. II B 2), QUICK faces along each axis line
+ * (Sec. II B 3), double-reflection walls (Sec. II B 5). */
 int ref3_step_fv(ref3_grid* G, int nsteps) {
     if (!G || !G->has_params || nsteps < 0) return -1;
     const double dt = G->p.dt;
@@ -451,6 +458,7 @@ int ref3_step_fv(ref3_grid* G, int nsteps) {
     return 0;
 }
 
+/* Cell moments rho, force-corrected u and T (Sec. II B 4, Eq. (LBg)). */
 int ref3_moments(const ref3_grid* G, double* rho, double* ux, double* uy, double* uz, double* T) {
     if (!G || !G->has_params) return -1;
     for (int k = 0; k < G->n[2]; ++k)
@@ -470,6 +478,7 @@ int ref3_moments(const ref3_grid* G, double* rho, double* ux, double* uy, double
     return 0;
 }
 
+/* Volume integrals sum V rho, sum V rho u (force-corrected u), sum V T. */
 int ref3_conservation(const ref3_grid* G, double* mass, double* mx, double* my, double* mz, double* heat) {
     if (!G || !G->has_params) return -1;
     double m = 0.0, px = 0.0, py = 0.0, pz = 0.0, e = 0.0;
