@@ -229,3 +229,25 @@ def test_create_grid3_rejects_bad_descriptions(case):
     L.lb_set_graph_steps(None, 2)
     assert L.lb3_create_grid(ctypes.byref(_desc3(lb, **BAD_3D[case])), ctypes.byref(h)) == lb.LB_ERR_ARG
     assert not h.value and lb.lb_last_error() not in ("", "grid is NULL")
+
+
+def _declared_arities():
+    out = {}
+    for hdr in ("lb.h", "lb3.h"):
+        text = open(os.path.join(ROOT, "include", hdr)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for name, params in re.findall(r"\b(lb3?_[a-z_]+)\s*\(([^)]*)\)\s*;", text):
+            params = params.strip()
+            out[name] = 0 if params in ("", "void") else len(params.split(","))
+    return out
+
+
+def test_binding_signatures_match_headers():
+    """The ctypes binding declares, for every entry point, as many argument
+    types as the header has parameters (a mismatch would marshal garbage)."""
+    import paper_1505_03271_gb300 as lb
+    L = lb.load()
+    arity = _declared_arities()
+    assert set(arity) == set(lb.SYMBOLS)
+    for name, n in arity.items():
+        assert len(getattr(L, name).argtypes or []) == n, name
