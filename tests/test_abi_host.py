@@ -251,3 +251,47 @@ def test_binding_signatures_match_headers():
     assert set(arity) == set(lb.SYMBOLS)
     for name, n in arity.items():
         assert len(getattr(L, name).argtypes or []) == n, name
+
+
+def _declared_param_types():
+    out = {}
+    for hdr in ("lb.h", "lb3.h"):
+        text = open(os.path.join(ROOT, "include", hdr)).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for name, params in re.findall(r"\b(lb3?_[a-z_]+)\s*\(([^)]*)\)\s*;", text):
+            ps = [p.strip() for p in params.split(",")]
+            out[name] = [] if ps in ([""], ["void"]) else \
+                [re.sub(r"\bconst\b", "", re.sub(r"\b[A-Za-z_0-9]+$", "", p)).replace(" ", "") for p in ps]
+    return out
+
+
+def _compatible(ctype_decl, ctype):
+    """Whether a ctypes argument type marshals the C parameter type."""
+    scalars = {"int": ctypes.c_int, "double": ctypes.c_double, "unsignedlonglong": ctypes.c_ulonglong}
+    if ctype_decl in scalars:
+        return ctype is scalars[ctype_decl]
+    assert ctype_decl.endswith("*"), ctype_decl
+    pointee = ctype_decl[:-1]
+    if ctype is ctypes.c_void_p:
+        return True  # opaque handles, device buffers
+    if not hasattr(ctype, "_type_") or not issubclass(ctype, ctypes._Pointer):
+        return False
+    target = ctype._type_
+    simple = {"double": ctypes.c_double, "float": ctypes.c_float, "int": ctypes.c_int,
+              "unsignedlonglong": ctypes.c_ulonglong}
+    if pointee in simple:
+        return target is simple[pointee]
+    if pointee.endswith("*"):  # handle out-parameter
+        return target is ctypes.c_void_p
+    return target.__name__ == pointee  # struct pointers: the mirror class of the same name
+
+
+def test_binding_types_match_headers():
+    """Each ctypes argument type marshals the header's parameter type:
+    int/double/unsigned long long exactly, pointers to the same scalar or
+    struct, opaque handles as void pointers."""
+    import paper_1505_03271_gb300 as lb
+    L = lb.load()
+    for name, decl in _declared_param_types().items():
+        for k, (cdecl, ct) in enumerate(zip(decl, getattr(L, name).argtypes or [])):
+            assert _compatible(cdecl, ct), (name, k, cdecl, ct)
