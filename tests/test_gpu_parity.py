@@ -532,6 +532,32 @@ def test_conservation_and_nusselt(lbgpu, oracle):
         assert np.abs(a - b).max() < 1e-14
 
 
+@pytest.mark.parametrize("scheme,sy", [("st", 0), ("fv", 0), ("fv", 1)])
+@pytest.mark.parametrize("store,tol", [("f64", 1e-14), ("f32", 1e-7), ("f16dev", 3e-6)])
+def test_rb_barometric_rest_state(lbgpu, oracle, scheme, sy, store, tol):
+    """The RB preset's barometric conductive start (Sec. IV) without
+    perturbation, beta g dT = 1e-3: the GPU's velocities after 100 ST or 20
+    FV steps match the oracle's, which are O((beta g)^2) in the bulk (the
+    oracle pins fix that), to the storage's rounding: FP64 a few ulps of the
+    O(1e-4) force-shift deviations; FP32 6e-8 and FP16 2.4e-4 of them per
+    step, over 100 steps.  The density profiles agree to rounding."""
+    ny = 24
+    dt = 1.0 if scheme == "st" else 0.1
+    g, r = pair(lbgpu, oracle, 6, ny, store, ly=float(ny), sy=sy, stretch_y=2.0, bcy=1,
+                thermal=True, tau=0.2, tau_g=0.2, dt=dt, beta=1e-3, grav=1.0, T0=1.0, T_bot=1.5,
+                T_top=0.5, kind=3, amp=0.0)
+    rho_g = g.moments()[0]
+    rho_r = r.moments()[0]
+    assert np.abs(rho_g - rho_r).max() < (1e-15 if store == "f64" else 1e-6)
+    n = 100 if scheme == "st" else 20
+    (g.step_st if scheme == "st" else g.step_fv)(n)
+    (r.step_st if scheme == "st" else r.step_fv)(n)
+    _, ux, uy, _ = g.moments()
+    _, vx, vy, _ = r.moments()
+    assert np.abs(ux - vx).max() < tol and np.abs(uy - vy).max() < tol
+    assert np.abs(vy).max() < 2e-4   # oracle: first-order wall kink (FV) at most
+
+
 def test_rb_nusselt_f16_vs_oracle(lbgpu, oracle):
     """Reduced-precision storage: FP16 deviation storage keeps the Nusselt
     numbers within 1e-3 of the FP64 oracle over 500 FV steps of an RB cell."""

@@ -283,6 +283,92 @@ def test_rb_preset_perturbation_is_seeded(oracle):
             assert np.isclose(T[j, i], 1.0 + (0.5 - yc[j] / 6) + 1e-3 * (2 * U - 1), rtol=0, atol=1e-15)
 
 
+def _rb_rest_grid(O, sy, bg, ny=24, dt=1.0, rho="barometric"):
+    """RB cell between plates at T0 -/+ dT/2 (dT = 1), no perturbation; beta g
+    = bg.  rho="uniform" restarts the same conductive T with rho = 1, the
+    start the barometric density exists to replace (Sec. IV)."""
+    g = _grid(O, 3, ny, ly=float(ny), sy=sy, stretch_y=2.0, bcy=1, thermal=True)
+    g.set_params(tau=0.2, dt=dt, tau_g=0.2, beta=bg, grav=1.0, T0=1.0, T_bot=1.5, T_top=0.5)
+    g.init_preset(O.INIT_RB, amp=0.0)
+    if rho == "uniform":
+        r, ux, uy, T = g.moments()
+        g.init_fields(np.ones_like(r), np.zeros_like(ux), np.zeros_like(uy), T)
+    return g
+
+
+@pytest.mark.parametrize("sy", [0, 1])
+def test_rb_barometric_density_solves_hydrostatics(oracle, sy):
+    """The RB preset's density (Sec. IV, barometric equation) is the solution
+    of c_s^2 d(ln rho)/dy = a_y = beta g (T_c - T0) with the conductive
+    T_c = T0 + dT (1/2 - y/H), normalised to sum V rho = sum V.  ln rho is
+    then quadratic in y, so its difference quotient between neighbouring
+    centres equals the ODE's right-hand side at their midpoint exactly.  A
+    sign error, a missing 1/c_s^2 = 3, or the wrong normalisation each fails
+    one assertion; so does an asymmetric profile (rho(y) = rho(H - y))."""
+    ny, bg = 24, 1e-3
+    g = _rb_rest_grid(oracle, sy, bg, ny=ny)
+    rho, ux, uy, T = g.moments()
+    yc = g.centers()[1]
+    assert np.ptp(rho, axis=1).max() == 0.0
+    r = rho[:, 0]
+    ybar = 0.5 * (yc[1:] + yc[:-1])
+    dq = np.diff(np.log(r)) / np.diff(yc)
+    assert np.allclose(dq, 3.0 * bg * (0.5 - ybar / ny), rtol=0, atol=1e-12)
+    assert np.allclose(r, r[::-1], rtol=0, atol=1e-15)
+    assert abs(g.conservation()[0] / (3.0 * ny) - 1.0) < 1e-14
+    assert np.abs(ux).max() < 1e-16 and np.abs(uy).max() < 1e-16
+
+
+def test_rb_barometric_start_is_at_rest_st(oracle):
+    """ST from the barometric conductive state (Sec. IV: the barometric start
+    avoids pressure waves at start-up).  The lattice's hydrostatic balance
+    differs from the continuum one only at second order in beta g, so after
+    100 steps the spurious velocity is O((beta g)^2): ten times weaker beta g
+    leaves it at least 50 times smaller, and it stays 1e4 times below that of
+    the uniform-density start, whose imbalance rho a is first order.  Every
+    Nusselt number stays 1 to the same order."""
+    out = {}
+    for bg in (1e-3, 1e-4):
+        for rho in ("barometric", "uniform"):
+            g = _rb_rest_grid(oracle, 0, bg, rho=rho)
+            g.step_st(100)
+            _, ux, uy, _ = g.moments()
+            out[bg, rho] = (max(np.abs(ux).max(), np.abs(uy).max()), g.nusselt())
+    assert out[1e-3, "barometric"][0] < 3e-8
+    assert out[1e-4, "barometric"][0] < 3e-10
+    assert out[1e-3, "barometric"][0] > 50 * out[1e-4, "barometric"][0]
+    for bg in (1e-3, 1e-4):
+        assert out[bg, "barometric"][0] < 1e-4 * out[bg, "uniform"][0]
+        assert out[bg, "uniform"][0] > 0.5 * bg
+        for nu in out[bg, "barometric"][1]:
+            assert abs(nu - 1.0) < 5.0 * bg * bg
+
+
+@pytest.mark.parametrize("sy", [0, 1])
+def test_rb_barometric_start_is_at_rest_fv_interior(oracle, sy):
+    """FV (Heun) from the barometric conductive state, uniform and tanh
+    plates.  The double-reflection ghosts mirror rho evenly, so the wall
+    cells see a first-order density kink (Sec. II B 5 calls the wall rule
+    first order); one step reaches four rows into the fluid (two QUICK
+    stages of two rows each).  Beyond those rows one step leaves only the
+    O((beta g)^2) residual of QUICK on ln rho quadratic, 1e4 times below the
+    uniform-density start's dt * a."""
+    ny, dt = 24, 0.1
+    res = {}
+    for bg in (1e-3, 1e-4):
+        for rho in ("barometric", "uniform"):
+            g = _rb_rest_grid(oracle, sy, bg, ny=ny, dt=dt, rho=rho)
+            g.step_fv(1)
+            _, ux, uy, _ = g.moments()
+            assert np.abs(ux).max() < 1e-18
+            res[bg, rho] = np.abs(uy[4:ny - 4]).max()
+    assert res[1e-3, "barometric"] < 2e-9
+    assert res[1e-3, "barometric"] > 50 * res[1e-4, "barometric"]
+    for bg in (1e-3, 1e-4):
+        assert res[bg, "barometric"] < 1e-4 * res[bg, "uniform"]
+        assert res[bg, "uniform"] > 0.2 * dt * bg
+
+
 def _golden_rb():
     import os
     path = os.path.join(os.path.dirname(__file__), "golden", "rb_ra1e4.txt")
