@@ -270,9 +270,11 @@ lb_status lb_get_window(lb_grid* grid, int x0, int y0, int w, int h, double* f, 
  * Its scratch is a fixed array inside the library (one per GPU that loads it,
  * held until the process exits), so a call handles at most 8,388,608 cells;
  * larger grids return LB_ERR_ARG.  All calls share that array: calls that
- * overlap on the GPU race and must be serialised.  The first call on a device
- * looks up the array's address with that device current; make it before any
- * stream capture begins.  LB_ERR_ARG on NULL or inconsistent sizes,
+ * overlap on the GPU race and must be serialised.  Every call looks up the
+ * array's address in the calling thread's current context (so a reset device
+ * or a non-primary context uses its own copy); the first call in a context
+ * loads the library's module there, so make it before any stream capture
+ * begins.  LB_ERR_ARG on NULL or inconsistent sizes,
  * LB_ERR_CUDA if the launch fails. */
 lb_status lb_conservation_noalloc(const float* f, const float* g, int nx, int ny, int pitch,
                                   const double* dx, const double* dy, double dt, double ax,

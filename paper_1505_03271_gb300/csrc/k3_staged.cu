@@ -355,12 +355,9 @@ template <typename R, typename S, bool CORR>
 cudaError_t run_staged(const Args3<R>& A, int np, cudaStream_t s) {
     const Shape sh = staged_shape(A.n[0], A.n[2], sizeof(R), A.sshape[0], A.sshape[1], A.sshape[2]);
     if (sh.bytes > kMaxSmem) return cudaErrorInvalidValue;
-    static bool configured = false;  // attribute is per function, set once
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k3_adv_staged<R, S, CORR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kMaxSmem);
+    {
+        cudaError_t e = set_max_smem((const void*)k3_adv_staged<R, S, CORR>, kMaxSmem);
         if (e != cudaSuccess) return e;
-        configured = true;
     }
     const dim3 g((A.n[1] + sh.ty - 1) / sh.ty, (A.n[2] + sh.kc - 1) / sh.kc, np);
     k3_adv_staged<R, S, CORR><<<g, kThreads + 32, sh.bytes, s>>>(A, sh);

@@ -307,12 +307,9 @@ static cudaError_t run_fv_batched(const void* reqs, const int4* tiles, const int
                                   cudaStream_t s) {
     constexpr int NQ = TH ? 2 * Q : Q;
     constexpr size_t smem = sizeof(R) * (size_t)NQ * ((TX + 8) * (TY + 8) + 2 * (TX + 4) * (TY + 4));
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_fv_batched<R, S, TH, TX, TY>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+        cudaError_t e = set_max_smem((const void*)k_fv_batched<R, S, TH, TX, TY>, (int)smem);
         if (e != cudaSuccess) return e;
-        configured = true;
     }
     k_fv_batched<R, S, TH, TX, TY><<<capacity, kFvThreads, smem, s>>>(static_cast<const BatchReq<R>*>(reqs),
                                                                       tiles, ntiles, k);
@@ -350,12 +347,9 @@ static cudaError_t run_fv(const void* vargs, cudaStream_t s) {
     constexpr int NQ = TH ? 2 * Q : Q;
     constexpr size_t smem = sizeof(R) * (size_t)NQ * ((TX + 8) * (TY + 8) + 2 * (TX + 4) * (TY + 4));
     static_assert(smem <= 232448, "shared memory per CTA");
-    static bool configured = false;  // attribute is per function, set once
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_fv<R, S, TH, TX, TY>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+        cudaError_t e = set_max_smem((const void*)k_fv<R, S, TH, TX, TY>, (int)smem);
         if (e != cudaSuccess) return e;
-        configured = true;
     }
     dim3 grid((A.nx + TX - 1) / TX, (A.ny + TY - 1) / TY);
     k_fv<R, S, TH, TX, TY><<<grid, kFvThreads, smem, s>>>(A);

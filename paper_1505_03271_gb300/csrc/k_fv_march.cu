@@ -295,12 +295,9 @@ static cudaError_t run_march(const void* vargs, int chunk, cudaStream_t s) {
     constexpr int NQ = TH ? 2 * Q : Q;
     constexpr size_t smem = sizeof(R) * 15 * NQ * NT;
     static_assert(smem <= 232448, "shared memory per CTA");
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_fv_march<R, S, TH, NT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+        cudaError_t e = set_max_smem((const void*)k_fv_march<R, S, TH, NT>, (int)smem);
         if (e != cudaSuccess) return e;
-        configured = true;
     }
     const int ch = chunk < 8 ? 8 : chunk;
     dim3 grid((A.nx + (NT - 8) - 1) / (NT - 8), (A.ny + ch - 1) / ch);

@@ -762,15 +762,10 @@ static cudaError_t run_split(const void* vargs, cudaStream_t s) {
     constexpr size_t smem_a = sizeof(V2) * NQ * (((TX + 4) / 2) * (TY + 4) + (TX / 2) * TY);
     constexpr size_t smem_c = sizeof(V2) * NQ * ((TX + 4) / 2) * (TY + 4);
     static_assert(smem_a <= 232448, "shared memory per CTA");
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_fv_split_a<S, TH, TX, TY, NTH>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_a);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_fv_split_c<S, TH, TX, TY, NTH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem_c);
+    {
+        cudaError_t e = set_max_smem((const void*)k_fv_split_a<S, TH, TX, TY, NTH>, (int)smem_a);
+        if (e == cudaSuccess) e = set_max_smem((const void*)k_fv_split_c<S, TH, TX, TY, NTH>, (int)smem_c);
         if (e != cudaSuccess) return e;
-        configured = true;
     }
     dim3 grid((A.nx + TX - 1) / TX, (A.ny + TY - 1) / TY);
     k_fv_split_a<S, TH, TX, TY, NTH><<<grid, NTH, smem_a, s>>>(A);
@@ -827,12 +822,9 @@ static cudaError_t run_ptile_batched(const void* reqs, const int4* tiles, const 
     constexpr int NQ = TH ? 2 * Q : Q;
     constexpr int NTH = TH ? 512 : 256;
     constexpr size_t smem = sizeof(V2) * NQ * (((32 + 8) / 2) * (16 + 8) + 2 * ((32 + 4) / 2) * (16 + 4));
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_fv_ptile_batched<S, TH, 32, 16, NTH>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+        cudaError_t e = set_max_smem((const void*)k_fv_ptile_batched<S, TH, 32, 16, NTH>, (int)smem);
         if (e != cudaSuccess) return e;
-        configured = true;
     }
     k_fv_ptile_batched<S, TH, 32, 16, NTH><<<capacity, NTH, smem, s>>>(static_cast<const BatchReq<float>*>(reqs),
                                                                       tiles, ntiles, k);
@@ -862,12 +854,9 @@ static cudaError_t run_ptile(const void* vargs, cudaStream_t s) {
     constexpr int NQ = TH ? 2 * Q : Q;
     constexpr size_t smem = sizeof(V2) * NQ * (((TX + 8) / 2) * (TY + 8) + 2 * ((TX + 4) / 2) * (TY + 4));
     static_assert(smem <= 232448, "shared memory per CTA");
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_fv_ptile<S, TH, TX, TY, NTH, MINB>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    {
+        cudaError_t e = set_max_smem((const void*)k_fv_ptile<S, TH, TX, TY, NTH, MINB>, (int)smem);
         if (e != cudaSuccess) return e;
-        configured = true;
     }
     dim3 grid((A.nx + TX - 1) / TX, (A.ny + TY - 1) / TY);
     k_fv_ptile<S, TH, TX, TY, NTH, MINB><<<grid, NTH, smem, s>>>(A);
@@ -907,12 +896,9 @@ static cudaError_t run_pair(const void* vargs, int chunk, cudaStream_t s) {
     constexpr int NQ = TH ? 2 * Q : Q;
     constexpr size_t smem = sizeof(V2) * (2 * ring_off(NQ) + 5 * NQ) * NT;
     static_assert(smem <= 232448, "shared memory per CTA");
-    static bool configured = false;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_fv_pair<S, TH, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem);
+    {
+        cudaError_t e = set_max_smem((const void*)k_fv_pair<S, TH, NT>, (int)smem);
         if (e != cudaSuccess) return e;
-        configured = true;
     }
     const int ch = chunk < 8 ? 8 : chunk;
     constexpr int W = 2 * NT - 8;

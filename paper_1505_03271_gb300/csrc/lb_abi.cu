@@ -6,7 +6,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
+#include <set>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "lb_grid.cuh"
@@ -45,6 +48,18 @@ namespace lbgb {
 void count_launch() {
     if (t_captured) ++*t_captured;
     else g_launches.fetch_add(1, std::memory_order_relaxed);
+}
+cudaError_t set_max_smem(const void* fn, int bytes) {
+    static std::mutex mu;
+    static std::set<std::tuple<int, const void*, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count({dev, fn, bytes})) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.insert({dev, fn, bytes});
+    return e;
 }
 // Record a failure message for lb_last_error() from another translation unit.
 lb_status set_last_error(lb_status s, const char* msg) { return fail(s, "%s", msg); }

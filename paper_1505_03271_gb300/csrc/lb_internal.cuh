@@ -270,4 +270,9 @@ struct InitArgs {
 cudaError_t launch_init(Prec p, bool thermal, const InitArgs& a, cudaStream_t s);
 
 void count_launch();
+
+// Raise a kernel's dynamic shared-memory limit to `bytes` on the current
+// device.  The attribute belongs to the function in each device's context, so
+// it is set once per (device, function) under a lock; safe from any thread.
+cudaError_t set_max_smem(const void* fn, int bytes);
 }  // namespace lbgb

@@ -19,10 +19,11 @@
 //   - Every call uses the same array.  Calls whose work overlaps on the GPU
 //     (different streams, or different host threads on the same device)
 //     race on it and give wrong sums; serialise them.
-//   - The first call on a device looks up the array's device address
-//     (cudaGetSymbolAddress) with that device current; make that first call
-//     before any stream capture begins.
-#include <mutex>
+//   - Every call looks up the array's device address (cudaGetSymbolAddress)
+//     in the context current on the calling thread, so a device that was
+//     reset, or a non-primary context, gets the address of its own copy.
+//     The first call in a context loads the library's module there; make
+//     that first call before any stream capture begins.
 
 #include "lb_internal.cuh"
 
@@ -44,10 +45,6 @@ constexpr int kCounter = kSums * kMaxBlocks;  // slot of the completion counter
 // Partial sums [kSums][kMaxBlocks] followed by the completion counter
 // (4 * 4096 * 8 B + 256 B = 128.25 KiB per device).
 static __device__ __align__(256) double g_scratch[kSums * kMaxBlocks + 32];
-
-constexpr int kMaxDevices = 64;
-double* g_scratch_addr[kMaxDevices] = {};
-std::mutex g_setup_mutex;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -140,22 +137,16 @@ k_conservation_noalloc(const float* f, const float* g, int nx, int ny, int pitch
     }
 }
 
-// Device address of g_scratch on the current device, looked up once per
-// device (the first call on a device does it).
+// Device address of g_scratch in the current context.  The lookup is a
+// symbol-table query once the module is loaded, so it is repeated on every
+// call rather than cached: a cached address would be stale after
+// cudaDeviceReset or under another context of the same device.
 lb_status scratch_address(double** ptr) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return lbgb::set_last_error(LB_ERR_CUDA, cudaGetErrorString(e));
-    if (dev < 0 || dev >= kMaxDevices) return lbgb::set_last_error(LB_ERR_ARG, "device index out of range");
-    std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
-        void* p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess || !p)
-            return lbgb::set_last_error(LB_ERR_CUDA, "cudaGetSymbolAddress of the no-alloc scratch failed");
-        g_scratch_addr[dev] = static_cast<double*>(p);
-    }
-    *ptr = g_scratch_addr[dev];
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess || !p)
+        return lbgb::set_last_error(LB_ERR_CUDA, "cudaGetSymbolAddress of the no-alloc scratch failed");
+    *ptr = static_cast<double*>(p);
     return LB_OK;
 }
 

@@ -255,7 +255,8 @@ lb_status lb_server_pump(lb_server* S, int* n_active, int* n_pending) {
         const Pending& p = S->pending.front();
         const size_t need = grid_bytes(p.req.grid);
         size_t free_b = 0, total_b = 0;
-        cudaMemGetInfo(&free_b, &total_b);
+        cudaError_t me = cudaMemGetInfo(&free_b, &total_b);
+        if (me != cudaSuccess) return fail(LB_ERR_CUDA, std::string("server admission: ") + cudaGetErrorString(me));
         if (S->used + need > S->budget || need + (64u << 20) > free_b) break;
         Active a;
         a.req = p.req;
@@ -342,9 +343,14 @@ lb_status lb_server_pump(lb_server* S, int* n_active, int* n_pending) {
                 for (int x = 0; x < nbx; ++x) S->h_tiles[b++] = make_int4(i, x, y, 0);
         }
         *S->h_ntiles = ntiles;
-        cudaMemcpyAsync(S->d_reqs, S->h_reqs, req_size(S->prec) * S->active.size(), cudaMemcpyHostToDevice, S->stream);
-        cudaMemcpyAsync(S->d_tiles, S->h_tiles, sizeof(int4) * ntiles, cudaMemcpyHostToDevice, S->stream);
-        cudaMemcpyAsync(S->d_ntiles, S->h_ntiles, sizeof(int), cudaMemcpyHostToDevice, S->stream);
+        // a failed upload would leave the previous pump's tables in place: stop before stepping
+        cudaError_t ue = cudaMemcpyAsync(S->d_reqs, S->h_reqs, req_size(S->prec) * S->active.size(),
+                                         cudaMemcpyHostToDevice, S->stream);
+        if (ue == cudaSuccess)
+            ue = cudaMemcpyAsync(S->d_tiles, S->h_tiles, sizeof(int4) * ntiles, cudaMemcpyHostToDevice, S->stream);
+        if (ue == cudaSuccess)
+            ue = cudaMemcpyAsync(S->d_ntiles, S->h_ntiles, sizeof(int), cudaMemcpyHostToDevice, S->stream);
+        if (ue != cudaSuccess) return fail(LB_ERR_CUDA, std::string("server table upload: ") + cudaGetErrorString(ue));
         st = run_batch(S);
         if (st != LB_OK) return st;
         cudaError_t e = cudaStreamSynchronize(S->stream);

@@ -74,3 +74,41 @@ def test_noalloc_flow_only_and_size_limit(lbgpu):
                                    one_y.data_ptr(), 1.0, 0.0, 0.0, 0.0, 1.0, out.data_ptr(), stream)
     assert e.value.status == lb.LB_ERR_ARG
     assert "8388608" in lb.lb_last_error()
+
+
+def test_noalloc_stretched_grid_volume_weights(lbgpu, oracle):
+    """A tanh-refined y axis and a sinh-refined x axis with nx != ny: the
+    volume weight V = dx[i] * dy[j] varies along both axes, so a swapped or
+    mis-indexed width changes every sum.  The cell widths are the grid's own
+    (Eq. (grids)), passed as device FP64 arrays; the state is random fields
+    stepped twice, so mass, momentum and heat all vary from cell to cell."""
+    import torch
+    from tests import inputs
+    lb = lbgpu
+    nx, ny = 96, 70
+    T0 = 1.0
+    g = lb.Grid(nx, ny, sx=lb.LB_AXIS_SINH, sy=lb.LB_AXIS_TANH, stretch_x=3.0, stretch_y=2.0,
+                thermal=True, store="f32")
+    params = dict(tau=0.2, dt=0.05, tau_g=0.2, ax=1e-5, ay=-2e-6, beta=1e-3, grav=1.0, T0=T0)
+    rho, ux, uy, T = inputs.random_fields(nx, ny, seed=21, T_amp=0.05, T0=T0)
+    g.init(rho=rho, ux=ux, uy=uy, T=T, **params)
+    g.step_fv(2)
+    ref = np.array(g.conservation())
+    f, gg = g.get_pops()
+    fd = _device_copy(torch, f, 1.0, nx, ny, nx)
+    gd = _device_copy(torch, gg, T0, nx, ny, nx)
+    wx = np.diff(oracle.faces(nx, float(nx), oracle.SINH, 3.0))
+    wy = np.diff(oracle.faces(ny, float(ny), oracle.TANH, 2.0))
+    assert np.ptp(wx) > 0.1 and np.ptp(wy) > 0.1
+    dx = torch.from_numpy(wx).cuda()
+    dy = torch.from_numpy(wy).cuda()
+    out = torch.empty(4, dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    for _ in range(2):
+        out.fill_(float("nan"))
+        lb.lb_conservation_noalloc(fd.data_ptr(), gd.data_ptr(), nx, ny, nx, dx.data_ptr(),
+                                   dy.data_ptr(), params["dt"], params["ax"], params["ay"],
+                                   params["beta"] * params["grav"], T0, out.data_ptr(), stream)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy()
+        assert np.all(np.abs(got - ref) <= 1e-12 * np.abs(ref) + 1e-15), (got, ref)
