@@ -310,6 +310,7 @@ int ref_init_fields(ref_grid* G, const double* rho, const double* ux, const doub
                     const double* T) {
     if (!G || !G->has_params) return -1;
     const ref_params* p = &G->p;
+#pragma omp parallel for schedule(static)
     for (int j = 0; j < G->ny; ++j)
         for (int i = 0; i < G->nx; ++i) {
             size_t c = (size_t)j * G->nx + i;
@@ -347,6 +348,8 @@ int ref_init_preset(ref_grid* G, int kind, double u0, double amp, int mode,
     const double PI = 3.14159265358979323846;
     int rc = 0;
     if (kind == REF_INIT_RB && !G->d.thermal) rc = -1;
+    if (kind != REF_INIT_TGV && kind != REF_INIT_SHEAR && kind != REF_INIT_POISEUILLE && kind != REF_INIT_RB)
+        rc = -1;
     /* barometric density of the conductive state (Sec. IV): c_s^2 d(rho)/dy =
      * rho * beta g (T_c - T0), normalised so that sum V rho = sum V. */
     double dT = p->T_bot - p->T_top;
@@ -359,7 +362,9 @@ int ref_init_preset(ref_grid* G, int kind, double u0, double amp, int mode,
         }
         norm = Ly / s;
     }
-    for (int j = 0; j < ny && rc == 0; ++j)
+    const int rows = rc == 0 ? ny : 0; /* nothing to fill for a rejected kind */
+#pragma omp parallel for schedule(static)
+    for (int j = 0; j < rows; ++j)
         for (int i = 0; i < nx; ++i) {
             size_t c = (size_t)j * nx + i;
             double x = G->xc[i], y = G->yc[j];
@@ -379,8 +384,6 @@ int ref_init_preset(ref_grid* G, int kind, double u0, double amp, int mode,
                 double U = ref_splitmix_uniform(seed, (unsigned long long)c);
                 T[c] = p->T0 + dT * (0.5 - y / Ly) + amp * dT * (2.0 * U - 1.0);
                 rho[c] = norm * exp(3.0 * p->beta * p->grav * dT * (0.5 * y - 0.5 * y * y / Ly));
-            } else {
-                rc = -1;
             }
         }
     if (rc == 0) rc = ref_init_fields(G, rho, ux, uy, T);
@@ -716,6 +719,7 @@ int ref_step_fv(ref_grid* G, int nsteps) {
 /* Cell moments rho, force-corrected u and T (Sec. II B 4, Eq. (LBg)). */
 int ref_moments(const ref_grid* G, double* rho, double* ux, double* uy, double* T) {
     if (!G || !G->has_params) return -1;
+#pragma omp parallel for schedule(static)
     for (int j = 0; j < G->ny; ++j)
         for (int i = 0; i < G->nx; ++i) {
             double fc[Q], gc[Q];
