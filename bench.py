@@ -1,16 +1,22 @@
 """Benchmark of the lattice Boltzmann time step on GB300.
 
-Default workload: the FV body-force channel, 256 x 512 cells, tanh wall
-refinement (delta = 2) on y, FP32 arithmetic on f - w storage, Re = 10.
-One bench step = one FV time step (one fused kernel launch).  The state is
-9.4 MB, far below the 129 MB L2, so a 256 MiB buffer is written between timed
-steps and each step is timed alone with CUDA events on the launching stream.
+Headline workload (config 4, the largest single-GPU configuration): the ST
+step on an 8192 x 8192 periodic D2Q9 grid (Taylor-Green mode 1 plus a mode-2
+shear wave), FP32 storage and arithmetic.  One bench step = one ST time step
+(one kernel launch), timed alone with CUDA events on the launching stream;
+the state (9.7 GB) is far larger than the 129 MB L2, so no flush is needed.
+The line carries the HBM roofline of that kernel, the FP64 oracle timed on
+this host's cores over a fixed 10-step window (and its error against the
+GPU after the same window), and the end-to-end figure through the C ABI
+(host fields in, the config's 500 steps, u_x out).
 
-Extra lines in the same JSON object (not the headline): ST on 8192^2 (FP32,
-BF16 and FP16 deviation storage; state larger than L2), FV on 4096^2 FP32 and
-FV thermal RB 1024^2 with FP16 storage.
+Extra lines in the same JSON object: the serving stream; ST 8192^2 with BF16
+and FP16 deviation storage; FV 4096^2; FV RB 1024^2 FP32; the 3-D Table rb
+grids; and, as full lines with their own roofline, oracle baseline, oracle
+error and end-to-end figure, config 2 (the FV channel 256 x 512) and config
+3 (FV thermal RB 1024^2 at Ra = 1e8 with FP16 deviation storage).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--case NAME]
 """
 from __future__ import annotations
 
@@ -241,35 +247,84 @@ def alu_roofline(cfg, w, mean_ms, clocks):
             "peak_source": "%d SMs x 128 FP32 lanes x 2 x %.0f MHz (derived)" % (sms, mhz)}
 
 
-def extra_lines(lb, torch, cfg, stream, peak, peak_kind, flush):
+STORE_LABEL = {0: "FP64", 1: "FP32", 2: "FP16 (f - w) deviations", 3: "BF16 (f - w) deviations"}
+
+
+def state_bytes(cfg, w):
+    """Device bytes of a grid's two population buffers."""
+    return cfg.bytes_per_cell(w.grid["store"], w.grid.get("thermal", False),
+                              19 if "nz" in w.grid else 9) * w.cells
+
+
+def needs_flush(cfg, w):
+    """L2 is flushed between timed steps unless the state is larger than
+    four times the 129 MB L2."""
+    return state_bytes(cfg, w) < 4 * 129e6
+
+
+def measure(lb, torch, cfg, w, stream, peak, peak_kind, flush, steps, warmup, case):
+    """Time `steps` single-step launches of a workload (after warm-up, L2
+    flushed before each when the state is small).  Returns the grid (its
+    schedule is the autotuner's) and the figures of its line."""
+    g = make_grid(lb, w, stream)
+    fl = flush if needs_flush(cfg, w) else None
+    ms, launches = time_steps(lb, torch, g, w.scheme, steps, warmup, fl)
+    mean = sum(ms) / len(ms)
+    bpc = cfg.bytes_per_cell(w.grid["store"], w.grid.get("thermal", False), 19 if "nz" in w.grid else 9)
+    sched = schedule_name(lb, g, w.scheme)
+    tcase, scale = case if isinstance(case, tuple) else (case, 1)
+    traffic = measured_traffic(sched, tcase) if tcase else None
+    rl = roofline(bpc * w.cells, mean, peak, peak_kind, traffic * scale if traffic else None)
+    if traffic and scale != 1:
+        rl["traffic_source"] = "ncu on the %s case, scaled x%d by cells" % (tcase, scale)
+    return g, {"mlups": round(w.cells / (mean * 1e-3) / 1e6, 1), "ms_per_step": round(mean, 5),
+               "bytes_per_cell": bpc, "schedule": sched, "launches": launches, "roofline": rl,
+               "roofline_alu": None if "nz" in w.grid else alu_roofline(cfg, w, mean, None),
+               "l2": "flushed" if fl is not None else "state > L2"}
+
+
+def compact(m):
+    """One extra line in few characters: throughput, both roof fractions,
+    the schedule and the ncu traffic when it is current."""
+    out = {"mlups": m["mlups"], "ms_per_step": m["ms_per_step"], "frac_hbm": m["roofline"]["frac"],
+           "bytes_per_cell": m["bytes_per_cell"], "schedule": m["schedule"]}
+    if m["roofline"]["traffic"]:
+        out["traffic"] = m["roofline"]["traffic"]
+    if m.get("roofline_alu"):
+        out["frac_alu"] = m["roofline_alu"]["frac"]
+    return out
+
+
+def extra_lines(lb, torch, cfg, stream, peak, peak_kind, flush, serving=None, cpu=True):
+    """The other workloads.  The compact lines first; then config 2 (the FV
+    channel) and config 3 (the FV thermal RB cell, the paper's Sec. IV
+    workload) as full lines with their own roofline, oracle baseline,
+    oracle error and end-to-end figure, config 3 last."""
     out = {}
-    # (name, workload, steps, flush, traffic case); the 8192^2 ST traffic is
-    # the ncu capture of 4096^2 scaled by the cell count (ST moves every
-    # cell's populations once, so its DRAM bytes grow with the cells)
-    specs = [("st8192_f32", cfg.st_sweep(8192, lb.LB_STORE_F32), 20, None, ("st4096", 4)),
-             ("st8192_bf16dev", cfg.st_sweep(8192, lb.LB_STORE_BF16DEV), 20, None, None),
-             ("st8192_f16dev", cfg.st_sweep(8192, lb.LB_STORE_F16DEV), 20, None, ("st4096_f16dev", 4)),
-             ("fv4096_f32", _fv_big(cfg, 4096), 10, None, None),
-             ("fv_rb1024_f16dev", cfg.rayleigh_benard(1024, 1e8), 20, flush, "rb1024"),
-             ("fv_rb1024_f32", cfg.rayleigh_benard(1024, 1e8, store=lb.LB_STORE_F32), 20, flush, None),
-             ("rb3d_fv_f32", cfg.rb3d_table("fv"), 10, None, "rb3d_fv"),
-             ("rb3d_st_f32", cfg.rb3d_table("st"), 20, None, "rb3d_st")]
-    for name, w, k, fl, case in specs:
-        g = make_grid(lb, w, stream)
-        ms, _ = time_steps(lb, torch, g, w.scheme, k, 3, fl)
-        mean = sum(ms) / len(ms)
-        bpc = cfg.bytes_per_cell(w.grid["store"], w.grid.get("thermal", False), 19 if "nz" in w.grid else 9)
-        sched = schedule_name(lb, g, w.scheme)
-        case, scale = case if isinstance(case, tuple) else (case, 1)
-        traffic = measured_traffic(sched, case) if case else None
-        rl = roofline(bpc * w.cells, mean, peak, peak_kind, traffic * scale if traffic else None)
-        if traffic and scale != 1:
-            rl["traffic_source"] = "ncu on the %s case, scaled x%d by cells" % (case, scale)
-        out[name] = {"mlups": round(w.cells / (mean * 1e-3) / 1e6, 1), "ms_per_step": round(mean, 5),
-                     "bytes_per_cell": bpc, "schedule": sched,
-                     "roofline": rl,
-                     "roofline_alu": None if "nz" in w.grid else alu_roofline(cfg, w, mean, None),
-                     "cells": w.cells, "l2": "flushed" if fl is not None else "state > L2"}
+    if serving is not None:
+        out["serving"] = serving
+    specs = [("st8192_bf16dev", cfg.st_sweep(8192, lb.LB_STORE_BF16DEV), 20, None),
+             ("st8192_f16dev", cfg.st_sweep(8192, lb.LB_STORE_F16DEV), 20, ("st4096_f16dev", 4)),
+             ("fv4096_f32", _fv_big(cfg, 4096), 10, "fv4096"),
+             ("fv_rb1024_f32", cfg.rayleigh_benard(1024, 1e8, store=lb.LB_STORE_F32), 20, "rb1024"),
+             ("rb3d_fv_f32", cfg.rb3d_table("fv"), 10, "rb3d_fv"),
+             ("rb3d_st_f32", cfg.rb3d_table("st"), 20, "rb3d_st")]
+    for name, w, k, case in specs:
+        g, m = measure(lb, torch, cfg, w, stream, peak, peak_kind, flush, k, 3, case)
+        out[name] = compact(m)
+        g.close()
+        torch.cuda.empty_cache()
+    for name, w, k, case, window, single, inner in (
+            ("channel_f32", cfg.channel(), 200, "channel", 500, 50, 1000),
+            ("fv_rb1024_f16dev", cfg.rayleigh_benard(1024, 1e8), 20, "rb1024", 20, 2, 2000)):
+        g, m = measure(lb, torch, cfg, w, stream, peak, peak_kind, flush, k, 3, case)
+        line = {"workload": describe(w), "mlups": m["mlups"], "ms_per_step": m["ms_per_step"],
+                "schedule": m["schedule"], "l2": m["l2"], "roofline": m["roofline"],
+                "roofline_alu": m["roofline_alu"]}
+        line["e2e"] = e2e_measure(lb, torch, w, stream, g.fv_schedule(), inner)
+        if cpu:
+            line["cpu_baseline"], line["oracle_error"] = cpu_leg(lb, w, stream, g, window, single)
+        out[name] = line
         g.close()
         torch.cuda.empty_cache()
     return out
@@ -327,46 +382,51 @@ def serving_measure(lb, torch, count=120, rate=25.0):
             "max_abs_nu_vol_diff_server_vs_sequential": max(diffs) if diffs else None}
 
 
-def e2e_measure(lb, torch, w, stream, reps=3, inner=1000):
-    """Through the public API with host buffers: per iteration, upload rho, ux,
-    uy from pinned host memory (lb_init FIELDS), advance `inner` FV steps,
-    read u_x back to host (lb_moments)."""
+def e2e_measure(lb, torch, w, stream, fv_schedule=None, inner=None, reps=2):
+    """The same metric end to end through the public API, host buffers in and
+    out.  Per iteration: lb_init from pinned host fields (rho, u_x, u_y, and
+    T for a thermal grid), `inner` steps in one lb_step call (long runs
+    replay a captured CUDA graph), then u_x (and the Nusselt numbers of a
+    thermal grid) read back to host.  The fields are the workload's own
+    initial state, read once from the GPU before timing."""
+    inner = inner or w.steps
     nx, ny = w.grid["nx"], w.grid["ny"]
+    thermal = bool(w.grid.get("thermal", False))
     grid = dict(w.grid)
     store = grid.pop("store")
     g = lb.Grid(store=store, stream=stream, **grid)
+    g.init(**w.params, **w.init)
+    if fv_schedule is not None and w.scheme == "fv":
+        g.set_fv_schedule(*fv_schedule)
     pin = lambda: torch.empty((ny, nx), dtype=torch.float64, pin_memory=True).numpy()
-    rho, ux, uy, out = pin(), pin(), pin(), pin()
-    from paper_1505_03271_gb300 import configs as cfg
-    xi = cfg.faces(ny, w.grid["ly"], w.grid["sy"], w.grid["stretch_y"])
-    yc = 0.5 * (xi[1:] + xi[:-1])
-    rho[:] = 1.0
-    ux[:] = (4 * w.init["u0"] * yc * (w.grid["ly"] - yc) / w.grid["ly"] ** 2)[:, None]
-    uy[:] = 0.0
-
-    def timed(graph_steps):
-        g.set_graph_steps(graph_steps)
-        times = []
-        for r in range(reps + 1):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            g.init(**w.params, kind=lb.LB_INIT_FIELDS, rho=rho, ux=ux, uy=uy)
-            lb.lb_step_fv(g.handle, inner)
-            lb.lb_moments(g.handle, None, out, None, None)
-            t1 = time.perf_counter()
-            if r > 0:
-                times.append(t1 - t0)
-        return round(w.cells * inner / min(times) / 1e6, 1)
-
-    plain = timed(0)
-    graph_steps = 32
-    v = timed(graph_steps)
+    rho, ux, uy, T, out = pin(), pin(), pin(), pin(), pin()
+    lb.lb_moments(g.handle, rho, ux, uy, T if thermal else None)
+    step = lb.lb_step_fv if w.scheme == "fv" else lb.lb_step_st
+    times = []
+    for r in range(reps + 1):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        g.init(**w.params, kind=lb.LB_INIT_FIELDS, rho=rho, ux=ux, uy=uy, T=T if thermal else None)
+        step(g.handle, inner)
+        lb.lb_moments(g.handle, None, out, None, None)
+        if thermal:
+            g.nusselt()
+        t1 = time.perf_counter()
+        if r > 0:
+            times.append(t1 - t0)
     g.close()
-    return {"value": v, "unit": "MLUPS",
-            "h2d_bytes_per_step": 3 * 8 * nx * ny, "d2h_bytes_per_step": 8 * nx * ny,
-            "lb_steps_per_step": inner, "graph_steps": graph_steps, "value_plain_launches": plain,
-            "note": "step = lb_init from pinned host rho,ux,uy + %d FV steps (replays of a %d-step "
-                    "CUDA graph) + u_x to host" % (inner, graph_steps)}
+    fields = 4 if thermal else 3
+    l2 = "state stays in the 129 MB L2 across the run" if state_bytes_of(w) < 129e6 else "state > L2"
+    return {"value": round(w.cells * inner / (sum(times) / len(times)) / 1e6, 1), "unit": "MLUPS",
+            "h2d_bytes_per_step": fields * 8 * nx * ny, "d2h_bytes_per_step": 8 * nx * ny + (24 if thermal else 0),
+            "lb_steps_per_step": inner,
+            "note": "step = lb_init from %d pinned host fields + %d %s steps in one call (CUDA-graph replays) + "
+                    "u_x%s to host; %s" % (fields, inner, w.scheme.upper(), " and Nu" if thermal else "", l2)}
+
+
+def state_bytes_of(w):
+    from paper_1505_03271_gb300 import configs as cfg
+    return state_bytes(cfg, w)
 
 
 # ------------------------------------------------------------------ oracle --
@@ -392,10 +452,12 @@ def cpu_model():
     return platform.machine()
 
 
-def oracle_sample(w, budget_s=15.0, steps_cap=None, threads=None):
-    """Oracle FV/ST steps on the workload for about budget_s seconds, on
-    `threads` OpenMP threads (default: every host core)."""
+def oracle_window(w, steps, threads=None):
+    """Oracle steps of a workload from its initial state: exactly `steps`
+    steps (a fixed window) on `threads` OpenMP threads (default: every host
+    core).  Returns the grid, the seconds the steps took and the threads."""
     import oracle as O
+    O.build()
     threads = threads or os.cpu_count() or 1
     O.set_threads(threads)
     grid = dict(w.grid)
@@ -408,76 +470,136 @@ def oracle_sample(w, budget_s=15.0, steps_cap=None, threads=None):
     r.init_preset(kind, w.init.get("u0", 0.0), w.init.get("amp", 0.0), w.init.get("mode", 1),
                   w.init.get("seed", 0))
     step = r.step_fv if w.scheme == "fv" else r.step_st
+    t0 = time.perf_counter()
+    step(steps)
+    return r, time.perf_counter() - t0, threads
+
+
+def oracle_sample(w, budget_s=15.0, steps_cap=None, threads=None):
+    """Oracle steps for about budget_s seconds (one step at a time)."""
+    r, _, threads = oracle_window(w, 0, threads)
+    step = r.step_fv if w.scheme == "fv" else r.step_st
     done, t0 = 0, time.perf_counter()
     while time.perf_counter() - t0 < budget_s and (steps_cap is None or done < steps_cap):
         step(1)
         done += 1
-    el = time.perf_counter() - t0
-    return r, done, el, threads
+    return r, done, time.perf_counter() - t0, threads
+
+
+def cpu_leg(lb, w, stream, g, window, single):
+    """The oracle timed on this host's cores over a fixed window of the
+    workload (`window` steps on every core, `single` steps on one thread),
+    and the GPU's error against it after the same window: relative L2 of u,
+    and for a thermal grid the largest relative Nusselt-number error."""
+    r, el, thr = oracle_window(w, window)
+    _, el1, _ = oracle_window(w, single, threads=1)
+    grid = dict(w.grid)
+    store = grid.pop("store")
+    g2 = lb.Grid(store=store, stream=stream, **grid)
+    g2.init(**w.params, **w.init)
+    if w.scheme == "fv":
+        g2.set_fv_schedule(*g.fv_schedule())
+        lb.lb_step_fv(g2.handle, window)
+    else:
+        lb.lb_step_st(g2.handle, window)
+    _, ux, uy, _ = g2.moments()
+    _, vx, vy, _ = r.moments()
+    err = {"steps": window,
+           "rel_l2_u": float(np.sqrt(((ux - vx) ** 2 + (uy - vy) ** 2).sum() / (vx**2 + vy**2).sum()))}
+    if w.grid.get("thermal"):
+        err["nu_rel_err"] = float(max(abs(a / b - 1.0) for a, b in zip(g2.nusselt(), r.nusselt())))
+    g2.close()
+    base = {"value": round(w.cells * window / el / 1e6, 3), "unit": "MLUPS", "cores": thr, "kind": "oracle",
+            "sample": "%d %s steps of the full %dx%d grid (%.1f s)" % (window, w.scheme.upper(), w.grid["nx"],
+                                                                      w.grid["ny"], el),
+            "cpu_model": cpu_model(),
+            "single_thread": {"value": round(w.cells * single / el1 / 1e6, 3),
+                              "sample": "%d steps, full grid (%.1f s)" % (single, el1)}}
+    return base, err
 
 
 def run_reference(args):
+    """The reference arm of this tier: the FP64 oracle, as it stands, on the
+    headline workload and this host's cores.  One reference step is one
+    oracle step of the full grid."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     from paper_1505_03271_gb300 import configs as cfg
-    w = cfg.channel()
-    import oracle as O
-    O.build()
-    O.set_threads(os.cpu_count() or 1)
-    grid = dict(w.grid)
-    grid.pop("store")
-    r = O.RefGrid(grid["nx"], grid["ny"], grid["lx"], grid["ly"], 0, grid["sy"], 0.0,
-                  grid["stretch_y"], 0, grid["bcy"], False)
-    r.set_params(**w.params)
-    r.init_preset(O.INIT_POISEUILLE, w.init["u0"])
-    # each reference step: one oracle FV step of the full channel
+    w = case_workload(cfg, args.case)
+    r, _, thr = oracle_window(w, 0)
+    step = r.step_fv if w.scheme == "fv" else r.step_st
     for _ in range(args.warmup):
-        r.step_fv(1)
+        step(1)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        r.step_fv(1)
+        step(1)
     el = time.perf_counter() - t0
     v = w.cells * args.steps / el / 1e6
     line = {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": "MLUPS",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": round(el / args.steps * 1e3, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": _config(w),
-            "cpu_baseline": {"value": round(v, 3), "unit": "MLUPS", "cores": O.get_threads(),
-                             "kind": "oracle", "sample": "%d full FV steps of the channel" % args.steps,
+            "config": _config(w, args.gpus),
+            "schedule": "FP64 oracle, one cell at a time, OpenMP over rows",
+            "cpu_baseline": {"value": round(v, 3), "unit": "MLUPS", "cores": thr, "kind": "oracle",
+                             "sample": "%d full %s steps of the %dx%d grid" % (args.steps, w.scheme.upper(),
+                                                                            w.grid["nx"], w.grid["ny"]),
                              "cpu_model": cpu_model()},
             "e2e": {"value": round(v, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
 
+HEADLINE = "st8192"
+
+
 def case_workload(cfg, name):
-    """Workloads that --case selects (the default, 'channel', is the headline)."""
+    """Workloads that --case selects (the default, 'st8192', is the headline:
+    config 4, the largest single-GPU configuration)."""
     import paper_1505_03271_gb300 as lb
     table = {
-        "channel": lambda: cfg.channel(),
         "st8192": lambda: cfg.st_sweep(8192, lb.LB_STORE_F32),
+        "channel": lambda: cfg.channel(),
         "st4096": lambda: cfg.st_sweep(4096, lb.LB_STORE_F32),
         "st4096_f16dev": lambda: cfg.st_sweep(4096, lb.LB_STORE_F16DEV),
+        "st4096_bf16dev": lambda: cfg.st_sweep(4096, lb.LB_STORE_BF16DEV),
         "fv4096": lambda: _fv_big(cfg, 4096),
         "fv2048": lambda: _fv_big(cfg, 2048),
         "rb1024": lambda: cfg.rayleigh_benard(1024, 1e8),
+        "rb1024_f32": lambda: cfg.rayleigh_benard(1024, 1e8, store=lb.LB_STORE_F32),
         "rb3d_fv": lambda: cfg.rb3d_table("fv"),
         "rb3d_st": lambda: cfg.rb3d_table("st"),
     }
     return table[name]()
 
 
-def _config(w, case="channel"):
-    if case != "channel":
-        return {"workload": w.name, "cells": w.cells, "scheme": w.scheme,
-                "store": w.grid["store"], "thermal": bool(w.grid.get("thermal", False)),
-                "l2": "flushed: 256 MiB write between timed steps"}
-    return {"workload": "FV channel %dx%d, tanh delta=2 walls on y, tau=0.2 (ST tau~=0.7), Re=10, "
-                        "FP32 math on f-w storage" % (w.grid["nx"], w.grid["ny"]),
-            "cells": w.cells, "scheme": "fv semi-implicit + Heun + QUICK",
-            "dt": round(w.params["dt"], 6), "l2": "flushed: 256 MiB write between timed steps"}
+def describe(w):
+    """What a workload is, with its sizes."""
+    g = w.grid
+    store = STORE_LABEL[g["store"]]
+    if w.name.startswith("st") and "nz" not in g:
+        return ("ST D2Q9 %dx%d periodic, Taylor-Green mode 1 + shear wave mode 2 (u0 = A = 0.01), "
+                "quoted tau = 0.8, %s storage, FP32 math" % (g["nx"], g["ny"], store)
+                if g["store"] != 0 else "ST D2Q9 %dx%d periodic, FP64" % (g["nx"], g["ny"]))
+    if w.name.startswith("channel"):
+        return ("FV channel %dx%d, tanh delta=2 walls on y, tau=0.2 (ST tau~=0.7), Re=10, %s storage, "
+                "FP32 math" % (g["nx"], g["ny"], store))
+    if w.name.startswith("rb") and "nz" not in g:
+        return ("FV thermal Rayleigh-Benard %dx%d, Ra=1e8, Pr=1, x periodic, tanh delta=2 plates, "
+                "%s storage, FP32 math" % (g["nx"], g["ny"], store))
+    return w.name
+
+
+def _config(w, world=1):
+    """The workload fields of the JSON line, the same for both arms."""
+    from paper_1505_03271_gb300 import configs as cfg
+    sb = state_bytes(cfg, w)
+    return {"workload": describe(w), "cells": w.cells, "scheme": w.scheme,
+            "steps_per_run": w.steps,
+            "l2": ("flushed: 256 MiB write between timed steps" if needs_flush(cfg, w)
+                   else "state %.1f GB > 129 MB L2, no flush" % (sb / 1e9)),
+            "parallelism": "replicas" if world > 1 else "single"}
 
 
 def visible_gpu_index(local):
@@ -490,14 +612,14 @@ def visible_gpu_index(local):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-extra", action="store_true", help="headline only (for profiling)")
-    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baseline")
-    ap.add_argument("--case", default="channel",
-                    help="workload to time: channel (headline), st8192, st4096, st4096_f16dev, "
-                         "fv4096, fv2048, rb1024, rb3d_fv, rb3d_st (3-D Table rb grids)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle baselines")
+    ap.add_argument("--case", default=HEADLINE,
+                    help="workload to time: st8192 (headline), channel, st4096, st4096_f16dev, "
+                         "st4096_bf16dev, fv4096, fv2048, rb1024, rb1024_f32, rb3d_fv, rb3d_st")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving stream")
     ap.add_argument("--roofline-sweep", default=None, metavar="N,N,...",
                     help="print the ST/FV roofline curve over these n x n grid sizes instead of the bench line")
@@ -530,8 +652,8 @@ def main():
     lb.load()
     stream = torch.cuda.current_stream().cuda_stream
     peak, peak_kind = load_peaks()
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
     if args.roofline_sweep:
-        flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
         sizes = [int(v) for v in args.roofline_sweep.split(",")]
         with ClockSampler(visible_gpu_index(local)) as clk:
             rows = roofline_sweep(lb, torch, cfg, stream, peak, flush, sizes)
@@ -542,7 +664,7 @@ def main():
         return
     w = case_workload(cfg, args.case)
     g = make_grid(lb, w, stream)
-    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    fl = flush if needs_flush(cfg, w) else None
 
     def barrier():
         torch.cuda.synchronize()
@@ -553,47 +675,38 @@ def main():
     gpu_index = visible_gpu_index(local)
     barrier()
     with ClockSampler(gpu_index) as clk:
-        ms, launches = time_steps(lb, torch, g, w.scheme, args.steps, args.warmup, flush)
+        ms, launches = time_steps(lb, torch, g, w.scheme, args.steps, args.warmup, fl)
     barrier()
     total_s, value = aggregate(sum(ms) * 1e-3, w.cells, args.steps, world, dist, "cuda")
     mean_ms = total_s * 1e3 / args.steps
     bpc = cfg.bytes_per_cell(w.grid["store"], w.grid.get("thermal", False), 19 if "nz" in w.grid else 9)
     dtype = "f64" if w.grid["store"] == lb.LB_STORE_F64 else "f32"
+    sched = schedule_name(lb, g, w.scheme)
+    tcase = {"st8192": ("st4096", 4)}.get(args.case, args.case)
+    tcase, scale = tcase if isinstance(tcase, tuple) else (tcase, 1)
+    traffic = measured_traffic(sched, tcase)
+    rl = roofline(bpc * w.cells, mean_ms, peak, peak_kind, traffic * scale if traffic else None)
+    if traffic and scale != 1:
+        rl["traffic_source"] = "ncu on the %s case, scaled x%d by cells" % (tcase, scale)
     line = {"metric": METRIC, "value": round(value, 2), "unit": "MLUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(mean_ms, 5),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
-            "data": "synthetic", "config": _config(w, args.case), "gpu_launches": launches,
-            "roofline": roofline(bpc * w.cells, mean_ms, peak, peak_kind,
-                                 measured_traffic(schedule_name(lb, g, w.scheme), args.case)),
-            "clocks": clk.summary()}
-    line["roofline_alu"] = None if "nz" in w.grid else alu_roofline(cfg, w, mean_ms, line["clocks"])
-    line["config"]["parallelism"] = "replicas" if world > 1 else "single"
-    line["config"]["schedule"] = schedule_name(lb, g, w.scheme)
-    if not args.no_extra and args.case == "channel":
-        line["e2e"] = e2e_measure(lb, torch, w, stream)
-        line["extra"] = extra_lines(lb, torch, cfg, stream, peak, peak_kind, flush)
-        if not args.no_serving:
-            line["extra"]["serving"] = serving_measure(lb, torch, args.serving_requests, args.serving_rate)
-    if rank == 0 and world == 1 and not args.no_cpu and args.case == "channel":
-        import oracle as O
-        O.build()
-        r, done, el, thr = oracle_sample(w, budget_s=15.0)
-        _, done1, el1, _ = oracle_sample(w, budget_s=5.0, threads=1)
-        # error of the GPU against the oracle after the same number of steps
-        g2 = make_grid(lb, w, stream, tune=False)
-        g2.set_fv_schedule(*g.fv_schedule())
-        lb.lb_step_fv(g2.handle, done)
-        _, ux, uy, _ = g2.moments()
-        _, vx, vy, _ = r.moments()
-        err = float(np.sqrt(((ux - vx) ** 2 + (uy - vy) ** 2).sum() / (vx**2 + vy**2).sum()))
-        line["cpu_baseline"] = {"value": round(w.cells * done / el / 1e6, 3), "unit": "MLUPS",
-                                "cores": thr, "kind": "oracle",
-                                "sample": "%d FV steps of the full channel (%.1f s)" % (done, el),
-                                "cpu_model": cpu_model(),
-                                "single_thread": {"value": round(w.cells * done1 / el1 / 1e6, 3),
-                                                  "sample": "%d FV steps of the full channel (%.1f s)"
-                                                            % (done1, el1)}}
-        line["oracle_error"] = {"rel_l2_u": err, "steps": done}
+            "data": "synthetic", "config": _config(w, world), "schedule": sched,
+            "gpu_launches": launches}
+    full = not args.no_extra and args.case == HEADLINE
+    cpu = rank == 0 and world == 1 and not args.no_cpu
+    if full:
+        serving = None if args.no_serving else serving_measure(lb, torch, args.serving_requests,
+                                                               args.serving_rate)
+        line["extra"] = extra_lines(lb, torch, cfg, stream, peak, peak_kind, flush, serving, cpu)
+    line["roofline"] = rl
+    line["roofline_alu"] = None if "nz" in w.grid else alu_roofline(cfg, w, mean_ms, None)
+    if cpu and args.case in (HEADLINE, "channel", "rb1024"):
+        window, single = {"st8192": (10, 1), "channel": (500, 50), "rb1024": (20, 2)}[args.case]
+        line["cpu_baseline"], line["oracle_error"] = cpu_leg(lb, w, stream, g, window, single)
+    if full:
+        line["e2e"] = e2e_measure(lb, torch, w, stream, g.fv_schedule() if w.scheme == "fv" else None)
+    line["clocks"] = clk.summary()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

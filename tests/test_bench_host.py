@@ -19,18 +19,18 @@ import bench  # noqa: E402
 def test_reference_arm_line():
     """`bench.py --impl reference` times the oracle on the headline workload
     and prints one JSON line in the contract's shape."""
-    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "2", "--warmup", "3"],
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3"],
                        cwd=ROOT, capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stderr
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["metric"] == bench.METRIC
     assert line["unit"] == "MLUPS" and line["value"] > 0 and line["higher_is_better"] is True
-    assert line["steps"] == 2 and line["warmup"] == 3 and line["n_gpus"] == 1
+    assert line["steps"] == 1 and line["warmup"] == 3 and line["n_gpus"] == 1
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
     assert line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"] == {"value": line["value"], "unit": "MLUPS", "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
-    assert "channel 256x512" in line["config"]["workload"]
+    assert "ST D2Q9 8192x8192" in line["config"]["workload"]
 
 
 def test_source_hash_ignores_comments(tmp_path, monkeypatch):
