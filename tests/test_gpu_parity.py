@@ -424,14 +424,17 @@ def test_config_channel_re10_holds_parabola(lbgpu):
     assert err < 1e-3
 
 
-def _strip_compare(lb, O, w, steps, strip, x0, tol_rel):
+def _strip_compare(lb, O, w, steps, strip, x0, tol_rel, schedule=None):
     """Sample a full-height strip of a large x-periodic grid: the oracle runs
     the strip (periodic in x) from the GPU's own state; cells 4*steps away from
-    the strip's x-edges are unaffected by the cut and must match."""
+    the strip's x-edges are unaffected by the cut and must match.  Returns the
+    GPU grid's FV schedule (kernel, resolved chunk)."""
     grid = dict(w.grid)
     store = grid.pop("store")
     g = lb.Grid(store=store, **grid)
     g.init(**w.params, **w.init)
+    if schedule is not None:
+        g.set_fv_schedule(*schedule)
     ny = grid["ny"]
     f0, g0 = g.get_window(x0, 0, strip, ny)
     r = O.RefGrid(strip, ny, float(strip), grid.get("ly", ny), 0, grid.get("sy", 0), 0.0,
@@ -449,6 +452,7 @@ def _strip_compare(lb, O, w, steps, strip, x0, tol_rel):
     if g1 is not None:
         gscale = np.abs(g0 - O.lattice()[2][:, None, None] * w.params["T0"]).max()
         assert np.abs(g1[:, :, sl] - gr[:, :, sl]).max() <= tol_rel * gscale
+    return g.fv_schedule() if w.scheme == "fv" else None
 
 
 @pytest.mark.parametrize("store,tol", [("f32", 1e-5), ("bf16dev", 2e-2), ("f16dev", 3e-3)])
@@ -511,6 +515,23 @@ def test_config_channel_strip_f32(lbgpu, oracle):
     from paper_1505_03271_gb300 import configs as cfg
     w = cfg.channel(u_max=0.05)
     _strip_compare(lbgpu, oracle, w, 3, 30, 100, 1e-5)
+
+
+@pytest.mark.parametrize("case", ["tgv2048", "channel2048x1024"])
+def test_pair_march_auto_chunk_strip(lbgpu, oracle, case):
+    """The paired marching kernel at its automatic chunk (the rows per CTA
+    that large grids run with, far more than the small-grid tests use), on
+    a 2048^2 periodic TGV and on a 2048 x 1024 tanh-walled channel: a 3-step
+    full-height strip matches the oracle at the FP32 bar, 2e-6 of the
+    deviation scale."""
+    from paper_1505_03271_gb300 import configs as cfg
+    if case == "tgv2048":
+        w = cfg.Workload("tgv2048", dict(nx=2048, ny=2048, store=lbgpu.LB_STORE_F32),
+                         dict(tau=0.3, dt=0.5, ax=1e-6), dict(kind=0, u0=0.02, amp=0.01, mode=3), 3, "fv")
+    else:
+        w = cfg.channel(u_max=0.05, nx=2048, ny=1024)
+    kernel, chunk = _strip_compare(lbgpu, oracle, w, 3, 30, 777, 2e-6, schedule=(lbgpu.LB_FV_PAIR, 0))
+    assert kernel == lbgpu.LB_FV_PAIR and chunk >= 32
 
 
 # ------------------------------------------------------------ observables --

@@ -128,6 +128,32 @@ def test_served_request_matches_oracle(lbgpu, oracle):
         assert abs(a - b) <= 1e-10 * max(1.0, abs(b))
 
 
+@pytest.mark.parametrize("store,tol", [("f32", 1e-6), ("f16dev", 1e-3)])
+def test_served_mix_matches_oracle_reduced_precision(lbgpu, oracle, store, tol):
+    """FP32 arithmetic in the paired batched kernel (k_fv_ptile_batched), with
+    FP32 and FP16 deviation storage: each request of a three-request mix has
+    Nusselt numbers within the storage's bar of the FP64 oracle's (1e-6
+    relative for FP32, 1e-3 for FP16 storage), as on a single grid."""
+    lb = lbgpu
+    oracle.set_threads(os.cpu_count() or 1)
+    reqs = _requests()
+    s = lb.Server(store=store, thermal=True, steps_per_launch=8)
+    for r in reqs:
+        s.submit(**r)
+    got = _drain(s)
+    for r in reqs:
+        assert got[r["rid"]]["status"] == lb.LB_OK
+        ref = oracle.RefGrid(r["nx"], r["ny"], sy=r.get("sy", 0), stretch_y=r.get("stretch_y", 0.0),
+                             bcy=r["bcy"], thermal=True)
+        ref.set_params(tau=r["tau"], dt=r["dt"], tau_g=r["tau_g"], beta=r["beta"], grav=r["grav"],
+                       T0=r["T0"], T_bot=r["T_bot"], T_top=r["T_top"])
+        ref.init_preset(oracle.INIT_RB, amp=r["amp"], seed=r["seed"])
+        ref.step_fv(r["nsteps"])
+        res = got[r["rid"]]
+        for a, b in zip((res["nu_vol"], res["nu_bot"], res["nu_top"]), ref.nusselt()):
+            assert abs(a / b - 1.0) < tol, (r["rid"], a, b)
+
+
 def test_arrival_policy_is_first_come_first_served(lbgpu):
     """LB_SERVE_ARRIVAL: when every request alone fills the GPU (a 1024^2
     grid is far more than two waves of tiles), they run one at a time in
