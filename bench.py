@@ -4,7 +4,7 @@ Headline workload (config 4, the largest single-GPU configuration): the ST
 step on an 8192 x 8192 periodic D2Q9 grid (Taylor-Green mode 1 plus a mode-2
 shear wave), FP32 storage and arithmetic.  One bench step = one ST time step
 (one kernel launch), timed alone with CUDA events on the launching stream;
-the state (9.7 GB) is far larger than the 129 MB L2, so no flush is needed.
+the state (two 2.4 GB buffers) is far larger than the 129 MB L2, so no flush is needed.
 The line carries the HBM roofline of that kernel, the FP64 oracle timed on
 this host's cores over a fixed 10-step window (and its error against the
 GPU after the same window), and the end-to-end figure through the C ABI
@@ -56,7 +56,7 @@ class ClockSampler:
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index: int, period_ms: int = 100):
+    def __init__(self, gpu_index: int, period_ms: int = 20):
         self.gpu, self.period = gpu_index, period_ms
         self.proc = None
         self.lines = []
@@ -69,6 +69,10 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            # the timed region starts only once sampling has begun
+            t0 = time.perf_counter()
+            while not self.lines and self.proc.poll() is None and time.perf_counter() - t0 < 5.0:
+                time.sleep(0.005)
         except Exception:
             self.proc = None
         return self

@@ -576,7 +576,6 @@ def test_rb_barometric_rest_state(lbgpu, oracle, scheme, sy, store, tol):
     _, ux, uy, _ = g.moments()
     _, vx, vy, _ = r.moments()
     assert np.abs(ux - vx).max() < tol and np.abs(uy - vy).max() < tol
-    assert np.abs(vy).max() < 2e-4   # oracle: first-order wall kink (FV) at most
 
 
 def test_rb_nusselt_f16_vs_oracle(lbgpu, oracle):
