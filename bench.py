@@ -154,6 +154,8 @@ def schedule_name(lb, g, scheme):
         if g.store == lb.LB_STORE_F64:
             return "st push, one thread per cell"
         if g.store in (lb.LB_STORE_F16DEV, lb.LB_STORE_BF16DEV) and not g.thermal:
+            if g.nx % 4 == 0 and g.desc.bcx == lb.LB_BC_PERIODIC:
+                return "st quad (64-bit words, f32x2), four cells of two rows per thread"
             return "st pair (f32x2), two cells of two rows per thread"
         return "st pair (f32x2), two cells per thread"
     k, c = g.fv_schedule()
@@ -568,6 +570,8 @@ def case_workload(cfg, name):
         "st4096": lambda: cfg.st_sweep(4096, lb.LB_STORE_F32),
         "st4096_f16dev": lambda: cfg.st_sweep(4096, lb.LB_STORE_F16DEV),
         "st4096_bf16dev": lambda: cfg.st_sweep(4096, lb.LB_STORE_BF16DEV),
+        "st8192_f16dev": lambda: cfg.st_sweep(8192, lb.LB_STORE_F16DEV),
+        "st8192_bf16dev": lambda: cfg.st_sweep(8192, lb.LB_STORE_BF16DEV),
         "fv4096": lambda: _fv_big(cfg, 4096),
         "fv2048": lambda: _fv_big(cfg, 2048),
         "rb1024": lambda: cfg.rayleigh_benard(1024, 1e8),

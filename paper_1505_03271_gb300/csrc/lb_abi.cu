@@ -61,6 +61,9 @@ cudaError_t set_max_smem(const void* fn, int bytes) {
     if (e == cudaSuccess) done.insert({dev, fn, bytes});
     return e;
 }
+// 16-bit ST on flow grids periodic in x with nx % 4 == 0 (k_st16.cu).
+bool st16_applies(Prec p, bool thermal, int nx, int bcx);
+cudaError_t launch_st16(Prec p, const void* args, cudaStream_t s);
 // Record a failure message for lb_last_error() from another translation unit.
 lb_status set_last_error(lb_status s, const char* msg) { return fail(s, "%s", msg); }
 }  // namespace lbgb
@@ -746,6 +749,7 @@ lb_status lb_step_st(lb_grid* G, int nsteps) {
             return launch_st(G->prec, th, &A, G->stream);
         }
         StepArgs<float> A = step_args<float>(G, 1.0);
+        if (st16_applies(G->prec, th, G->nx, G->d.bcx)) return launch_st16(G->prec, &A, G->stream);
         return launch_st(G->prec, th, &A, G->stream);
     });
 }

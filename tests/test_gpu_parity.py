@@ -85,6 +85,9 @@ ST_CASES = [
     dict(nx=300, ny=5),
     dict(nx=20, ny=12, bcy=1, thermal=True),
     dict(nx=1, ny=10),
+    dict(nx=260, ny=9, bcy=1),   # 16-bit flow: four-cell words, a partial warp, walls on y
+    dict(nx=4, ny=6),            # one thread per row pair
+    dict(nx=136, ny=3),          # odd row count, last row pair single
 ]
 
 
