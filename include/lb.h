@@ -316,12 +316,13 @@ typedef struct {
 
 /* Which admitted requests take steps in a pump:
  *   LB_SERVE_SHARE:    all of them (equal steps for everyone);
- *   LB_SERVE_SHORTEST: least remaining work (cells x steps) first, as many as
- *                      fit about two waves of CTAs (at least one); the others
- *                      keep their memory and wait;
- *   LB_SERVE_ARRIVAL:  the earliest submitted first, as many as fit about two
- *                      waves of CTAs (at least one): first-come first-served
- *                      for the large requests, batched for the small ones. */
+ *   LB_SERVE_SHORTEST: least remaining work (cells x steps) first: the first
+ *                      one, then as many as fit about two more waves of
+ *                      CTAs; the others keep their memory and wait;
+ *   LB_SERVE_ARRIVAL:  the earliest submitted first, then as many as fit
+ *                      about two more waves of CTAs: first-come first-served
+ *                      for the large requests, and the small ones batched,
+ *                      riding along with a large one that fills the GPU. */
 typedef enum { LB_SERVE_SHARE = 0, LB_SERVE_SHORTEST = 1, LB_SERVE_ARRIVAL = 2 } lb_serve_policy;
 
 /* store/thermal: the one storage type and model all requests use.

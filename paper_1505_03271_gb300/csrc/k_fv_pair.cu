@@ -224,13 +224,17 @@ __global__ void __launch_bounds__(NT) k_fv_pair(const StepArgs<float> A, const i
         }
     };
 
-    // register buffers: (b0, e0) hold row t, (b1, e1) row t + 1 (in flight)
+    // Two register buffers alternate between even and odd rows: row t's
+    // populations are read from its buffer, which then takes the loads of
+    // row t + 2.  The loop body is written out for both buffers, so no
+    // register copy waits on a load in flight: each load has two full rows
+    // of work to land.
     V2 b0[Q], e0[Q], b1[Q], e1[Q];
     prefetch(ys - 4, b0, e0);
     prefetch(ys - 3, b1, e1);
     int s0 = slot5(ys - 4);  // slot of row t
     int t3 = ((ys - 4) % 3 + 3) % 3;  // slot of row t in the 3-row rings
-    for (int t = ys - 4; t < ye + 4; ++t) {
+    auto row_step = [&](const int t, V2* bt, V2* et) {
         // 3-row ring slots of rows t - 2 and t - 4 (rows three apart share one)
         const int c3b = t3 == 2 ? 0 : t3 + 1, c3c = t3 == 0 ? 2 : t3 - 1;
         // m[i] = slot of row t - 4 + i (rows t - 4 .. t; m[4] = s0), since
@@ -248,14 +252,10 @@ __global__ void __launch_bounds__(NT) k_fv_pair(const StepArgs<float> A, const i
             V2 d[Q], e[Q];
 #pragma unroll
             for (int a = 0; a < Q; ++a) {
-                d[a] = b0[a];
-                b0[a] = b1[a];
-                if constexpr (TH) {
-                    e[a] = e0[a];
-                    e0[a] = e1[a];
-                }
+                d[a] = bt[a];
+                if constexpr (TH) e[a] = et[a];
             }
-            prefetch(t + 2, b1, e1);
+            prefetch(t + 2, bt, et);
             if (fluid_row(t, gy)) {
                 const float4 o = __ldg(reinterpret_cast<const float4*>(A.rowtab + 20 * gy) + 3);
                 PairCell<TH> c;
@@ -353,6 +353,11 @@ __global__ void __launch_bounds__(NT) k_fv_pair(const StepArgs<float> A, const i
         __syncthreads();
         s0 = m[0];  // slot of row t + 1 (= slot of row t - 4)
         t3 = t3 == 2 ? 0 : t3 + 1;
+    };
+    // the trip count is CTA-uniform, so every thread meets every barrier
+    for (int t = ys - 4; t < ye + 4; t += 2) {
+        row_step(t, b0, e0);
+        if (t + 1 < ye + 4) row_step(t + 1, b1, e1);
     }
 }
 

@@ -312,7 +312,10 @@ lb_status lb_server_pump(lb_server* S, int* n_active, int* n_pending) {
         std::vector<char> run(S->active.size(), 1);
         if (S->policy != LB_SERVE_SHARE) {
             // least remaining work first (SHORTEST) or the active list's
-            // arrival order (ARRIVAL), within about two waves of CTAs
+            // arrival order (ARRIVAL): the first request always steps, and
+            // the next ones join while their tiles fit in about two more
+            // waves of CTAs, so small requests ride along with a large one
+            // that fills the GPU by itself
             if (S->policy == LB_SERVE_SHORTEST)
                 std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
                     const Active &p = S->active[x], &q = S->active[y];
@@ -320,11 +323,11 @@ lb_status lb_server_pump(lb_server* S, int* n_active, int* n_pending) {
                            (double)q.req.grid.nx * q.req.grid.ny * q.remaining;
                 });
             const int target = 2 * S->sms * (S->thermal ? 1 : 2);
-            int sum = 0;
+            int sum = 0;  // tiles of the requests after the first
             for (size_t j = 0; j < order.size(); ++j) {
                 const int t = tiles_of(S->active[order[j]]);
                 run[order[j]] = (j == 0 || sum + t <= target) ? 1 : 0;
-                if (run[order[j]]) sum += t;
+                if (run[order[j]] && j > 0) sum += t;
             }
         }
         int ntiles = 0;

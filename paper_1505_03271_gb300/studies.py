@@ -428,7 +428,7 @@ def rb3d_long(lb, torch):
     return rb3d(lb, torch, 600.0, 500.0, 250)
 
 
-def predictability_horizon(lb, torch, n=1024, Ra=1e8, chunk=2000, max_steps=200000, budget_s=900.0,
+def predictability_horizon(lb, torch, n=1024, Ra=1e8, chunk=2000, max_steps=200000, budget_s=540.0,
                            tol=1e-3):
     """Predictability horizon t_h of the chaotic RB cell (config 3): two FP64
     runs whose only difference is the seeded perturbation's amplitude, 1e-3
@@ -473,6 +473,7 @@ def predictability_horizon(lb, torch, n=1024, Ra=1e8, chunk=2000, max_steps=2000
             if first[k] is None and d > tol:
                 first[k] = steps
         hist.append(row)
+        print(json.dumps({"horizon_progress": row}), file=sys.stderr, flush=True)
         if first["f64_ulp"] is not None:
             break
     for g in grids.values():
