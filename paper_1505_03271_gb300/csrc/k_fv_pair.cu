@@ -49,6 +49,27 @@ struct YPair {
     float ro, to, dref[4];
 };
 
+// The raw 80 bytes of a row entry, so that a row's entry can be loaded one
+// row ahead of its use and unpacked when it is needed.
+struct RowRaw {
+    float4 a, b, c, d, e;
+};
+__device__ __forceinline__ void load_raw(const float* tab, int g, RowRaw& R) {
+    const float4* p = reinterpret_cast<const float4*>(tab + 20 * g);
+    R.a = __ldg(p); R.b = __ldg(p + 1); R.c = __ldg(p + 2); R.d = __ldg(p + 3); R.e = __ldg(p + 4);
+}
+__device__ __forceinline__ void unpack_row(const RowRaw& R, YPair& Y) {
+    const float4 a = R.a, b = R.b, c = R.c, d = R.d, e = R.e;
+    Y.ps[0] = bc(a.x); Y.ps[1] = bc(a.y); Y.ps[2] = bc(a.z);
+    Y.pn[0] = bc(a.w); Y.pn[1] = bc(b.x); Y.pn[2] = bc(b.y);
+    Y.ms[0] = bc(b.z); Y.ms[1] = bc(b.w); Y.ms[2] = bc(c.x);
+    Y.mn[0] = bc(c.y); Y.mn[1] = bc(c.z); Y.mn[2] = bc(c.w);
+    Y.inv = bc(d.x);
+    Y.ro = d.y;
+    Y.to = d.z;
+    Y.dref[0] = d.w; Y.dref[1] = e.x; Y.dref[2] = e.y; Y.dref[3] = e.z;
+}
+
 __device__ __forceinline__ void load_row(const float* tab, int g, YPair& Y) {
     const float4* p = reinterpret_cast<const float4*>(tab + 20 * g);
     const float4 a = __ldg(p), b = __ldg(p + 1), c = __ldg(p + 2), d = __ldg(p + 3), e = __ldg(p + 4);
@@ -210,11 +231,13 @@ __global__ void __launch_bounds__(NT) k_fv_pair(const StepArgs<float> A, const i
             out = mk(Store<S>::ld(base + row + gxl), Store<S>::ld(base + row + gxr));
         }
     };
-    // populations of row r into (bd, be); rows are loaded two iterations
-    // before stage A needs them, so the DRAM latency overlaps two rows of work
-    auto prefetch = [&](int r, V2* bd, V2* be) {
+    // populations of row r into (bd, be), and the row's base-state offsets
+    // into bo; rows are loaded two iterations before stage A needs them, so
+    // the DRAM latency overlaps two rows of work
+    auto prefetch = [&](int r, V2* bd, V2* be, float4& bo) {
         int gy;
         if (r < ye + 4 && fluid_row(r, gy)) {
+            bo = __ldg(reinterpret_cast<const float4*>(A.rowtab + 20 * gy) + 3);
 #pragma unroll
             for (int a = 0; a < Q; ++a) load_pair(fin + a * A.plane, gy, bd[a]);
             if constexpr (TH) {
@@ -224,17 +247,24 @@ __global__ void __launch_bounds__(NT) k_fv_pair(const StepArgs<float> A, const i
         }
     };
 
-    // Two register buffers alternate between even and odd rows: row t's
-    // populations are read from its buffer, which then takes the loads of
-    // row t + 2.  The loop body is written out for both buffers, so no
-    // register copy waits on a load in flight: each load has two full rows
-    // of work to land.
+    // register buffers: (b0, e0, o0) hold row t, (b1, e1, o1) row t + 1 (in flight)
     V2 b0[Q], e0[Q], b1[Q], e1[Q];
-    prefetch(ys - 4, b0, e0);
-    prefetch(ys - 3, b1, e1);
+    float4 o0 = make_float4(0.f, 0.f, 0.f, 0.f), o1 = o0;
+    prefetch(ys - 4, b0, e0, o0);
+    prefetch(ys - 3, b1, e1, o1);
+    // row tables of stages B (row t - 2) and C (row t - 4), loaded one
+    // iteration before their use
+    RowRaw rb{}, rc{};
+    auto next_tables = [&](int t) {
+        int gy;
+        const int r = t - 2;
+        if (r >= ys - 2 && r < ye + 2 && fluid_row(r, gy) && colB) load_raw(A.rowtab, gy, rb);
+        if (t - 4 >= ys && t - 4 < ye && colC) load_raw(A.rowtab, t - 4, rc);
+    };
+    next_tables(ys - 4);
     int s0 = slot5(ys - 4);  // slot of row t
     int t3 = ((ys - 4) % 3 + 3) % 3;  // slot of row t in the 3-row rings
-    auto row_step = [&](const int t, V2* bt, V2* et) {
+    for (int t = ys - 4; t < ye + 4; ++t) {
         // 3-row ring slots of rows t - 2 and t - 4 (rows three apart share one)
         const int c3b = t3 == 2 ? 0 : t3 + 1, c3c = t3 == 0 ? 2 : t3 - 1;
         // m[i] = slot of row t - 4 + i (rows t - 4 .. t; m[4] = s0), since
@@ -252,12 +282,17 @@ __global__ void __launch_bounds__(NT) k_fv_pair(const StepArgs<float> A, const i
             V2 d[Q], e[Q];
 #pragma unroll
             for (int a = 0; a < Q; ++a) {
-                d[a] = bt[a];
-                if constexpr (TH) e[a] = et[a];
+                d[a] = b0[a];
+                b0[a] = b1[a];
+                if constexpr (TH) {
+                    e[a] = e0[a];
+                    e0[a] = e1[a];
+                }
             }
-            prefetch(t + 2, bt, et);
+            const float4 o = o0;
+            o0 = o1;
+            prefetch(t + 2, b1, e1, o1);
             if (fluid_row(t, gy)) {
-                const float4 o = __ldg(reinterpret_cast<const float4*>(A.rowtab + 20 * gy) + 3);
                 PairCell<TH> c;
                 c.build(d, e, A, o.y, TH ? o.z : 0.0f);
 #pragma unroll
@@ -292,7 +327,7 @@ __global__ void __launch_bounds__(NT) k_fv_pair(const StepArgs<float> A, const i
                 if (fluid_row(r, gy)) {
                     if (colB) {
                         YPair Y;
-                        load_row(A.rowtab, gy, Y);
+                        unpack_row(rb, Y);
                         const int sl[5] = {m[0], m[1], m[2], m[3], m[4]};
                         V2 adv[NQ];
                         advect_all<TH, NQ, NT, 0>(sH, sl, c3b, k, X, Y, A, gy, adv);
@@ -335,7 +370,7 @@ __global__ void __launch_bounds__(NT) k_fv_pair(const StepArgs<float> A, const i
             if (r >= ys && r < ye && colC) {
                 const int s = m[0];
                 YPair Y;
-                load_row(A.rowtab, r, Y);
+                unpack_row(rc, Y);
                 const int sl[5] = {m[3], m[4], m[0], m[1], m[2]};
                 V2 adv[NQ];
                 advect_all<TH, NQ, NT, 0>(sS, sl, c3c, k, X, Y, A, r, adv);
@@ -350,14 +385,10 @@ __global__ void __launch_bounds__(NT) k_fv_pair(const StepArgs<float> A, const i
                 }
             }
         }
+        next_tables(t + 1);
         __syncthreads();
         s0 = m[0];  // slot of row t + 1 (= slot of row t - 4)
         t3 = t3 == 2 ? 0 : t3 + 1;
-    };
-    // the trip count is CTA-uniform, so every thread meets every barrier
-    for (int t = ys - 4; t < ye + 4; t += 2) {
-        row_step(t, b0, e0);
-        if (t + 1 < ye + 4) row_step(t + 1, b1, e1);
     }
 }
 
