@@ -412,6 +412,26 @@ __device__ __forceinline__ void load_col(const float* tab, int g, XPair& X) {
     X.inv = mk(e.z, e.w);
 }
 
+// The same entries from a shared-memory copy of the tables.
+__device__ __forceinline__ void load_col_s(const float4* p, XPair& X) {
+    const float4 a = p[0], b = p[1], c = p[2], d = p[3], e = p[4];
+    X.wp[0] = a.x; X.wp[1] = a.y; X.wp[2] = a.z;
+    X.mp[0] = a.w; X.mp[1] = b.x; X.mp[2] = b.y;
+    X.ep[0] = b.z; X.ep[1] = b.w; X.ep[2] = c.x;
+    X.wm[0] = c.y; X.wm[1] = c.z; X.wm[2] = c.w;
+    X.mm[0] = d.x; X.mm[1] = d.y; X.mm[2] = d.z;
+    X.em[0] = d.w; X.em[1] = e.x; X.em[2] = e.y;
+    X.inv = mk(e.z, e.w);
+}
+__device__ __forceinline__ void load_row_s(const float4* p, YPair& Y) {
+    RowRaw R{p[0], p[1], p[2], p[3], p[4]};
+    unpack_row(R, Y);
+}
+
+// Floats of the per-tile copy of the row and column tables: the rows and
+// pair-columns of region E2 (tile + 2).
+__host__ __device__ constexpr int ptile_tab_floats(int TX, int TY) { return 20 * ((TY + 4) + (TX + 4) / 2); }
+
 // Flux divergence of population a at pair-cell (px, y) of a region plane
 // with row stride W pairs.
 template <int a>
@@ -526,9 +546,27 @@ __device__ __forceinline__ void ptile_body(const StepArgs<float>& A, const int x
     V2* sH = reinterpret_cast<V2*>(smem_raw);  // [NQ][EH][EW] h^n
     V2* sFC = sH + NQ * NE;                    // [NQ][BH][BW] f~ + Coll, then - dt/2 A[h^n]
     V2* sHs = sFC + NQ * NB;                   // [NQ][BH][BW] h*
+    static_assert((NQ * (NE + 2 * NB)) % 2 == 0, "table copy must start 16-byte aligned");
+    float4* sRow = reinterpret_cast<float4*>(sHs + NQ * NB);  // [BH][5] row entries of E2's rows
+    float4* sCol = sRow + 5 * BH;                              // [BW][5] entries of E2's pair-columns
     const int nx = A.nx;
     const S* fin = static_cast<const S*>(A.fin);
     const S* gin = static_cast<const S*>(A.gin);
+
+    // The row and column tables of region E2, copied before stage A so that
+    // their loads overlap it; the barrier after stage A publishes them.
+    for (int k = threadIdx.x; k < 5 * (BH + BW); k += NTH) {
+        const int e = k / 5, part = k % 5;
+        if (e < BH) {
+            int gy;
+            if (map_axis(y0 - 2 + e, A.ny, A.bcy, gy))
+                sRow[k] = __ldg(reinterpret_cast<const float4*>(A.rowtab) + 5 * gy + part);
+        } else {
+            const int xu = x0 - 2 + 2 * (e - BH);
+            const int gxl = ((xu % nx) + nx) % nx;
+            sCol[(e - BH) * 5 + part] = __ldg(reinterpret_cast<const float4*>(A.coltab) + 5 * gxl + part);
+        }
+    }
 
     // ---- time level n on E4 ----
     for (int k = threadIdx.x; k < NE; k += NTH) {
@@ -575,12 +613,10 @@ __device__ __forceinline__ void ptile_body(const StepArgs<float>& A, const int x
         const int bx = k % BW, by = k / BW;
         int gy;
         if (!map_axis(y0 - 2 + by, A.ny, A.bcy, gy)) continue;
-        const int xu = x0 - 2 + 2 * bx;
-        const int gxl = ((xu % nx) + nx) % nx;
         XPair X;
-        load_col(A.coltab, gxl, X);
+        load_col_s(sCol + 5 * bx, X);
         YPair Y;
-        load_row(A.rowtab, gy, Y);
+        load_row_s(sRow + 5 * by, Y);
         V2 adv[NQ];
         advect_region_all<TH, NQ, EH, EW, 0>(sH, bx + 1, by + 2, X, Y, adv);
         const bool tile = bx >= 1 && bx < BW - 1 && by >= 2 && by < BH - 2;
@@ -622,9 +658,9 @@ __device__ __forceinline__ void ptile_body(const StepArgs<float>& A, const int x
         const int gx = x0 + 2 * tx, gy = y0 + ty;
         if (gx >= nx || gy >= A.ny) continue;
         XPair X;
-        load_col(A.coltab, gx, X);
+        load_col_s(sCol + 5 * (tx + 1), X);
         YPair Y;
-        load_row(A.rowtab, gy, Y);
+        load_row_s(sRow + 5 * (ty + 2), Y);
         if (!SPLIT) {
             corrector_write<S, TH, BH, BW, ALL>(sHs, sFC, tx, ty, gx, gy, X, Y, A);
         } else if (k < TW * TY) {
@@ -857,7 +893,8 @@ static cudaError_t run_ptile_batched(const void* reqs, const int4* tiles, const 
                                      cudaStream_t s) {
     constexpr int NQ = TH ? 2 * Q : Q;
     constexpr int NTH = TH ? 512 : 256;
-    constexpr size_t smem = sizeof(V2) * NQ * (((32 + 8) / 2) * (16 + 8) + 2 * ((32 + 4) / 2) * (16 + 4));
+    constexpr size_t smem = sizeof(V2) * NQ * (((32 + 8) / 2) * (16 + 8) + 2 * ((32 + 4) / 2) * (16 + 4)) +
+                            sizeof(float) * ptile_tab_floats(32, 16);
     {
         cudaError_t e = set_max_smem((const void*)k_fv_ptile_batched<S, TH, 32, 16, NTH>, (int)smem);
         if (e != cudaSuccess) return e;
@@ -888,7 +925,8 @@ template <typename S, bool TH, int TX, int TY, int NTH, int MINB>
 static cudaError_t run_ptile(const void* vargs, cudaStream_t s) {
     const StepArgs<float>& A = *static_cast<const StepArgs<float>*>(vargs);
     constexpr int NQ = TH ? 2 * Q : Q;
-    constexpr size_t smem = sizeof(V2) * NQ * (((TX + 8) / 2) * (TY + 8) + 2 * ((TX + 4) / 2) * (TY + 4));
+    constexpr size_t smem = sizeof(V2) * NQ * (((TX + 8) / 2) * (TY + 8) + 2 * ((TX + 4) / 2) * (TY + 4)) +
+                            sizeof(float) * ptile_tab_floats(TX, TY);
     static_assert(smem <= 232448, "shared memory per CTA");
     {
         cudaError_t e = set_max_smem((const void*)k_fv_ptile<S, TH, TX, TY, NTH, MINB>, (int)smem);

@@ -112,22 +112,30 @@ __device__ __forceinline__ V2 xdiv(V2 P, const XW& X) {
 struct FW {
     V2 p[3], m[3];
 };
-__device__ __forceinline__ void load_fw(const float* tab, int j, int ny, bool wall, FW& F) {
-    int r = j, op = 0, om = 6;
-    if (j < 0 || j >= ny) {
-        if (wall) {
-            r = j < 0 ? 0 : ny - 1;
-            op = j < 0 ? 0 : 3;
-            om = j < 0 ? 6 : 9;
-        } else {
-            r = ((j % ny) + ny) % ny;
-        }
+// The table is the chunk's copy in shared memory: entry i is row base + i
+// (wrapped on a periodic axis).  Indices outside the copy are clamped; only
+// faces that no written row uses fall outside it.
+struct ChunkTab {
+    const float* t;
+    int base, rows;
+    __device__ __forceinline__ const float* entry(int r) const {
+        int i = r - base;
+        i = i < 0 ? 0 : (i >= rows ? rows - 1 : i);
+        return t + 20 * i;
     }
-    const float* e = tab + 20 * r;
+};
+__device__ __forceinline__ void load_fw(const ChunkTab& T, int j, int ny, bool wall, FW& F) {
+    int r = j, op = 0, om = 6;
+    if (wall && j >= ny) {
+        r = ny - 1;
+        op = 3;
+        om = 9;
+    }
+    const float* e = T.entry(r);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-        F.p[i] = bc(__ldg(e + op + i));
-        F.m[i] = bc(__ldg(e + om + i));
+        F.p[i] = bc(e[op + i]);
+        F.m[i] = bc(e[om + i]);
     }
 }
 
@@ -135,13 +143,13 @@ __device__ __forceinline__ void load_fw(const float* tab, int j, int ny, bool wa
 struct RW {
     float inv, ro, to, dref[4];
 };
-__device__ __forceinline__ void load_rw(const float* tab, int r, RW& R) {
-    const float* e = tab + 20 * r;
-    R.inv = __ldg(e + 12);
-    R.ro = __ldg(e + 13);
-    R.to = __ldg(e + 14);
+__device__ __forceinline__ void load_rw(const ChunkTab& T, int r, RW& R) {
+    const float* e = T.entry(r);
+    R.inv = e[12];
+    R.ro = e[13];
+    R.to = e[14];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) R.dref[i] = __ldg(e + 15 + i);
+    for (int i = 0; i < 4; ++i) R.dref[i] = e[15 + i];
 }
 __device__ __forceinline__ RW zero_rw() { return RW{0.f, 0.f, 0.f, {0.f, 0.f, 0.f, 0.f}}; }
 
@@ -284,7 +292,8 @@ __device__ __forceinline__ void partial_sums(const V2* d, V2& r, V2& jx, V2& jy,
 
 // The whole march of one warp of role ROLE.
 template <typename S, bool TH, int SPW, int ROLE, int NW>
-__device__ __forceinline__ void march(const StepArgs<float>& A, const int CH, V2* ring, V2* xch, V2* ghost) {
+__device__ __forceinline__ void march(const StepArgs<float>& A, const int CH, V2* ring, V2* xch, V2* ghost,
+                                      const ChunkTab& T) {
     constexpr int NTH = 32 * NW;
     constexpr int RP = ring_pops<TH, SPW>();
     constexpr bool G = is_g<TH, ROLE>();
@@ -376,7 +385,7 @@ __device__ __forceinline__ void march(const StepArgs<float>& A, const int CH, V2
         int gA;
         const bool fA = fluid(t, gA);
         RW RA = zero_rw();
-        if (fA) load_rw(A.rowtab, gA, RA);
+        if (fA) load_rw(T, t, RA);  // the copy is indexed by the unwrapped row
         {
             V2 r, jx, jy, td;
             partial_sums<TH, SPW, ROLE>(d, r, jx, jy, td);
@@ -425,7 +434,7 @@ __device__ __forceinline__ void march(const StepArgs<float>& A, const int CH, V2
         }
         if (wall && t == 1 && ys == 0) {
             FW F0;
-            load_fw(A.rowtab, 0, ny, wall, F0);
+            load_fw(T, 0, ny, wall, F0);
             Ch.bottom_wall(h, F0, sgn);
         }
 
@@ -434,7 +443,7 @@ __device__ __forceinline__ void march(const StepArgs<float>& A, const int CH, V2
         int gB;
         const bool fB = fluid(rB, gB);
         RW RB = zero_rw();
-        if (fB) load_rw(A.rowtab, gB, RB);
+        if (fB) load_rw(T, rB, RB);
         V2 adv[Q];
 #pragma unroll
         for (int a = 0; a < Q; ++a) adv[a] = bc(0.0f);
@@ -446,8 +455,8 @@ __device__ __forceinline__ void march(const StepArgs<float>& A, const int CH, V2
         }
         {
             FW Ft, Fm;
-            load_fw(A.rowtab, t, ny, wall, Ft);
-            load_fw(A.rowtab, t - 1, ny, wall, Fm);
+            load_fw(T, t, ny, wall, Ft);
+            load_fw(T, t - 1, ny, wall, Fm);
             V2 dy[Q];
             Ch.advance(h, Ft, Fm, bc(RB.inv), dy);
 #pragma unroll
@@ -520,7 +529,7 @@ __device__ __forceinline__ void march(const StepArgs<float>& A, const int CH, V2
         }
         if (wall && rB == 1 && ys == 0) {
             FW F0;
-            load_fw(A.rowtab, 0, ny, wall, F0);
+            load_fw(T, 0, ny, wall, F0);
             Cs.bottom_wall(hs, F0, sgn);
         }
 
@@ -528,7 +537,7 @@ __device__ __forceinline__ void march(const StepArgs<float>& A, const int CH, V2
         const int rC = t - 4;
         RW RC = zero_rw();
         const bool doC = rC >= ys && rC < ye;
-        if (doC) load_rw(A.rowtab, rC, RC);
+        if (doC) load_rw(T, rC, RC);
         V2 advs[Q];
 #pragma unroll
         for (int a = 0; a < Q; ++a) advs[a] = bc(0.0f);
@@ -539,8 +548,8 @@ __device__ __forceinline__ void march(const StepArgs<float>& A, const int CH, V2
         }
         {
             FW Ft, Fm;
-            load_fw(A.rowtab, rB, ny, wall, Ft);
-            load_fw(A.rowtab, rB - 1, ny, wall, Fm);
+            load_fw(T, rB, ny, wall, Ft);
+            load_fw(T, rB - 1, ny, wall, Fm);
             V2 dy[Q];
             Cs.advance(hs, Ft, Fm, bc(RC.inv), dy);
 #pragma unroll
@@ -586,21 +595,34 @@ __global__ void __launch_bounds__(32 * NW) k_fv_warp(const StepArgs<float> A, co
     V2* ring = reinterpret_cast<V2*>(smem_raw);  // [5][RP][NTH]
     V2* ghost = ring + 5 * RP * NTH;             // [2][RP][NTH]
     V2* xch = ghost + 2 * RP * NTH;              // [NW / SPW][2][2][4][32]
+    float* tab = reinterpret_cast<float*>(xch + (NW / SPW) * 2 * 2 * 4 * 32);  // [CH + 8][20]
+    // the chunk's rows ys-4 .. ye+3 of the per-row table, copied once
+    const int ys = blockIdx.y * CH, ye = min(ys + CH, A.ny);
+    const ChunkTab T{tab, ys - 4, ye - ys + 8};
+    for (int k = threadIdx.x; k < 5 * T.rows; k += NTH) {
+        int gy;
+        const float4 v = map_axis(T.base + k / 5, A.ny, A.bcy, gy)
+                             ? __ldg(reinterpret_cast<const float4*>(A.rowtab) + 5 * gy + k % 5)
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+        reinterpret_cast<float4*>(tab)[k] = v;
+    }
+    __syncthreads();
     const int role = (threadIdx.x >> 5) % SPW;
-    if (role == 0) march<S, TH, SPW, 0, NW>(A, CH, ring, xch, ghost);
-    else if constexpr (SPW == 2) march<S, TH, SPW, 1, NW>(A, CH, ring, xch, ghost);
+    if (role == 0) march<S, TH, SPW, 0, NW>(A, CH, ring, xch, ghost, T);
+    else if constexpr (SPW == 2) march<S, TH, SPW, 1, NW>(A, CH, ring, xch, ghost, T);
 }
 
 template <typename S, bool TH, int SPW>
 static cudaError_t run_warp(const StepArgs<float>& A, int chunk, cudaStream_t s) {
     constexpr int NW = 4;
     constexpr int NTH = 32 * NW;
-    constexpr size_t smem = sizeof(V2) * ((5 + 2) * ring_pops<TH, SPW>() * NTH + (NW / SPW) * 2 * 2 * 4 * 32);
+    const int ch = chunk < 8 ? 8 : (chunk > 1024 ? 1024 : chunk);
+    const size_t smem = sizeof(V2) * ((5 + 2) * ring_pops<TH, SPW>() * NTH + (NW / SPW) * 2 * 2 * 4 * 32) +
+                        sizeof(float) * 20 * (size_t)(ch + 8);
     {
         cudaError_t e = set_max_smem((const void*)k_fv_warp<S, TH, SPW, NW>, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    const int ch = chunk < 8 ? 8 : chunk;
     const int strips = (A.nx + kOut - 1) / kOut;
     constexpr int per_cta = NW / SPW;
     dim3 grid((strips + per_cta - 1) / per_cta, (A.ny + ch - 1) / ch);

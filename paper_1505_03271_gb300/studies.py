@@ -15,9 +15,9 @@
   * ``dt_max``: the largest stable FV time step as a function of tau for the
     Euler, semi-implicit and Heun schemes on the decaying [1, 64] shear wave
     (Fig. KOL3).
-  * ``predictability_horizon``: the step at which two FP64 runs of the
-    chaotic 1024^2 Ra = 1e8 cell that start one ulp apart part by 1e-3 in a
-    Nusselt number, with the FP32 and FP16 forms' departures from FP64.
+  * ``predictability_horizon``: the step at which two runs of the chaotic
+    1024^2 Ra = 1e8 cell that start one ulp apart (one population of one
+    cell) part by 1e-3 in a Nusselt number, in FP64 and in FP32.
   * ``rb3d_stats``: the 3-D Rayleigh-Benard runs of Table rb with FV (sinh z
     grid) and ST (uniform), time- and plane-averaged profiles T_m(z),
     T_rms(z), k_m(z) and Nu(z), and the cells inside the thermal boundary
@@ -428,61 +428,80 @@ def rb3d_long(lb, torch):
     return rb3d(lb, torch, 600.0, 500.0, 250)
 
 
-def predictability_horizon(lb, torch, n=1024, Ra=1e8, chunk=2000, max_steps=200000, budget_s=540.0,
-                           tol=1e-3):
-    """Predictability horizon t_h of the chaotic RB cell (config 3): two FP64
-    runs whose only difference is the seeded perturbation's amplitude, 1e-3
-    and the next double above it (a relative change of 2e-16); t_h is the
-    first sampled step at which a Nusselt number (volume or either plate) of
-    the two differs by more than `tol` relatively.  FP32 and FP16-deviation
-    runs of the same start are stepped alongside: their first departure from
-    the FP64 run by `tol` bounds the window in which the reduced-precision
-    forms track FP64 to that tolerance.  Stops at t_h, at max_steps or
-    after budget_s seconds; a run that never departs reports a lower bound."""
+def _nudge_one_cell(g, rel=None):
+    """Change population 5 of one cell (a third of the way across, mid
+    height) by the smallest step its storage keeps: one ulp of the FP64
+    value, or, for 32-bit storage, the smallest power-of-two step that
+    survives the round trip.  Returns the absolute change."""
+    f, gg = g.get_pops()
+    j, i = f.shape[1] // 2, f.shape[2] // 3
+    v = f[5, j, i]
+    step = float(np.nextafter(v, np.inf) - v)
+    while True:
+        f2 = f.copy()
+        f2[5, j, i] = v + step
+        g.set_pops(f2, gg)
+        back = g.get_pops()[0][5, j, i]
+        if back != v:
+            return float(back - v)
+        step *= 2.0
+
+
+def predictability_horizon(lb, torch, n=1024, Ra=1e8, chunk=2000, max_steps=2000000, budget_s=420.0,
+                           tol=1e-3, stores=("f64", "f32")):
+    """Predictability horizon t_h of the chaotic RB cell (config 3): for each
+    storage in `stores`, two runs of the same start, one of them with a
+    single population of one cell changed by the smallest step the storage
+    keeps (one ulp in FP64); t_h is the first sampled step at which a
+    Nusselt number (volume or either plate) of the pair differs by more than
+    `tol` relatively.  The pairs advance together, `chunk` steps at a time,
+    until every pair has parted, max_steps, or budget_s seconds; a pair that
+    has not parted reports a lower bound."""
     import time
-    from . import LB_STORE_F16DEV, LB_STORE_F32
-    amp = 1e-3
-    runs = {"f64": (LB_STORE_F64, amp), "f64_ulp": (LB_STORE_F64, float(np.nextafter(amp, 1.0))),
-            "f32": (LB_STORE_F32, amp), "f16dev": (LB_STORE_F16DEV, amp)}
-    grids = {}
-    for name, (store, a) in runs.items():
-        w = cfg.rayleigh_benard(n, Ra, store=store, amp=a)
+    from . import STORE_NAMES
+    pairs = {}
+    for name in stores:
+        w = cfg.rayleigh_benard(n, Ra, store=STORE_NAMES[name])
         grid = dict(w.grid)
         grid.pop("store")
-        g = lb.Grid(store=store, **grid)
-        g.init(**w.params, **w.init)
-        grids[name] = g
+        a = lb.Grid(store=STORE_NAMES[name], **grid).init(**w.params, **w.init)
+        b = lb.Grid(store=STORE_NAMES[name], **grid).init(**w.params, **w.init)
+        delta = _nudge_one_cell(b)
+        pairs[name] = {"grids": (a, b), "delta": delta, "t_h": None, "last": 0.0}
     dt = w.params["dt"]
-    first = {"f64_ulp": None, "f32": None, "f16dev": None}
-    hist = []
     t0 = time.perf_counter()
     steps = 0
-
-    def rel(a, b):
-        return max(abs(x / y - 1.0) for x, y in zip(a, b))
-
+    hist = []
     while steps < max_steps and time.perf_counter() - t0 < budget_s:
-        for g in grids.values():
-            g.step_fv(chunk)
+        live = [k for k, v in pairs.items() if v["t_h"] is None]
+        if not live:
+            break
+        for k in live:
+            for g in pairs[k]["grids"]:
+                g.step_fv(chunk)
         steps += chunk
-        nu = {k: g.nusselt() for k, g in grids.items()}
-        row = {"step": steps, "nu_f64": [round(v, 6) for v in nu["f64"]]}
-        for k in first:
-            d = rel(nu[k], nu["f64"])
+        row = {"step": steps}
+        for k in live:
+            a, b = pairs[k]["grids"]
+            na, nb = a.nusselt(), b.nusselt()
+            d = max(abs(x / y - 1.0) for x, y in zip(nb, na))
+            pairs[k]["last"] = d
             row["d_" + k] = d
-            if first[k] is None and d > tol:
-                first[k] = steps
+            row["nu_" + k] = [round(v, 6) for v in na]
+            if d > tol:
+                pairs[k]["t_h"] = steps
         hist.append(row)
         print(json.dumps({"horizon_progress": row}), file=sys.stderr, flush=True)
-        if first["f64_ulp"] is not None:
-            break
-    for g in grids.values():
-        g.close()
-    return {"grid": "%d^2, Ra=%g, tanh plates, dt=%.6g" % (n, Ra, dt), "tol": tol, "sampled_every": chunk,
-            "steps_run": steps, "seconds": round(time.perf_counter() - t0, 1),
-            "t_h_steps": first["f64_ulp"], "t_h_lower_bound": None if first["f64_ulp"] else steps,
-            "f32_departs_at": first["f32"], "f16dev_departs_at": first["f16dev"],
-            "history": hist[:: max(1, len(hist) // 40)] + hist[-1:]}
+    out = {"grid": "%d^2, Ra=%g, tanh plates, dt=%.6g" % (n, Ra, dt), "tol": tol, "sampled_every": chunk,
+           "seconds": round(time.perf_counter() - t0, 1)}
+    for k, v in pairs.items():
+        for g in v["grids"]:
+            g.close()
+        out[k] = {"nudge": v["delta"], "t_h_steps": v["t_h"],
+                  "t_h_lower_bound": None if v["t_h"] else max(r["step"] for r in hist if "d_" + k in r),
+                  "last_rel_diff": v["last"]}
+    out["history"] = hist[:: max(1, len(hist) // 40)] + hist[-1:]
+    return out
 
 
 def main(argv=None):
