@@ -635,6 +635,9 @@ def main():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving stream")
     ap.add_argument("--roofline-sweep", default=None, metavar="N,N,...",
                     help="print the ST/FV roofline curve over these n x n grid sizes instead of the bench line")
+    ap.add_argument("--serving-full", type=float, default=None, metavar="LOAD",
+                    help="run the configured serving stream (2000 requests, 1e3-2e4 steps) at LOAD x the "
+                         "measured one-at-a-time capacity and print its JSON line instead of the bench line")
     ap.add_argument("--serving-requests", type=int, default=160)
     ap.add_argument("--serving-rate", type=float, default=60.0, help="Poisson arrivals per second")
     ap.add_argument("--fv-schedule", default="tune",
@@ -673,6 +676,13 @@ def main():
             r["peak"], r["peak_source"] = peak, f"{peak_kind} hbm_gbs"
             print(json.dumps(r), flush=True)
         print(json.dumps({"clocks": clk.summary()}), flush=True)
+        return
+    if args.serving_full is not None:
+        from paper_1505_03271_gb300 import serving
+        with ClockSampler(visible_gpu_index(local), period_ms=1000) as clk:
+            res = serving.full_stream(lb, torch, load=args.serving_full)
+        res["clocks"] = clk.summary()
+        print(json.dumps({"serving_full": res}), flush=True)
         return
     w = case_workload(cfg, args.case)
     g = make_grid(lb, w, stream)

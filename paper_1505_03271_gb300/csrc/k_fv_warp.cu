@@ -631,17 +631,17 @@ static cudaError_t run_warp(const StepArgs<float>& A, int chunk, cudaStream_t s)
     return cudaGetLastError();
 }
 
-// Flow grids split each strip over two warps; thermal grids step f and g in
+// Flow grids march each strip with one warp; thermal grids step f and g in
 // the strip's two warps.
 cudaError_t launch_fv_warp(Prec p, bool th, const void* args, int chunk, cudaStream_t s) {
     const StepArgs<float>& A = *static_cast<const StepArgs<float>*>(args);
     switch (p) {
         case Prec::F32:
-            return th ? run_warp<float, true, 2>(A, chunk, s) : run_warp<float, false, 2>(A, chunk, s);
+            return th ? run_warp<float, true, 2>(A, chunk, s) : run_warp<float, false, 1>(A, chunk, s);
         case Prec::F16:
-            return th ? run_warp<__half, true, 2>(A, chunk, s) : run_warp<__half, false, 2>(A, chunk, s);
+            return th ? run_warp<__half, true, 2>(A, chunk, s) : run_warp<__half, false, 1>(A, chunk, s);
         case Prec::BF16:
-            return th ? run_warp<__nv_bfloat16, true, 2>(A, chunk, s) : run_warp<__nv_bfloat16, false, 2>(A, chunk, s);
+            return th ? run_warp<__nv_bfloat16, true, 2>(A, chunk, s) : run_warp<__nv_bfloat16, false, 1>(A, chunk, s);
         default:
             return cudaErrorInvalidValue;
     }
@@ -649,9 +649,6 @@ cudaError_t launch_fv_warp(Prec p, bool th, const void* args, int chunk, cudaStr
 
 int warp_width() { return kOut; }
 // Strips per CTA and shared memory per CTA of launch_fv_warp's kernels.
-int warp_strips_per_cta() { return 2; }
-size_t warp_smem(bool th) {
-    return sizeof(float2) * ((5 + 2) * (th ? Q : 5) * 128 + 2 * 2 * 2 * 4 * 32);
-}
+int warp_strips_per_cta(bool th) { return th ? 2 : 4; }
 
 }  // namespace lbgb

@@ -139,11 +139,11 @@ int resolved_chunk(const lb_grid* G) {
     if (G->fv_chunk > 0) return G->fv_chunk;
     const bool th = G->d.thermal != 0;
     if (resolved_kernel(G) == LB_FV_WARP) {
-        // about four waves of resident CTAs (registers allow three flow or
-        // two thermal CTAs of four warps per SM)
+        // about four waves of resident CTAs (registers allow two CTAs of
+        // four warps per SM)
         const int strips = (G->nx + warp_width() - 1) / warp_width();
-        const int ctas_x = (strips + warp_strips_per_cta() - 1) / warp_strips_per_cta();
-        const long long slots = (long long)G->sms * (th ? 2 : 3);
+        const int ctas_x = (strips + warp_strips_per_cta(th) - 1) / warp_strips_per_cta(th);
+        const long long slots = (long long)G->sms * 2;
         long long chunks = (4 * slots + ctas_x - 1) / ctas_x;
         if (chunks < 1) chunks = 1;
         const int ch = (int)((G->ny + chunks - 1) / chunks);

@@ -213,8 +213,7 @@ size_t pair_smem(bool thermal);
 // per strip, warp_strips_per_cta() strips per CTA (x-periodic, FP32 arithmetic)
 cudaError_t launch_fv_warp(Prec p, bool thermal, const void* args, int chunk, cudaStream_t s);
 int warp_width();
-int warp_strips_per_cta();
-size_t warp_smem(bool thermal);
+int warp_strips_per_cta(bool thermal);
 // paired tile kernel: shape 0 = 32 x 16, 16 = 16 x 16 (x-periodic, FP32 arithmetic)
 cudaError_t launch_fv_ptile(Prec p, bool thermal, const void* args, int shape, cudaStream_t s);
 // split paired schedule: two launches per step (collision + predictor, corrector),

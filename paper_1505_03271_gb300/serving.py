@@ -134,3 +134,43 @@ def run_sequential(lb, torch, requests, store=LB_STORE_F16DEV):
                           "nu_top": nu[2]}
         clock = end
     return summarize(requests, results)
+
+
+def mean_work(steps_lo: int = 1000, steps_hi: int = 20000, sizes=SIZES) -> float:
+    """Expected cell updates of one request of the stream: E[N^2] E[steps]."""
+    return float(np.mean([n * n for n in sizes])) * 0.5 * (steps_lo + steps_hi)
+
+
+def sequential_capacity(lb, torch, sample: int = 10, steps_lo: int = 1000, steps_hi: int = 20000,
+                        store=LB_STORE_F16DEV) -> float:
+    """Requests per second the one-at-a-time path sustains on the full
+    stream's request mix: a seeded sample of requests (seeds 5 and 6, not the
+    stream's), each of every size, run back to back; capacity = measured
+    cell updates per second / the stream's mean work per request."""
+    pool = make_requests(20 * len(SIZES), 1e9, steps_lo, steps_hi, seed_arrivals=5, seed_params=6)
+    per = max(1, sample // len(SIZES))
+    reqs = []
+    for n in SIZES:  # the same number of each size, as in the stream
+        reqs += [r for r in pool if r.n == n][:per]
+    res = run_sequential(lb, torch, [Request(r.rid, 0.0, r.n, r.Ra, r.nsteps, r.params) for r in reqs], store)
+    return res["mlups"] * 1e6 / mean_work(steps_lo, steps_hi)
+
+
+def full_stream(lb, torch, load: float = 0.8, count: int = 2000, steps_lo: int = 1000, steps_hi: int = 20000,
+                capacity: float | None = None, store=LB_STORE_F16DEV):
+    """The configured serving stream: `count` requests with the full step
+    range, Poisson arrivals at `load` times the measured one-at-a-time
+    capacity, through the arrival-order server and one at a time."""
+    from . import LB_SERVE_ARRIVAL
+    cap = capacity if capacity is not None else sequential_capacity(lb, torch, steps_lo=steps_lo, steps_hi=steps_hi)
+    rate = load * cap
+    reqs = make_requests(count, rate, steps_lo, steps_hi)
+    srv = run_server(lb, reqs, store=store, policy=LB_SERVE_ARRIVAL)
+    seq = run_sequential(lb, torch, reqs, store)
+    keep = ("requests", "ok", "unstable", "cell_updates", "wall_s", "mlups", "tts_p50_s", "tts_p99_s")
+    diffs = [abs(srv["results"][r.rid]["nu_vol"] - seq["results"][r.rid]["nu_vol"]) for r in reqs
+             if srv["results"][r.rid]["status"] == 0 and seq["results"][r.rid]["status"] == 0]
+    return {"requests": count, "steps": [steps_lo, steps_hi], "load": load,
+            "capacity_req_per_s": cap, "rate_req_per_s": rate,
+            "server_arrival": {k: srv[k] for k in keep}, "sequential": {k: seq[k] for k in keep},
+            "max_abs_nu_vol_diff": max(diffs) if diffs else None}
