@@ -135,8 +135,6 @@ def make_grid(lb, w, stream, tune=True):
             g.set_fv_schedule(lb.LB_FV_PTILE, int(FV_SCHEDULE.split(":")[1]) if ":" in FV_SCHEDULE else 0)
         elif FV_SCHEDULE.startswith("tile"):
             g.set_fv_schedule(lb.LB_FV_TILE, int(FV_SCHEDULE.split(":")[1]) if ":" in FV_SCHEDULE else 0)
-        elif FV_SCHEDULE.startswith("warp"):
-            g.set_fv_schedule(lb.LB_FV_WARP, int(FV_SCHEDULE.split(":")[1]) if ":" in FV_SCHEDULE else 0)
         elif FV_SCHEDULE.startswith("march") or FV_SCHEDULE.startswith("pair"):
             kern = lb.LB_FV_MARCH if FV_SCHEDULE.startswith("march") else lb.LB_FV_PAIR
             g.set_fv_schedule(kern, int(FV_SCHEDULE.split(":")[1]) if ":" in FV_SCHEDULE else 0)
@@ -168,8 +166,6 @@ def schedule_name(lb, g, scheme):
     if k == lb.LB_FV_PTILE:
         return "fv pair-tile (f32x2) %s (halo 4)" % {0: "32x16", 14: "32x14", 16: "16x16", 512: "32x16, 512 threads",
                                                       526: "32x14, 512 threads"}[c]
-    if k == lb.LB_FV_WARP:
-        return "fv warp-march (f32x2, shuffles, two warps per strip), %d rows per CTA" % c
     return ("fv pair-march (f32x2)" if k == lb.LB_FV_PAIR else "fv march") + ", %d rows per CTA" % c
 
 

@@ -176,21 +176,14 @@ lb_status lb_get_graph_steps(lb_grid* grid, int* n, unsigned long long* replays)
  *                the predictor on the tile, then the corrector; h* and
  *                f~ + Coll - dt/2 A[h^n] pass through two library-owned FP32
  *                buffers allocated on first use (same restrictions as
- *                LB_FV_PAIR); chunk 0 = 32 x 16, 16 = 16 x 16;
- *   LB_FV_WARP:  strips of 64 columns (56 written) marched up `chunk` rows
- *                by warps of their own, with no block-wide barrier: the y
- *                stencil carried in registers, the x stencil by warp
- *                shuffles; flow strips split their populations over two
- *                warps, thermal strips step f and g in two warps (same
- *                restrictions as LB_FV_PAIR).
+ *                LB_FV_PAIR); chunk 0 = 32 x 16, 16 = 16 x 16.
  * LB_FV_AUTO picks by grid size.  For the marching kernels chunk = 0 lets
  * the library size the chunks to fill the GPU; for LB_FV_TILE chunk picks
  * the tile: 0 = 32 x 16, 16 = 16 x 16, 8 = 16 x 8 (smaller tiles recompute
  * more halo but suit small, latency-bound grids).  LB_ERR_ARG on an unknown
  * kernel or chunk. */
 typedef enum {
-    LB_FV_AUTO = 0, LB_FV_TILE = 1, LB_FV_MARCH = 2, LB_FV_PAIR = 3, LB_FV_PTILE = 4, LB_FV_SPLIT = 5,
-    LB_FV_WARP = 6
+    LB_FV_AUTO = 0, LB_FV_TILE = 1, LB_FV_MARCH = 2, LB_FV_PAIR = 3, LB_FV_PTILE = 4, LB_FV_SPLIT = 5
 } lb_fv_kernel;
 lb_status lb_set_fv_schedule(lb_grid* grid, int kernel, int chunk);
 /* The schedule lb_step_fv will use now (after AUTO has been resolved). */

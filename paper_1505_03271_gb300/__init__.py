@@ -100,7 +100,7 @@ SYMBOLS = ["lb_create_grid", "lb_init", "lb_step_fv", "lb_step_st", "lb_moments"
            "lb3_set_fv_staged_shape", "lb3_get_fv_staged_shape", "lb3_autotune_fv",
            "lb_autotune_fv", "lb_server_create", "lb_server_submit", "lb_server_pump",
            "lb_server_results", "lb_server_clock", "lb_server_destroy"]
-LB_FV_AUTO, LB_FV_TILE, LB_FV_MARCH, LB_FV_PAIR, LB_FV_PTILE, LB_FV_SPLIT, LB_FV_WARP = 0, 1, 2, 3, 4, 5, 6
+LB_FV_AUTO, LB_FV_TILE, LB_FV_MARCH, LB_FV_PAIR, LB_FV_PTILE, LB_FV_SPLIT = 0, 1, 2, 3, 4, 5
 LB_SERVE_SHARE, LB_SERVE_SHORTEST, LB_SERVE_ARRIVAL = 0, 1, 2
 LB_FV_HEUN, LB_FV_SEMI, LB_FV_EULER = 0, 1, 2
 LB3_FV_AUTO, LB3_FV_PLAIN, LB3_FV_STAGED = 0, 1, 2

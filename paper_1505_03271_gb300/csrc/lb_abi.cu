@@ -138,17 +138,6 @@ int resolved_kernel(const lb_grid* G) {
 int resolved_chunk(const lb_grid* G) {
     if (G->fv_chunk > 0) return G->fv_chunk;
     const bool th = G->d.thermal != 0;
-    if (resolved_kernel(G) == LB_FV_WARP) {
-        // about four waves of resident CTAs (registers allow two CTAs of
-        // four warps per SM)
-        const int strips = (G->nx + warp_width() - 1) / warp_width();
-        const int ctas_x = (strips + warp_strips_per_cta(th) - 1) / warp_strips_per_cta(th);
-        const long long slots = (long long)G->sms * 2;
-        long long chunks = (4 * slots + ctas_x - 1) / ctas_x;
-        if (chunks < 1) chunks = 1;
-        const int ch = (int)((G->ny + chunks - 1) / chunks);
-        return ch < 32 ? 32 : ch;
-    }
     const bool pr = resolved_kernel(G) == LB_FV_PAIR;
     const int width = pr ? pair_width() : march_width(G->prec, th);
     const int strips = (G->nx + width - 1) / width;
@@ -194,7 +183,6 @@ cudaError_t launch_fv_step(lb_grid* G) {
         return launch_fv_split(G->prec, th, &A, G->fv_chunk, G->stream);
     }
     if (k == LB_FV_PAIR) return launch_fv_pair(G->prec, th, &A, resolved_chunk(G), G->stream);
-    if (k == LB_FV_WARP) return launch_fv_warp(G->prec, th, &A, resolved_chunk(G), G->stream);
     if (k == LB_FV_PTILE) return launch_fv_ptile(G->prec, th, &A, G->fv_kernel == LB_FV_PTILE ? G->fv_chunk : 0,
                                                  G->stream);
     if (k == LB_FV_MARCH) return launch_fv_march(G->prec, th, &A, resolved_chunk(G), G->stream);
@@ -599,7 +587,7 @@ lb_status lb_get_graph_steps(lb_grid* G, int* n, unsigned long long* replays) {
 
 lb_status lb_set_fv_schedule(lb_grid* G, int kernel, int chunk) {
     if (!G) return fail(LB_ERR_ARG, "grid is NULL");
-    if (kernel < LB_FV_AUTO || kernel > LB_FV_WARP) return fail(LB_ERR_ARG, "unknown FV kernel %d", kernel);
+    if (kernel < LB_FV_AUTO || kernel > LB_FV_SPLIT) return fail(LB_ERR_ARG, "unknown FV kernel %d", kernel);
     if (chunk < 0) return fail(LB_ERR_ARG, "chunk must be >= 0");
     if (kernel == LB_FV_TILE && chunk != 0 && chunk != 8 && chunk != 16)
         return fail(LB_ERR_ARG, "tile shape must be 0 (32 x 16), 16 (16 x 16) or 8 (16 x 8)");
@@ -608,8 +596,7 @@ lb_status lb_set_fv_schedule(lb_grid* G, int kernel, int chunk) {
                                 "512 threads) or 526 (32 x 14, 512 threads)");
     if (kernel == LB_FV_SPLIT && chunk != 0 && chunk != 16)
         return fail(LB_ERR_ARG, "split tile shape must be 0 (32 x 16) or 16 (16 x 16)");
-    if ((kernel == LB_FV_PAIR || kernel == LB_FV_PTILE || kernel == LB_FV_SPLIT || kernel == LB_FV_WARP) &&
-        !pair_ok(G))
+    if ((kernel == LB_FV_PAIR || kernel == LB_FV_PTILE || kernel == LB_FV_SPLIT) && !pair_ok(G))
         return fail(LB_ERR_ARG, "the paired FV kernel needs FP32/FP16/BF16 storage and a periodic x axis");
     G->fv_kernel = kernel;
     G->fv_chunk = chunk;
@@ -682,8 +669,8 @@ lb_status lb_autotune_fv(lb_grid* G, int steps) {
             cands.push_back({LB_FV_SPLIT, 16});
         }
     }
-    for (int kern : {(int)LB_FV_MARCH, (int)LB_FV_PAIR, (int)LB_FV_WARP}) {
-        if ((kern == LB_FV_PAIR || kern == LB_FV_WARP) && !pair_ok(G)) continue;
+    for (int kern : {(int)LB_FV_MARCH, (int)LB_FV_PAIR}) {
+        if (kern == LB_FV_PAIR && !pair_ok(G)) continue;
         G->fv_kernel = kern;
         G->fv_chunk = 0;
         const int base = resolved_chunk(G);

@@ -209,11 +209,6 @@ size_t march_smem(Prec p, bool thermal);
 cudaError_t launch_fv_pair(Prec p, bool thermal, const void* args, int chunk, cudaStream_t s);
 int pair_width();
 size_t pair_smem(bool thermal);
-// warp-marching FV kernel: strips of warp_width() output columns, two warps
-// per strip, warp_strips_per_cta() strips per CTA (x-periodic, FP32 arithmetic)
-cudaError_t launch_fv_warp(Prec p, bool thermal, const void* args, int chunk, cudaStream_t s);
-int warp_width();
-int warp_strips_per_cta(bool thermal);
 // paired tile kernel: shape 0 = 32 x 16, 16 = 16 x 16 (x-periodic, FP32 arithmetic)
 cudaError_t launch_fv_ptile(Prec p, bool thermal, const void* args, int shape, cudaStream_t s);
 // split paired schedule: two launches per step (collision + predictor, corrector),

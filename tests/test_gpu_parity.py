@@ -204,8 +204,7 @@ def test_fv_step_f64(lbgpu, oracle, case, sched):
         assert np.abs(ggg - ggr).max() < 1e-13
 
 
-@pytest.mark.parametrize("sched", [(1, 0), (2, 16), (3, 8), (3, 16), (3, 0), (4, 0), (4, 14), (4, 16), (4, 512), (4, 526), (5, 0), (5, 16),
-                                   (6, 8), (6, 13), (6, 0)],
+@pytest.mark.parametrize("sched", [(1, 0), (2, 16), (3, 8), (3, 16), (3, 0), (4, 0), (4, 14), (4, 16), (4, 512), (4, 526), (5, 0), (5, 16)],
                          ids=lambda s: f"k{s[0]}c{s[1]}")
 @pytest.mark.parametrize("case", [c for c in FV_CASES if c.get("bcx", 0) == 0],
                          ids=lambda c: "-".join(f"{k}{v}" for k, v in c.items()))
@@ -507,14 +506,14 @@ def test_autotune_keeps_state_and_results(lbgpu, oracle):
     assert np.abs(fg - fr).max() < 1e-13 and np.abs(gg - gr).max() < 1e-13
 
 
-@pytest.mark.parametrize("kernel", ["auto", "warp"])
+@pytest.mark.parametrize("kernel", ["auto", "pair"])
 def test_config_rb1024_strip(lbgpu, oracle, kernel):
     """1024^2 RB at Ra = 1e8 with FP16 deviation storage: a full-height strip
     advanced 2 FV steps by the oracle from the GPU's state matches the GPU
-    (the default schedule, and the warp march at its automatic chunk)."""
+    (the default schedule, and the paired march at its automatic chunk)."""
     from paper_1505_03271_gb300 import configs as cfg
     w = cfg.rayleigh_benard(1024, 1e8, store=lbgpu.LB_STORE_F16DEV)
-    sched = None if kernel == "auto" else (lbgpu.LB_FV_WARP, 0)
+    sched = None if kernel == "auto" else (lbgpu.LB_FV_PAIR, 0)
     _strip_compare(lbgpu, oracle, w, 2, 24, 500, 4e-3, schedule=sched)
 
 
@@ -524,9 +523,8 @@ def test_config_channel_strip_f32(lbgpu, oracle):
     _strip_compare(lbgpu, oracle, w, 3, 30, 100, 1e-5)
 
 
-@pytest.mark.parametrize("kernel", ["pair", "warp"])
 @pytest.mark.parametrize("case", ["tgv2048", "channel2048x1024"])
-def test_pair_march_auto_chunk_strip(lbgpu, oracle, case, kernel):
+def test_pair_march_auto_chunk_strip(lbgpu, oracle, case):
     """The paired marching kernel at its automatic chunk (the rows per CTA
     that large grids run with, far more than the small-grid tests use), on
     a 2048^2 periodic TGV and on a 2048 x 1024 tanh-walled channel: a 3-step
@@ -538,9 +536,8 @@ def test_pair_march_auto_chunk_strip(lbgpu, oracle, case, kernel):
                          dict(tau=0.3, dt=0.5, ax=1e-6), dict(kind=0, u0=0.02, amp=0.01, mode=3), 3, "fv")
     else:
         w = cfg.channel(u_max=0.05, nx=2048, ny=1024)
-    k = lbgpu.LB_FV_PAIR if kernel == "pair" else lbgpu.LB_FV_WARP
-    got, chunk = _strip_compare(lbgpu, oracle, w, 3, 30, 777, 2e-6, schedule=(k, 0))
-    assert got == k and chunk >= 32
+    got, chunk = _strip_compare(lbgpu, oracle, w, 3, 30, 777, 2e-6, schedule=(lbgpu.LB_FV_PAIR, 0))
+    assert got == lbgpu.LB_FV_PAIR and chunk >= 32
 
 
 # ------------------------------------------------------------ observables --
