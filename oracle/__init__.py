@@ -10,11 +10,9 @@ face generators, Lagrange/QUICK weights, equilibrium, Guo force, the ST step,
 the FV step, the wall rules (the isothermal plates through the exactly
 steady conduction state) and the observables.
 
-Parity unpinned: the force part of the FV advected field, h = ... + dt/2 F
-(the literal form of Sec. II B 5).  The exact inverse of the tilde
-transformation would carry (dt/2)(1 - dt/(2 tau~)) F instead; the two differ
-by O(dt^2 F / tau~), below what the Poiseuille pins resolve, so no test
-tells them apart.
+The force part of the FV advected field is (dt/2)(1 - dt/(2 tau~)) F, the
+plain population of Appendix A's inversion; its pin is the hydrostatic
+column that stays at rest (tests/test_oracle_steps.py).
 """
 from __future__ import annotations
 

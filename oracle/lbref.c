@@ -26,11 +26,12 @@
  *     part alike (the FV counterpart of anti-bounce-back).
  *   - Streaming walls use half-way bounce-back (f) and anti-bounce-back (g).
  *
- * Parity unpinned: the force part of the FV advected field h is the literal
- * dt/2 F of Sec. II B 5.  The exact inverse of the tilde transformation would
- * give (dt/2)(1 - dt/(2 tau~)) F; the difference, O(dt^2 F / tau~), lies below
- * what the Poiseuille pins resolve.  Every other routine has a pin in the
- * oracle tests.
+ *   - The FV advected field is the plain population f of Appendix A, which
+ *     inverts the tilde transformation as f = f~ + dt/(2 tau + dt)(f~_eq -
+ *     f~) + dt/2 F with the tilded equilibrium f~_eq = f_eq - dt/2 F: its
+ *     force part is (dt/2)(1 - dt/(2 tau~)) F, so that sum c h = rho u and a
+ *     fluid at rest in hydrostatic balance stays at rest.
+ * Every routine has a pin in the oracle tests.
  */
 #include "lbref.h"
 
@@ -478,7 +479,9 @@ int ref_step_st(ref_grid* G, int nsteps) {
 /* ------------------------------------------------------------------ */
 
 /* For every fluid cell: the advected field
- *   h = f~ + dt/(2 tau~) (f_eq - f~) + dt/2 F      (bracket of Eq. (semi))
+ *   h = f~ + dt/(2 tau~) (f_eq - f~) + dt/2 (1 - dt/(2 tau~)) F
+ * (the bracket of Eq. (semi), i.e. the plain population of Appendix A's
+ * inversion with f~_eq = f_eq - dt/2 F)
  * and the collision + force term
  *   coll = dt/tau~ (f_eq - f~) + dt (1 - dt/(2 tau~)) F.
  * Thermal: hg = g~ + dt/(2 tau~_g)(g_eq - g~), collg = dt/tau~_g (g_eq - g~),
@@ -500,7 +503,7 @@ static void fv_eval(ref_grid* G, const double* f, const double* gsrc, double* co
             ref_guo_force(rho, ux, uy, ax, ay, F);
             for (int a = 0; a < Q; ++a) {
                 G->h[PIDX(G, a, i, j)] =
-                    fc[a] + dt / (2.0 * taut) * (feq[a] - fc[a]) + 0.5 * dt * F[a];
+                    fc[a] + dt / (2.0 * taut) * (feq[a] - fc[a]) + 0.5 * dt * (1.0 - dt / (2.0 * taut)) * F[a];
                 coll[IDX(G, a, i, j)] =
                     dt / taut * (feq[a] - fc[a]) + dt * (1.0 - dt / (2.0 * taut)) * F[a];
                 if (th) {

@@ -325,7 +325,8 @@ int ref3_step_st(ref3_grid* G, int nsteps) {
     return 0;
 }
 
-/* h = f~ + dt/(2 tau~)(f_eq - f~) + dt/2 F and coll = dt/tau~ (f_eq - f~)
+/* h = f~ + dt/(2 tau~)(f_eq - f~) + dt/2 (1 - dt/(2 tau~)) F (the plain
+ * population of Appendix A's inversion) and coll = dt/tau~ (f_eq - f~)
  * + dt (1 - dt/(2 tau~)) F; thermal hg, collg with g_eq = (T/rho) f_eq. */
 static void fv_eval3(ref3_grid* G, const double* f, const double* gsrc, double* coll, double* collg) {
     const ref3_params* p = &G->p;
@@ -342,7 +343,8 @@ static void fv_eval3(ref3_grid* G, const double* f, const double* gsrc, double* 
                 ref3_equilibrium(rho, u[0], u[1], u[2], feq);
                 ref3_guo_force(rho, u[0], u[1], u[2], acc[0], acc[1], acc[2], F);
                 for (int a = 0; a < Q3; ++a) {
-                    G->h[P3(G, a, i, j, k)] = fc[a] + dt / (2.0 * taut) * (feq[a] - fc[a]) + 0.5 * dt * F[a];
+                    G->h[P3(G, a, i, j, k)] =
+                        fc[a] + dt / (2.0 * taut) * (feq[a] - fc[a]) + 0.5 * dt * (1.0 - dt / (2.0 * taut)) * F[a];
                     coll[I3(G, a, i, j, k)] = dt / taut * (feq[a] - fc[a]) + dt * (1.0 - dt / (2.0 * taut)) * F[a];
                     if (th) {
                         double geq = (T / rho) * feq[a];

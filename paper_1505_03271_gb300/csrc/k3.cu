@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(256) k3_pre(const Args3<R> A) {
         R feqd, F, geqd;
         m.eq(a, A, feqd, F, geqd);
         const R neq = feqd - d[a];
-        A.H[a * NP + cp] = d[a] + A.omh * neq + A.hf * F;
+        A.H[a * NP + cp] = d[a] + A.omh * neq + A.hF * F;
         A.FC[a * N + c] = d[a] + A.om * neq + A.cf * F;
         if constexpr (TH) {
             const R neqg = geqd - e[a];
@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(256, sizeof(R) == 8 ? 1 : 2) k3_star(const Arg
         R feqd, F, geqd;
         m.eq(a, A, feqd, F, geqd);
         const R fs = A.HS[a * NP + cp];
-        A.HS[a * NP + cp] = fs + A.omh * (feqd - fs) + A.hf * F;
+        A.HS[a * NP + cp] = fs + A.omh * (feqd - fs) + A.hF * F;
         if constexpr (TH) {
             const R es = A.HGS[a * NP + cp];
             A.HGS[a * NP + cp] = es + A.omgh * (geqd - es);

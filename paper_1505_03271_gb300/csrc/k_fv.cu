@@ -190,7 +190,7 @@ __device__ __forceinline__ void fv_tile(const StepArgs<R>& A, const int x0, cons
             R feqd, F, geqd = 0;
             m.eq(a, A, feqd, F, geqd);
             const R neq = feqd - d[a];
-            sH[a * NE + k] = d[a] + A.omh * neq + A.hf * F;          // h, Eq. (semi) bracket
+            sH[a * NE + k] = d[a] + A.omh * neq + A.hF * F;          // h, Eq. (semi) bracket
             if (inB) sFC[a * NB + kb] = d[a] + A.om * neq + A.cf * F;  // f~ + Coll
             if constexpr (TH) {
                 const R neqg = geqd - e[a];
@@ -247,7 +247,7 @@ __device__ __forceinline__ void fv_tile(const StepArgs<R>& A, const int x0, cons
         for (int a = 0; a < Q; ++a) {
             R feqd, F, geqd = 0;
             m.eq(a, A, feqd, F, geqd);
-            sHs[a * NB + k] = fs[a] + A.omh * (feqd - fs[a]) + A.hf * F;
+            sHs[a * NB + k] = fs[a] + A.omh * (feqd - fs[a]) + A.hF * F;
             if constexpr (TH) sHs[(Q + a) * NB + k] = es[a] + A.omgh * (geqd - es[a]);
         }
     }

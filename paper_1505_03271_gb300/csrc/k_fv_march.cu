@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(NT) k_fv_march(const StepArgs<R> A, const int 
                         R feqd, F, geqd = 0;
                         m.eq(a, A, feqd, F, geqd);
                         const R neq = feqd - d[a];
-                        sH[(s * NQ + a) * NT + k] = d[a] + A.omh * neq + A.hf * F;
+                        sH[(s * NQ + a) * NT + k] = d[a] + A.omh * neq + A.hF * F;
                         sP[(s * NQ + a) * NT + k] = d[a] + A.om * neq + A.cf * F;
                         if constexpr (TH) {
                             const R neqg = geqd - e[a];
@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(NT) k_fv_march(const StepArgs<R> A, const int 
                         for (int a = 0; a < Q; ++a) {
                             R feqd, F, geqd = 0;
                             m.eq(a, A, feqd, F, geqd);
-                            sS[(s * NQ + a) * NT + k] = fs[a] + A.omh * (feqd - fs[a]) + A.hf * F;
+                            sS[(s * NQ + a) * NT + k] = fs[a] + A.omh * (feqd - fs[a]) + A.hF * F;
                             if constexpr (TH) sS[(s * NQ + Q + a) * NT + k] = es[a] + A.omgh * (geqd - es[a]);
                         }
                     }

@@ -300,7 +300,7 @@ __global__ void __launch_bounds__(NT) k_fv_pair(const StepArgs<float> A, const i
                     const V2 neq = c.feqd[a] - d[a];
                     if (ring_depth(a) > 0)
                         sH[(ring_off(a) + (ring_depth(a) == 5 ? s : t3)) * NT + k] =
-                            fma2(bc(A.omh), neq, fma2(bc(A.hf), c.F[a], d[a]));
+                            fma2(bc(A.omh), neq, fma2(bc(A.hF), c.F[a], d[a]));
                     sP[(s * NQ + a) * NT + k] = fma2(bc(A.om), neq, fma2(bc(A.cf), c.F[a], d[a]));
                     if constexpr (TH) {
                         const V2 neqg = c.geqd[a] - e[a];
@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(NT) k_fv_pair(const StepArgs<float> A, const i
                             if (ring_depth(a) == 0) continue;
                             const int sa = ring_depth(a) == 5 ? s : c3b;
                             sS[(ring_off(a) + sa) * NT + k] =
-                                fma2(bc(A.omh), c.feqd[a] - fs[a], fma2(bc(A.hf), c.F[a], fs[a]));
+                                fma2(bc(A.omh), c.feqd[a] - fs[a], fma2(bc(A.hF), c.F[a], fs[a]));
                             if constexpr (TH)
                                 sS[(ring_off(Q + a) + sa) * NT + k] = fma2(bc(A.omgh), c.geqd[a] - es[a], es[a]);
                         }
@@ -595,7 +595,7 @@ __device__ __forceinline__ void ptile_body(const StepArgs<float>& A, const int x
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
             const V2 neq = c.feqd[a] - d[a];
-            sH[a * NE + k] = fma2(bc(A.omh), neq, fma2(bc(A.hf), c.F[a], d[a]));
+            sH[a * NE + k] = fma2(bc(A.omh), neq, fma2(bc(A.hF), c.F[a], d[a]));
             if (inB) sFC[a * NB + kb] = fma2(bc(A.om), neq, fma2(bc(A.cf), c.F[a], d[a]));
             if constexpr (TH) {
                 const V2 neqg = c.geqd[a] - e[a];
@@ -636,7 +636,7 @@ __device__ __forceinline__ void ptile_body(const StepArgs<float>& A, const int x
         c.build(fs, es, A, Y.ro, TH ? Y.to : 0.0f);
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
-            sHs[a * NB + k] = fma2(bc(A.omh), c.feqd[a] - fs[a], fma2(bc(A.hf), c.F[a], fs[a]));
+            sHs[a * NB + k] = fma2(bc(A.omh), c.feqd[a] - fs[a], fma2(bc(A.hF), c.F[a], fs[a]));
             if constexpr (TH) sHs[(Q + a) * NB + k] = fma2(bc(A.omgh), c.geqd[a] - es[a], es[a]);
         }
     }
@@ -722,7 +722,7 @@ __global__ void __launch_bounds__(NTH) k_fv_split_a(const StepArgs<float> A) {
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
             const V2 neq = c.feqd[a] - d[a];
-            sH[a * NB + k] = fma2(bc(A.omh), neq, fma2(bc(A.hf), c.F[a], d[a]));
+            sH[a * NB + k] = fma2(bc(A.omh), neq, fma2(bc(A.hF), c.F[a], d[a]));
             if (inT) sFC[a * NT + kt] = fma2(bc(A.om), neq, fma2(bc(A.cf), c.F[a], d[a]));
             if constexpr (TH) {
                 const V2 neqg = c.geqd[a] - e[a];
@@ -762,7 +762,7 @@ __global__ void __launch_bounds__(NTH) k_fv_split_a(const StepArgs<float> A) {
         c.build(fs, es, A, Y.ro, TH ? Y.to : 0.0f);
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
-            const V2 hs = fma2(bc(A.omh), c.feqd[a] - fs[a], fma2(bc(A.hf), c.F[a], fs[a]));
+            const V2 hs = fma2(bc(A.omh), c.feqd[a] - fs[a], fma2(bc(A.hF), c.F[a], fs[a]));
             float* p = A.xh + a * A.plane + at;
             if (both) PairIO<float>::st(p, hs);
             else *p = hs.v.x;

@@ -69,6 +69,7 @@ struct Args3 {
     AxisMetric<R> m[3]; // QUICK weights and 1/width per axis
     const R* ft[3];     // the same, face-major (kFaceRow values per face)
     R dt, om, omh, cf, hf, omg, omgh;
+    R hF;  // force part of the advected field: dt/2 (1 - dt/(2 tau~))
     R ax, ay, az, bg, T0, dTb, dTt;  // dTb, dTt: plate temperature - T0 (z walls)
     // staged flux passes (k3_staged.cu): status word a CTA sets when a bounded
     // wait runs out, the limit of each wait, and the test hook that leaves

@@ -138,6 +138,7 @@ Args3<R> args3(const lb3_grid* G, bool st) {
     A.omh = (R)(dt / (2.0 * taut));
     A.cf = (R)(dt * (1.0 - dt / (2.0 * taut)));
     A.hf = (R)(0.5 * dt);
+    A.hF = (R)(0.5 * dt * (1.0 - dt / (2.0 * taut)));
     A.omg = (R)(dt / taugt);
     A.omgh = (R)(dt / (2.0 * taugt));
     A.ax = (R)p.ax;

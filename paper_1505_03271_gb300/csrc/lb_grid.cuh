@@ -166,6 +166,9 @@ inline StepArgs<R> step_args(const lb_grid* G, double dt) {
     A.omh = (R)(dt / (2.0 * taut));
     A.cf = (R)(dt * (1.0 - dt / (2.0 * taut)));
     A.hf = (R)(0.5 * dt);
+    // the advected field is the plain population f (Appendix A inverts the
+    // tilde transformation): its force part is dt/2 (1 - dt/(2 tau~)) F
+    A.hF = (R)(0.5 * dt * (1.0 - dt / (2.0 * taut)));
     A.omg = (R)(dt / taugt);
     A.omgh = (R)(dt / (2.0 * taugt));
     A.stages = G->fv_scheme == LB_FV_HEUN ? 2 : 1;
@@ -175,6 +178,7 @@ inline StepArgs<R> step_args(const lb_grid* G, double dt) {
         A.omh = (R)0;
         A.cf = (R)dt;
         A.hf = (R)0;
+        A.hF = (R)0;
         A.omg = (R)(dt / p.tau_g);
         A.omgh = (R)0;
     }

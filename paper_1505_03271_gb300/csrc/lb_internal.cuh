@@ -94,6 +94,7 @@ struct StepArgs {
     AxisMetric<R> mx, my;
     int stages;             // 2: Heun corrector (Eq. (semi-heun)); 1: the predictor is the new state
     R dt, om, omh, cf, hf;  // dt/tau~, dt/(2 tau~), dt (1 - dt/(2 tau~)), dt/2 (Euler: dt/tau, 0, dt, 0)
+    R hF;                   // force part of the advected field: dt/2 (1 - dt/(2 tau~)) (Euler: 0)
     R omg, omgh;            // dt/tau~_g, dt/(2 tau~_g)
     R ax, ay, bg;           // external acceleration, beta * grav
     R dTb, dTt;             // T_bot - T0, T_top - T0

@@ -80,7 +80,9 @@ class Exact:
                 cu = CX[a] * ux + CY[a] * uy
                 feq = W[a] * rho * (1 + 3 * cu + Fr(9, 2) * cu * cu - Fr(3, 2) * uu)
                 fa = W[a] * rho * ((3 * (CX[a] - ux) + 9 * cu * CX[a]) * ax + (3 * (CY[a] - uy) + 9 * cu * CY[a]) * ay)
-                hh.append(f[a] + dt / (2 * tt) * (feq - f[a]) + dt / 2 * fa)
+                # the plain population of Appendix A: f = f~ + dt/(2 tau + dt)(f~_eq - f~)
+                # + dt/2 F, with the tilded equilibrium f~_eq = f_eq - dt/2 F (2 tau + dt = 2 tau~)
+                hh.append(f[a] + dt / (2 * tt) * ((feq - dt / 2 * fa) - f[a]) + dt / 2 * fa)
                 cc.append(dt / tt * (feq - f[a]) + dt * (1 - dt / (2 * tt)) * fa)
                 if self.th:
                     geq = T / rho * feq

@@ -78,7 +78,9 @@ class Exact3:
                 ca = sum(C3[a][x] * acc[x] for x in range(3))
                 feq = W3[a] * rho * (1 + 3 * cu + Fr(9, 2) * cu * cu - Fr(3, 2) * uu)
                 fa = W3[a] * rho * (3 * (ca - ua) + 9 * cu * ca)
-                hh.append(f[a] + dt / (2 * tt) * (feq - f[a]) + dt / 2 * fa)
+                # the plain population of Appendix A: f = f~ + dt/(2 tau + dt)(f~_eq - f~)
+                # + dt/2 F, with the tilded equilibrium f~_eq = f_eq - dt/2 F (2 tau + dt = 2 tau~)
+                hh.append(f[a] + dt / (2 * tt) * ((feq - dt / 2 * fa) - f[a]) + dt / 2 * fa)
                 cc.append(dt / tt * (feq - f[a]) + dt * (1 - dt / (2 * tt)) * fa)
                 if self.th:
                     g = G[cell][a]

@@ -369,6 +369,29 @@ def test_rb_barometric_start_is_at_rest_fv_interior(oracle, sy):
         assert res[bg, "uniform"] > 0.2 * dt * bg
 
 
+@pytest.mark.parametrize("dt", [0.5, 0.25])
+def test_hydrostatic_column_stays_at_rest(oracle, dt):
+    """A column between walls under a uniform body force a_y, started in
+    hydrostatic balance (c_s^2 d rho/dy = rho a_y): a fluid at rest under
+    gravity stays at rest.  In the middle quarter of the column (away from
+    the first-order wall layers of Sec. II B 5) the FV state settles at
+    |u_y| below 1e-4 |a_y|, independent of dt.  This pins the force part of the advected field:
+    with the plain population of Appendix A, (dt/2)(1 - dt/(2 tau~)) F, the
+    advected mass flux sum c h equals rho u; with dt/2 F it would carry an
+    extra dt^2 rho a / (4 tau~), and the steady column would drift at
+    u_y = -dt^2 a_y / (4 tau~) (1.4e-4 at dt = 0.5 here)."""
+    ny, tau, ay = 32, 0.2, -1e-3
+    g = _grid(oracle, 3, ny, ly=float(ny), bcy=1).set_params(tau=tau, dt=dt, ay=ay)
+    yc = g.centers()[1]
+    rho = np.exp(3 * ay * (yc - ny / 2))[:, None] * np.ones((ny, 3))
+    g.init_fields(rho, np.zeros_like(rho), np.zeros_like(rho), None)
+    g.step_fv(int(12000 / dt))
+    uy = g.moments()[2][:, 0]
+    literal = -dt * dt * ay / (4 * (tau + dt / 2))
+    assert np.abs(uy[12:20]).max() < 1e-4 * abs(ay)
+    assert np.abs(uy[12:20]).max() < 0.01 * abs(literal)
+
+
 def _golden_rb():
     import os
     path = os.path.join(os.path.dirname(__file__), "golden", "rb_ra1e4.txt")
