@@ -584,6 +584,27 @@ def test_rb_barometric_rest_state(lbgpu, oracle, scheme, sy, store, tol):
     assert np.abs(ux - vx).max() < tol and np.abs(uy - vy).max() < tol
 
 
+@pytest.mark.parametrize("store,tol", [("f64", 1e-13), ("f32", 2e-7)])
+def test_hydrostatic_column_gpu(lbgpu, oracle, store, tol):
+    """The hydrostatic column under uniform a_y (the oracle pin of the
+    advected field's force part): after 4000 FV steps the GPU's velocities
+    match the oracle's to the storage's rounding, and the column's middle
+    stays at rest (|u_y| < 1e-4 |a_y|)."""
+    ny, ay = 32, -1e-3
+    g, r = pair(lbgpu, oracle, 6, ny, store, ly=float(ny), bcy=1, tau=0.2, dt=0.5, ay=ay)
+    yc = r.centers()[1]
+    rho = np.exp(3 * ay * (yc - ny / 2))[:, None] * np.ones((ny, 6))
+    zero = np.zeros_like(rho)
+    g.init(tau=0.2, dt=0.5, ay=ay, rho=rho, ux=zero, uy=zero)
+    r.init_fields(rho, zero, zero, None)
+    g.step_fv(4000)
+    r.step_fv(4000)
+    _, ux, uy, _ = g.moments()
+    _, vx, vy, _ = r.moments()
+    assert np.abs(uy - vy).max() < tol and np.abs(ux - vx).max() < tol
+    assert np.abs(uy[12:20]).max() < 1e-4 * abs(ay)
+
+
 def test_rb_nusselt_f16_vs_oracle(lbgpu, oracle):
     """Reduced-precision storage: FP16 deviation storage keeps the Nusselt
     numbers within 1e-3 of the FP64 oracle over 500 FV steps of an RB cell."""
