@@ -570,6 +570,7 @@ cudaError_t launch3_st(Prec p, bool th, const void* args, cudaStream_t s) {
     }
     if (p == Prec::F32) {
         const auto& A = *static_cast<const Args3<float>*>(args);
+        if (st3_pair_ok(p, A.n)) return launch3_st_pair(th, args, s);
         return th ? run_st3<float, float, true>(A, s) : run_st3<float, float, false>(A, s);
     }
     return cudaErrorInvalidValue;

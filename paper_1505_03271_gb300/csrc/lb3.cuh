@@ -100,6 +100,9 @@ bool adv3_staged_shape_ok(const int* n, Prec p, int ty, int kc, int ahead);
 void adv3_staged_resolve(const int* n, Prec p, int* ty, int* kc, int* ahead);
 cudaError_t launch3_adv_staged(Prec p, bool corr, int np, const void* args, cudaStream_t s);
 cudaError_t launch3_st(Prec p, bool th, const void* args, cudaStream_t s);
+// the paired FP32 ST step (k3_st_pair.cu): grids with an even nx
+bool st3_pair_ok(Prec p, const int* n);
+cudaError_t launch3_st_pair(bool th, const void* args, cudaStream_t s);
 // fields [5][N] (rho, ux, uy, uz, T) on the device -> storage (equilibrium in tilded variables)
 cudaError_t launch3_init(Prec p, bool th, const Aux3& a, const double* fields, void* f, void* g, cudaStream_t s);
 // storage -> fields [5][N]
