@@ -70,7 +70,11 @@ def test_fv3_step(lbgpu, oracle, case, store):
 
 @pytest.mark.parametrize("store", ["f64", "f32"])
 @pytest.mark.parametrize("case", [dict(nx=9, ny=7, nz=6), dict(nx=8, ny=6, nz=10, bcz=1, thermal=True),
-                                  dict(nx=6, ny=5, nz=7, bcy=1, bcz=1), dict(nx=1, ny=10, nz=8, bcz=1, thermal=True)],
+                                  dict(nx=6, ny=5, nz=7, bcy=1, bcz=1), dict(nx=1, ny=10, nz=8, bcz=1, thermal=True),
+                                  # even widths take the paired kernel: whole warps, a partial
+                                  # last warp, periodic wrap at the row ends, plates on z
+                                  dict(nx=130, ny=9, nz=5), dict(nx=64, ny=6, nz=7, bcz=1, thermal=True),
+                                  dict(nx=2, ny=4, nz=3)],
                          ids=_ids)
 def test_st3_step(lbgpu, oracle, case, store):
     lb = lbgpu
