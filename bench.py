@@ -146,6 +146,8 @@ def make_grid(lb, w, stream, tune=True):
 def schedule_name(lb, g, scheme):
     if isinstance(g, lb.Grid3):
         if scheme != "fv":
+            if g.store == lb.LB_STORE_F32 and g.desc.nx % 2 == 0:
+                return "3-D st pair (f32x2), two cells per thread, push"
             return "3-D st push"
         if g.fv_schedule == lb.LB3_FV_STAGED:
             return "3-D fv four passes (collision; staged predictor; star; staged corrector)"

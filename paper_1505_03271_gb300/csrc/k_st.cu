@@ -98,64 +98,7 @@ __global__ void __launch_bounds__(256, TH ? 2 : 4) k_st_pair(const StepArgs<floa
     m.build(d, e, A, ro, to);
     // Interior pairs (both cells and all their neighbours inside the grid)
     // stream to fixed offsets with no wrap or wall test.
-    const bool interior = x >= 1 && x + 2 < A.nx && y >= 1 && y + 1 < A.ny;
-    // Whole warps of interior pairs store every population as aligned pairs:
-    // a population moving in x is realigned across lanes by one shuffle (the
-    // value that crosses a pair boundary), and only the warp's end lanes add
-    // single stores for the cells whose pair another warp writes.
-    const unsigned act = __activemask();
-    if (act == 0xffffffffu && __all_sync(act, interior)) {
-        const int lane = threadIdx.x & 31;
-        const float rdn = A.roff[y - 1], rup = A.roff[y + 1];
-        const float tdn = TH ? A.toff[y - 1] : 0.0f, tup = TH ? A.toff[y + 1] : 0.0f;
-#pragma unroll
-        for (int a = 0; a < Q; ++a) {
-            const float w = wgt<float>(a);
-            const float rt = cy(a) > 0 ? rup : (cy(a) < 0 ? rdn : ro);
-            const float tt = cy(a) > 0 ? tup : (cy(a) < 0 ? tdn : to);
-            const V2 post = fma2(bc(A.om), m.feqd[a] - d[a], fma2(bc(A.cf), m.F[a], d[a])) + bc(w * (ro - rt));
-            V2 gpost = bc(0.0f);
-            if (TH) gpost = fma2(bc(A.omg), m.geqd[a] - e[a], e[a]) + bc(w * (to - tt));
-            // the destination row's pair that starts at column x
-            const long long o = a * A.plane + c + (long long)cy(a) * A.pitch;
-            if (cx(a) == 0) {
-                PairIO<S>::st(fout + o, post);
-                if (TH) PairIO<S>::st(gout + o, gpost);
-            } else if (cx(a) > 0) {
-                // cells x, x+1 move to x+1, x+2: the pair at x is (x-1's, x's)
-                const float pf = __shfl_up_sync(0xffffffffu, post.v.y, 1);
-                const float pg = TH ? __shfl_up_sync(0xffffffffu, gpost.v.y, 1) : 0.0f;
-                if (lane > 0) {
-                    PairIO<S>::st(fout + o, mk(pf, post.v.x));
-                    if (TH) PairIO<S>::st(gout + o, mk(pg, gpost.v.x));
-                } else {
-                    Store<S>::st(fout + o + 1, post.v.x);
-                    if (TH) Store<S>::st(gout + o + 1, gpost.v.x);
-                }
-                if (lane == 31) {
-                    Store<S>::st(fout + o + 2, post.v.y);
-                    if (TH) Store<S>::st(gout + o + 2, gpost.v.y);
-                }
-            } else {
-                // cells x, x+1 move to x-1, x: the pair at x is (x+1's, x+2's)
-                const float nf = __shfl_down_sync(0xffffffffu, post.v.x, 1);
-                const float ng = TH ? __shfl_down_sync(0xffffffffu, gpost.v.x, 1) : 0.0f;
-                if (lane < 31) {
-                    PairIO<S>::st(fout + o, mk(post.v.y, nf));
-                    if (TH) PairIO<S>::st(gout + o, mk(gpost.v.y, ng));
-                } else {
-                    Store<S>::st(fout + o, post.v.y);
-                    if (TH) Store<S>::st(gout + o, gpost.v.y);
-                }
-                if (lane == 0) {
-                    Store<S>::st(fout + o - 1, post.v.x);
-                    if (TH) Store<S>::st(gout + o - 1, gpost.v.x);
-                }
-            }
-        }
-        return;
-    }
-    if (interior) {
+    if (x >= 1 && x + 2 < A.nx && y >= 1 && y + 1 < A.ny) {
         const float rdn = A.roff[y - 1], rup = A.roff[y + 1];
         const float tdn = TH ? A.toff[y - 1] : 0.0f, tup = TH ? A.toff[y + 1] : 0.0f;
 #pragma unroll
