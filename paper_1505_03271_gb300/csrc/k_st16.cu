@@ -16,7 +16,8 @@
 //     warp's or a row's ends add 2- or 4-byte stores for the cells whose
 //     word another warp writes.
 // Rows at a wall on y (half-way bounce-back) store value by value; interior
-// and periodic rows take the word path.
+// and periodic rows take the word path.  On flow grids the base state is
+// rho_r = 1 on every row, so no row offsets enter the push.
 #include "lb_pair.cuh"
 
 namespace lbgb {
@@ -27,6 +28,13 @@ using namespace pairmath;
 
 template <typename S> struct Half;
 template <> struct Half<__half> {
+    static constexpr float kScale = kF16Scale;  // storage units per deviation unit
+    // two stored values as floats in storage units (no rescaling)
+    __device__ static V2 raw(unsigned u) { return {__half22float2(*reinterpret_cast<const __half2*>(&u))}; }
+    __device__ static unsigned raw_pack(V2 v) {
+        const __half2 h = __floats2half2_rn(v.v.x, v.v.y);
+        return *reinterpret_cast<const unsigned*>(&h);
+    }
     // two values -> one 32-bit word (low half = first), FP16 holds x * 2^12
     __device__ static unsigned pack(V2 v) {
         const __half2 h = __floats2half2_rn(v.v.x * kF16Scale, v.v.y * kF16Scale);
@@ -38,6 +46,12 @@ template <> struct Half<__half> {
     }
 };
 template <> struct Half<__nv_bfloat16> {
+    static constexpr float kScale = 1.0f;
+    __device__ static V2 raw(unsigned u) { return {__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u))}; }
+    __device__ static unsigned raw_pack(V2 v) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v.v.x, v.v.y);
+        return *reinterpret_cast<const unsigned*>(&h);
+    }
     __device__ static unsigned pack(V2 v) {
         const __nv_bfloat162 h = __floats2bfloat162_rn(v.v.x, v.v.y);
         return *reinterpret_cast<const unsigned*>(&h);
@@ -57,6 +71,56 @@ __device__ __forceinline__ void st64(void* base, long long i, unsigned lo, unsig
     *reinterpret_cast<uint2*>(reinterpret_cast<unsigned short*>(base) + i) = make_uint2(lo, hi);
 }
 
+// Collision of a pair of cells in storage units (deviations times K, the
+// FP16 scale 2^12 or 1 for BF16) on a flow grid, whose base state is
+// rho_r = 1 on every row.  The BGK relaxation with the Guo force,
+//   post_a = d_a + om (feq_a - f_a) + cf F_a,
+// is regrouped per pair of opposite populations a, b = inv(a): with
+// cu3 = 3 c_a.u, t = 3 c_a.a (a uniform constant), w = w_a and
+//   C0 = om (-1.5 u.u) + cf (-3 u.a),
+//   g  = (om/2) cu3 + cf t,   S = cu3 g + C0,   D = g + (om/2) cu3,
+// the two results are
+//   post_a = (1 - om) d_a + om w K (rho - 1) + w K rho (S + D),
+//   post_b = (1 - om) d_b + om w K (rho - 1) + w K rho (S - D),
+// which is the same polynomial as f_eq = w rho (1 + 3 c.u + 4.5 (c.u)^2
+// - 1.5 u.u) and F = w rho (3 (c - u).a + 9 (c.u)(c.a)) (Sec. II A), with
+// the even part S and the odd part D shared by a and b.  Moments come from
+// the sums divided by K once; no population is rescaled on load or store.
+template <typename S>
+__device__ __forceinline__ void collide_units(const V2* d, const StepArgs<float>& A, V2* post) {
+    constexpr float K = Half<S>::kScale, iK = 1.0f / K;
+    const float om = A.om, om1 = 1.0f - A.om, omh = 0.5f * A.om;
+    const V2 e1 = d[1] - d[3], e2 = d[2] - d[4], e57 = d[5] - d[7], e68 = d[6] - d[8];
+    const V2 rK = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+    const V2 jx = ((e1 + e57) - e68) * bc(iK), jy = ((e2 + e57) + e68) * bc(iK);
+    const V2 rho = fma2(rK, bc(iK), bc(1.0f));
+    const V2 ir = mk(__fdividef(1.0f, rho.v.x), __fdividef(1.0f, rho.v.y));
+    const V2 ux = fma2(jx, ir, bc(A.hf * A.ax));
+    const V2 uy = fma2(bc(A.ay), bc(A.hf), jy * ir);
+    const V2 ux3 = ux * bc(3.0f), uy3 = uy * bc(3.0f);
+    const V2 uuneg = fma2(ux, ux, uy * uy) * bc(-1.5f);
+    const V2 ua3neg = fma2(uy3, bc(-A.ay), ux3 * bc(-A.ax));
+    const V2 C0 = fma2(bc(om), uuneg, bc(A.cf) * ua3neg);
+    post[0] = fma2(rho * bc(K * wgt<float>(0)), C0, fma2(bc(om1), d[0], rK * bc(om * wgt<float>(0))));
+    const V2 wrA = rho * bc(K * wgt<float>(1)), wrD = rho * bc(K * wgt<float>(5));
+    const V2 bA = rK * bc(om * wgt<float>(1)), bD = rK * bc(om * wgt<float>(5));
+#pragma unroll
+    for (int a : {1, 2, 5, 6}) {
+        const int b = inv(a);
+        V2 cu3;
+        float ct;  // cf t
+        if (a == 1) { cu3 = ux3; ct = 3.0f * A.cf * A.ax; }
+        else if (a == 2) { cu3 = uy3; ct = 3.0f * A.cf * A.ay; }
+        else if (a == 5) { cu3 = ux3 + uy3; ct = 3.0f * A.cf * (A.ay + A.ax); }
+        else { cu3 = uy3 - ux3; ct = 3.0f * A.cf * (A.ay - A.ax); }  // a == 6: c = (-1, 1)
+        const V2 g = fma2(cu3, bc(omh), bc(ct));
+        const V2 Sv = fma2(cu3, g, C0), Dv = fma2(cu3, bc(omh), g);
+        const V2 wr = a < 5 ? wrA : wrD, bb = a < 5 ? bA : bD;
+        post[a] = fma2(wr, Sv + Dv, fma2(bc(om1), d[a], bb));
+        post[b] = fma2(wr, Sv - Dv, fma2(bc(om1), d[b], bb));
+    }
+}
+
 // One row of four cells x .. x+3 (interior or periodic in y): collide and
 // push.  u[a] holds population a of the four cells as two words (cells
 // x, x+1 and x+2, x+3).  All 32 lanes of the warp call this together (the
@@ -64,35 +128,23 @@ __device__ __forceinline__ void st64(void* base, long long i, unsigned lo, unsig
 template <typename S>
 __device__ __forceinline__ void row_words(const StepArgs<float>& A, int x, int y, bool on, const uint2* u) {
     void* fout = A.fout;
-    const float ro = A.roff[y];
     const int yd = y == 0 ? A.ny - 1 : y - 1, yu = y + 1 == A.ny ? 0 : y + 1;
-    const float rdn = A.roff[yd], rup = A.roff[yu];
     unsigned lo[Q], hi[Q];  // post-collision words of cells (x, x+1) and (x+2, x+3)
     {
-        V2 d[Q];
+        V2 d[Q], p[Q];
 #pragma unroll
-        for (int a = 0; a < Q; ++a) d[a] = Half<S>::unpack(u[a].x);
-        PairCell<false> m;
-        m.build(d, d, A, ro, 0.0f);
+        for (int a = 0; a < Q; ++a) d[a] = Half<S>::raw(u[a].x);
+        collide_units<S>(d, A, p);
 #pragma unroll
-        for (int a = 0; a < Q; ++a) {
-            const float rt = cy(a) > 0 ? rup : (cy(a) < 0 ? rdn : ro);
-            lo[a] = Half<S>::pack(fma2(bc(A.om), m.feqd[a] - d[a], fma2(bc(A.cf), m.F[a], d[a])) +
-                                  bc(wgt<float>(a) * (ro - rt)));
-        }
+        for (int a = 0; a < Q; ++a) lo[a] = Half<S>::raw_pack(p[a]);
     }
     {
-        V2 d[Q];
+        V2 d[Q], p[Q];
 #pragma unroll
-        for (int a = 0; a < Q; ++a) d[a] = Half<S>::unpack(u[a].y);
-        PairCell<false> m;
-        m.build(d, d, A, ro, 0.0f);
+        for (int a = 0; a < Q; ++a) d[a] = Half<S>::raw(u[a].y);
+        collide_units<S>(d, A, p);
 #pragma unroll
-        for (int a = 0; a < Q; ++a) {
-            const float rt = cy(a) > 0 ? rup : (cy(a) < 0 ? rdn : ro);
-            hi[a] = Half<S>::pack(fma2(bc(A.om), m.feqd[a] - d[a], fma2(bc(A.cf), m.F[a], d[a])) +
-                                  bc(wgt<float>(a) * (ro - rt)));
-        }
+        for (int a = 0; a < Q; ++a) hi[a] = Half<S>::raw_pack(p[a]);
     }
     const int lane = threadIdx.x & 31;
     // this lane's right neighbour in the row holds cells x+4..x+7
