@@ -159,6 +159,8 @@ def schedule_name(lb, g, scheme):
             if g.nx % 4 == 0 and g.desc.bcx == lb.LB_BC_PERIODIC:
                 return "st quad (64-bit words, f32x2), four cells of two rows per thread"
             return "st pair (f32x2), two cells of two rows per thread"
+        if g.store == lb.LB_STORE_F32 and not g.thermal and g.nx % 4 == 0 and g.desc.bcx == lb.LB_BC_PERIODIC:
+            return "st quad (128-bit words, f32x2), four cells per thread"
         return "st pair (f32x2), two cells per thread"
     k, c = g.fv_schedule()
     if k == lb.LB_FV_TILE:

@@ -9,7 +9,8 @@
 // bound by the number of memory requests in flight, not by DRAM.  Here
 //   - each population of four cells is one 8-byte load (256 bytes per warp
 //     instruction), both rows' loads issued before any arithmetic;
-//   - the collision runs on packed FP32 pairs (two PairCells per row);
+//   - the collision runs on packed FP32 pairs in storage units, with the
+//     even and odd parts of each pair of opposite populations shared;
 //   - every output is an aligned 8-byte store of four cells: the populations
 //     that move in x are realigned across lanes with one warp shuffle (the
 //     value that crosses a four-cell boundary), so only the lanes at a
@@ -28,7 +29,7 @@ using namespace pairmath;
 
 template <typename S> struct Half;
 template <> struct Half<__half> {
-    static constexpr float kScale = kF16Scale;  // storage units per deviation unit
+    static constexpr int kScale = int(kF16Scale);  // storage units per deviation unit
     // two stored values as floats in storage units (no rescaling)
     __device__ static V2 raw(unsigned u) { return {__half22float2(*reinterpret_cast<const __half2*>(&u))}; }
     __device__ static unsigned raw_pack(V2 v) {
@@ -46,7 +47,7 @@ template <> struct Half<__half> {
     }
 };
 template <> struct Half<__nv_bfloat16> {
-    static constexpr float kScale = 1.0f;
+    static constexpr int kScale = 1;
     __device__ static V2 raw(unsigned u) { return {__bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u))}; }
     __device__ static unsigned raw_pack(V2 v) {
         const __nv_bfloat162 h = __floats2bfloat162_rn(v.v.x, v.v.y);
@@ -71,56 +72,6 @@ __device__ __forceinline__ void st64(void* base, long long i, unsigned lo, unsig
     *reinterpret_cast<uint2*>(reinterpret_cast<unsigned short*>(base) + i) = make_uint2(lo, hi);
 }
 
-// Collision of a pair of cells in storage units (deviations times K, the
-// FP16 scale 2^12 or 1 for BF16) on a flow grid, whose base state is
-// rho_r = 1 on every row.  The BGK relaxation with the Guo force,
-//   post_a = d_a + om (feq_a - f_a) + cf F_a,
-// is regrouped per pair of opposite populations a, b = inv(a): with
-// cu3 = 3 c_a.u, t = 3 c_a.a (a uniform constant), w = w_a and
-//   C0 = om (-1.5 u.u) + cf (-3 u.a),
-//   g  = (om/2) cu3 + cf t,   S = cu3 g + C0,   D = g + (om/2) cu3,
-// the two results are
-//   post_a = (1 - om) d_a + om w K (rho - 1) + w K rho (S + D),
-//   post_b = (1 - om) d_b + om w K (rho - 1) + w K rho (S - D),
-// which is the same polynomial as f_eq = w rho (1 + 3 c.u + 4.5 (c.u)^2
-// - 1.5 u.u) and F = w rho (3 (c - u).a + 9 (c.u)(c.a)) (Sec. II A), with
-// the even part S and the odd part D shared by a and b.  Moments come from
-// the sums divided by K once; no population is rescaled on load or store.
-template <typename S>
-__device__ __forceinline__ void collide_units(const V2* d, const StepArgs<float>& A, V2* post) {
-    constexpr float K = Half<S>::kScale, iK = 1.0f / K;
-    const float om = A.om, om1 = 1.0f - A.om, omh = 0.5f * A.om;
-    const V2 e1 = d[1] - d[3], e2 = d[2] - d[4], e57 = d[5] - d[7], e68 = d[6] - d[8];
-    const V2 rK = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
-    const V2 jx = ((e1 + e57) - e68) * bc(iK), jy = ((e2 + e57) + e68) * bc(iK);
-    const V2 rho = fma2(rK, bc(iK), bc(1.0f));
-    const V2 ir = mk(__fdividef(1.0f, rho.v.x), __fdividef(1.0f, rho.v.y));
-    const V2 ux = fma2(jx, ir, bc(A.hf * A.ax));
-    const V2 uy = fma2(bc(A.ay), bc(A.hf), jy * ir);
-    const V2 ux3 = ux * bc(3.0f), uy3 = uy * bc(3.0f);
-    const V2 uuneg = fma2(ux, ux, uy * uy) * bc(-1.5f);
-    const V2 ua3neg = fma2(uy3, bc(-A.ay), ux3 * bc(-A.ax));
-    const V2 C0 = fma2(bc(om), uuneg, bc(A.cf) * ua3neg);
-    post[0] = fma2(rho * bc(K * wgt<float>(0)), C0, fma2(bc(om1), d[0], rK * bc(om * wgt<float>(0))));
-    const V2 wrA = rho * bc(K * wgt<float>(1)), wrD = rho * bc(K * wgt<float>(5));
-    const V2 bA = rK * bc(om * wgt<float>(1)), bD = rK * bc(om * wgt<float>(5));
-#pragma unroll
-    for (int a : {1, 2, 5, 6}) {
-        const int b = inv(a);
-        V2 cu3;
-        float ct;  // cf t
-        if (a == 1) { cu3 = ux3; ct = 3.0f * A.cf * A.ax; }
-        else if (a == 2) { cu3 = uy3; ct = 3.0f * A.cf * A.ay; }
-        else if (a == 5) { cu3 = ux3 + uy3; ct = 3.0f * A.cf * (A.ay + A.ax); }
-        else { cu3 = uy3 - ux3; ct = 3.0f * A.cf * (A.ay - A.ax); }  // a == 6: c = (-1, 1)
-        const V2 g = fma2(cu3, bc(omh), bc(ct));
-        const V2 Sv = fma2(cu3, g, C0), Dv = fma2(cu3, bc(omh), g);
-        const V2 wr = a < 5 ? wrA : wrD, bb = a < 5 ? bA : bD;
-        post[a] = fma2(wr, Sv + Dv, fma2(bc(om1), d[a], bb));
-        post[b] = fma2(wr, Sv - Dv, fma2(bc(om1), d[b], bb));
-    }
-}
-
 // One row of four cells x .. x+3 (interior or periodic in y): collide and
 // push.  u[a] holds population a of the four cells as two words (cells
 // x, x+1 and x+2, x+3).  All 32 lanes of the warp call this together (the
@@ -134,7 +85,7 @@ __device__ __forceinline__ void row_words(const StepArgs<float>& A, int x, int y
         V2 d[Q], p[Q];
 #pragma unroll
         for (int a = 0; a < Q; ++a) d[a] = Half<S>::raw(u[a].x);
-        collide_units<S>(d, A, p);
+        collide_units<Half<S>::kScale>(d, A, p);
 #pragma unroll
         for (int a = 0; a < Q; ++a) lo[a] = Half<S>::raw_pack(p[a]);
     }
@@ -142,7 +93,7 @@ __device__ __forceinline__ void row_words(const StepArgs<float>& A, int x, int y
         V2 d[Q], p[Q];
 #pragma unroll
         for (int a = 0; a < Q; ++a) d[a] = Half<S>::raw(u[a].y);
-        collide_units<S>(d, A, p);
+        collide_units<Half<S>::kScale>(d, A, p);
 #pragma unroll
         for (int a = 0; a < Q; ++a) hi[a] = Half<S>::raw_pack(p[a]);
     }
@@ -231,54 +182,63 @@ __device__ void row_wall(const StepArgs<float>& A, int x, int y, const uint2* u)
 
 }  // namespace
 
-// Two rows per thread (y = 2 blockIdx.y and y + 1), four cells each; both
-// rows' loads are issued before the first row's arithmetic.
-template <typename S>
-__global__ void __launch_bounds__(256, 2) k_st16_quad(const StepArgs<float> A) {
+// R rows per thread (y = R blockIdx.y ...), four cells each; all rows'
+// loads are issued before the first row's arithmetic.
+template <typename S, int R, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_st16_quad(const StepArgs<float> A) {
     const int x = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
-    const int y = 2 * blockIdx.y;
+    const int y0 = R * blockIdx.y;
     const bool on = x < A.nx;
-    const bool second = y + 1 < A.ny;
     const S* fin = static_cast<const S*>(A.fin);
-    uint2 u0[Q], u1[Q];
+    uint2 u[R][Q];
     if (on) {
-        const uint2* p = reinterpret_cast<const uint2*>(fin + (long long)y * A.pitch + x);
+        const uint2* p = reinterpret_cast<const uint2*>(fin + (long long)y0 * A.pitch + x);
         const long long pl = A.plane / 4, pr = A.pitch / 4;  // in 8-byte words
 #pragma unroll
-        for (int a = 0; a < Q; ++a) u0[a] = __ldg(p + a * pl);
-        if (second) {
+        for (int r = 0; r < R; ++r) {
+            if (r == 0 || y0 + r < A.ny) {
 #pragma unroll
-            for (int a = 0; a < Q; ++a) u1[a] = __ldg(p + a * pl + pr);
+                for (int a = 0; a < Q; ++a) u[r][a] = __ldg(p + a * pl + r * pr);
+            }
         }
     } else {
 #pragma unroll
-        for (int a = 0; a < Q; ++a) u0[a] = u1[a] = make_uint2(0u, 0u);
+        for (int r = 0; r < R; ++r)
+#pragma unroll
+            for (int a = 0; a < Q; ++a) u[r][a] = make_uint2(0u, 0u);
     }
     const bool walls = A.bcy == LB_BC_WALLS;
     // a block's threads share their rows, so these branches are uniform
-    if (walls && (y == 0 || y == A.ny - 1)) {
-        if (on) row_wall<S>(A, x, y, u0);
-    } else {
-        row_words<S>(A, x, y, on, u0);
-    }
-    if (second) {
-        if (walls && y + 1 == A.ny - 1) {
-            if (on) row_wall<S>(A, x, y + 1, u1);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int y = y0 + r;
+        if (r > 0 && y >= A.ny) break;
+        if (walls && (y == 0 || y == A.ny - 1)) {
+            if (on) row_wall<S>(A, x, y, u[r]);
         } else {
-            row_words<S>(A, x, y + 1, on, u1);
+            row_words<S>(A, x, y, on, u[r]);
         }
     }
 }
 
-template <typename S>
-static cudaError_t run_st16(const void* vargs, cudaStream_t s) {
-    const StepArgs<float>& A = *static_cast<const StepArgs<float>*>(vargs);
+template <typename S, int R, int MINB>
+static cudaError_t run_st16_r(const StepArgs<float>& A, cudaStream_t s) {
     const int quads = A.nx / 4;
     const int bx = quads >= 256 ? 256 : ((quads + 31) / 32) * 32;
-    dim3 grid((quads + bx - 1) / bx, (A.ny + 1) / 2);
-    k_st16_quad<S><<<grid, bx, 0, s>>>(A);
+    dim3 grid((quads + bx - 1) / bx, (A.ny + R - 1) / R);
+    k_st16_quad<S, R, MINB><<<grid, bx, 0, s>>>(A);
     count_launch();
     return cudaGetLastError();
+}
+
+// Two rows per thread at three CTAs of 256 threads per SM (80 registers, a
+// 48-byte spill).  At 8192^2 this beats two CTAs at 128 registers by 16 %
+// (FP16) and 14 % (BF16): the latency of the loads and of the f32x2
+// dependency chains is hidden by 24 warps per SM instead of 16.  One row per
+// thread, three or four rows, and four CTAs per SM were slower.
+template <typename S>
+static cudaError_t run_st16(const void* vargs, cudaStream_t s) {
+    return run_st16_r<S, 2, 3>(*static_cast<const StepArgs<float>*>(vargs), s);
 }
 
 bool st16_applies(Prec p, bool thermal, int nx, int bcx) {

@@ -64,6 +64,9 @@ cudaError_t set_max_smem(const void* fn, int bytes) {
 // 16-bit ST on flow grids periodic in x with nx % 4 == 0 (k_st16.cu).
 bool st16_applies(Prec p, bool thermal, int nx, int bcx);
 cudaError_t launch_st16(Prec p, const void* args, cudaStream_t s);
+// FP32 ST on flow grids periodic in x with nx % 4 == 0 (k_st_quad.cu).
+bool st_quad_applies(Prec p, bool thermal, int nx, int bcx);
+cudaError_t launch_st_quad(const void* args, cudaStream_t s);
 // Record a failure message for lb_last_error() from another translation unit.
 lb_status set_last_error(lb_status s, const char* msg) { return fail(s, "%s", msg); }
 }  // namespace lbgb
@@ -750,6 +753,7 @@ lb_status lb_step_st(lb_grid* G, int nsteps) {
         }
         StepArgs<float> A = step_args<float>(G, 1.0);
         if (st16_applies(G->prec, th, G->nx, G->d.bcx)) return launch_st16(G->prec, &A, G->stream);
+        if (st_quad_applies(G->prec, th, G->nx, G->d.bcx)) return launch_st_quad(&A, G->stream);
         return launch_st(G->prec, th, &A, G->stream);
     });
 }

@@ -108,5 +108,55 @@ struct PairCell {
     }
 };
 
+// Collision of a pair of cells in storage units (deviations times K: the
+// FP16 scale 2^12, or 1 for BF16 and FP32) on a flow grid, whose base state is
+// rho_r = 1 on every row.  The BGK relaxation with the Guo force,
+//   post_a = d_a + om (feq_a - f_a) + cf F_a,
+// is regrouped per pair of opposite populations a, b = inv(a): with
+// cu3 = 3 c_a.u, t = 3 c_a.a (a uniform constant), w = w_a and
+//   C0 = om (-1.5 u.u) + cf (-3 u.a),
+//   g  = (om/2) cu3 + cf t,   S = cu3 g + C0,   D = g + (om/2) cu3,
+// the two results are
+//   post_a = (1 - om) d_a + om w K (rho - 1) + w K rho (S + D),
+//   post_b = (1 - om) d_b + om w K (rho - 1) + w K rho (S - D),
+// which is the same polynomial as f_eq = w rho (1 + 3 c.u + 4.5 (c.u)^2
+// - 1.5 u.u) and F = w rho (3 (c - u).a + 9 (c.u)(c.a)) (Sec. II A), with
+// the even part S and the odd part D shared by a and b.  Moments come from
+// the sums divided by K once; no population is rescaled on load or store.
+template <int K_>
+__device__ __forceinline__ void collide_units(const V2* d, const StepArgs<float>& A, V2* post) {
+    constexpr float K = float(K_), iK = 1.0f / K;
+    const float om = A.om, om1 = 1.0f - A.om, omh = 0.5f * A.om;
+    const V2 e1 = d[1] - d[3], e2 = d[2] - d[4], e57 = d[5] - d[7], e68 = d[6] - d[8];
+    const V2 rK = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+    const V2 jx = ((e1 + e57) - e68) * bc(iK), jy = ((e2 + e57) + e68) * bc(iK);
+    const V2 rho = fma2(rK, bc(iK), bc(1.0f));
+    const V2 ir = mk(__fdividef(1.0f, rho.v.x), __fdividef(1.0f, rho.v.y));
+    const V2 ux = fma2(jx, ir, bc(A.hf * A.ax));
+    const V2 uy = fma2(bc(A.ay), bc(A.hf), jy * ir);
+    const V2 ux3 = ux * bc(3.0f), uy3 = uy * bc(3.0f);
+    const V2 uuneg = fma2(ux, ux, uy * uy) * bc(-1.5f);
+    const V2 ua3neg = fma2(uy3, bc(-A.ay), ux3 * bc(-A.ax));
+    const V2 C0 = fma2(bc(om), uuneg, bc(A.cf) * ua3neg);
+    post[0] = fma2(rho * bc(K * wgt<float>(0)), C0, fma2(bc(om1), d[0], rK * bc(om * wgt<float>(0))));
+    const V2 wrA = rho * bc(K * wgt<float>(1)), wrD = rho * bc(K * wgt<float>(5));
+    const V2 bA = rK * bc(om * wgt<float>(1)), bD = rK * bc(om * wgt<float>(5));
+#pragma unroll
+    for (int a : {1, 2, 5, 6}) {
+        const int b = inv(a);
+        V2 cu3;
+        float ct;  // cf t
+        if (a == 1) { cu3 = ux3; ct = 3.0f * A.cf * A.ax; }
+        else if (a == 2) { cu3 = uy3; ct = 3.0f * A.cf * A.ay; }
+        else if (a == 5) { cu3 = ux3 + uy3; ct = 3.0f * A.cf * (A.ay + A.ax); }
+        else { cu3 = uy3 - ux3; ct = 3.0f * A.cf * (A.ay - A.ax); }  // a == 6: c = (-1, 1)
+        const V2 g = fma2(cu3, bc(omh), bc(ct));
+        const V2 Sv = fma2(cu3, g, C0), Dv = fma2(cu3, bc(omh), g);
+        const V2 wr = a < 5 ? wrA : wrD, bb = a < 5 ? bA : bD;
+        post[a] = fma2(wr, Sv + Dv, fma2(bc(om1), d[a], bb));
+        post[b] = fma2(wr, Sv - Dv, fma2(bc(om1), d[b], bb));
+    }
+}
+
 }  // namespace pairmath
 }  // namespace lbgb

@@ -88,6 +88,7 @@ ST_CASES = [
     dict(nx=260, ny=9, bcy=1),   # 16-bit flow: four-cell words, a partial warp, walls on y
     dict(nx=4, ny=6),            # one thread per row pair
     dict(nx=136, ny=3),          # odd row count, last row pair single
+    dict(nx=1032, ny=5),         # four-cell kernels: two CTAs per row, the second with 2 quads
 ]
 
 
