@@ -293,21 +293,23 @@ __global__ void __launch_bounds__(NT) k_fv_pair(const StepArgs<float> A, const i
             o0 = o1;
             prefetch(t + 2, b1, e1, o1);
             if (fluid_row(t, gy)) {
-                PairCell<TH> c;
+                PairMom<TH> c;
                 c.build(d, e, A, o.y, TH ? o.z : 0.0f);
+                V2 hv[Q], pv[Q], hg[Q], pg[Q];
+                c.relax_f(d, A, A.omh, A.hF, hv);
+                c.relax_f(d, A, A.om, A.cf, pv);
+                if constexpr (TH) {
+                    c.relax_g(e, A.omgh, hg);
+                    c.relax_g(e, A.omg, pg);
+                }
 #pragma unroll
                 for (int a = 0; a < Q; ++a) {
-                    const V2 neq = c.feqd[a] - d[a];
-                    if (ring_depth(a) > 0)
-                        sH[(ring_off(a) + (ring_depth(a) == 5 ? s : t3)) * NT + k] =
-                            fma2(bc(A.omh), neq, fma2(bc(A.hF), c.F[a], d[a]));
-                    sP[(s * NQ + a) * NT + k] = fma2(bc(A.om), neq, fma2(bc(A.cf), c.F[a], d[a]));
+                    if (ring_depth(a) > 0) sH[(ring_off(a) + (ring_depth(a) == 5 ? s : t3)) * NT + k] = hv[a];
+                    sP[(s * NQ + a) * NT + k] = pv[a];
                     if constexpr (TH) {
-                        const V2 neqg = c.geqd[a] - e[a];
                         if (ring_depth(a) > 0)
-                            sH[(ring_off(Q + a) + (ring_depth(a) == 5 ? s : t3)) * NT + k] =
-                                fma2(bc(A.omgh), neqg, e[a]);
-                        sP[(s * NQ + Q + a) * NT + k] = fma2(bc(A.omg), neqg, e[a]);
+                            sH[(ring_off(Q + a) + (ring_depth(a) == 5 ? s : t3)) * NT + k] = hg[a];
+                        sP[(s * NQ + Q + a) * NT + k] = pg[a];
                     }
                 }
             } else if (wally && (t == A.ny || t == A.ny + 1)) {
@@ -343,16 +345,17 @@ __global__ void __launch_bounds__(NT) k_fv_pair(const StepArgs<float> A, const i
                                 sP[(s * NQ + Q + a) * NT + k] = fma2(bc(-A.hf), adv[Q + a], gc);
                             }
                         }
-                        PairCell<TH> c;
+                        PairMom<TH> c;
                         c.build(fs, es, A, Y.ro, TH ? Y.to : 0.0f);
+                        V2 hv[Q], hg[Q];
+                        c.relax_f(fs, A, A.omh, A.hF, hv);
+                        if constexpr (TH) c.relax_g(es, A.omgh, hg);
 #pragma unroll
                         for (int a = 0; a < Q; ++a) {
                             if (ring_depth(a) == 0) continue;
                             const int sa = ring_depth(a) == 5 ? s : c3b;
-                            sS[(ring_off(a) + sa) * NT + k] =
-                                fma2(bc(A.omh), c.feqd[a] - fs[a], fma2(bc(A.hF), c.F[a], fs[a]));
-                            if constexpr (TH)
-                                sS[(ring_off(Q + a) + sa) * NT + k] = fma2(bc(A.omgh), c.geqd[a] - es[a], es[a]);
+                            sS[(ring_off(a) + sa) * NT + k] = hv[a];
+                            if constexpr (TH) sS[(ring_off(Q + a) + sa) * NT + k] = hg[a];
                         }
                     }
                 } else if (wally && (r == A.ny || r == A.ny + 1)) {
@@ -588,19 +591,26 @@ __device__ __forceinline__ void ptile_body(const StepArgs<float>& A, const int x
             }
         }
         const float4 o = __ldg(reinterpret_cast<const float4*>(A.rowtab + 20 * gy) + 3);
-        PairCell<TH> c;
+        PairMom<TH> c;
         c.build(d, e, A, o.y, TH ? o.z : 0.0f);
         const bool inB = px >= 1 && px < EW - 1 && ey >= 2 && ey < EH - 2;
         const int kb = (ey - 2) * BW + (px - 1);
+        V2 hv[Q], hg[Q];
+        c.relax_f(d, A, A.omh, A.hF, hv);
+        if constexpr (TH) c.relax_g(e, A.omgh, hg);
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
-            const V2 neq = c.feqd[a] - d[a];
-            sH[a * NE + k] = fma2(bc(A.omh), neq, fma2(bc(A.hF), c.F[a], d[a]));
-            if (inB) sFC[a * NB + kb] = fma2(bc(A.om), neq, fma2(bc(A.cf), c.F[a], d[a]));
-            if constexpr (TH) {
-                const V2 neqg = c.geqd[a] - e[a];
-                sH[(Q + a) * NE + k] = fma2(bc(A.omgh), neqg, e[a]);
-                if (inB) sFC[(Q + a) * NB + kb] = fma2(bc(A.omg), neqg, e[a]);
+            sH[a * NE + k] = hv[a];
+            if constexpr (TH) sH[(Q + a) * NE + k] = hg[a];
+        }
+        if (inB) {
+            V2 pv[Q], pg[Q];
+            c.relax_f(d, A, A.om, A.cf, pv);
+            if constexpr (TH) c.relax_g(e, A.omg, pg);
+#pragma unroll
+            for (int a = 0; a < Q; ++a) {
+                sFC[a * NB + kb] = pv[a];
+                if constexpr (TH) sFC[(Q + a) * NB + kb] = pg[a];
             }
         }
     }
@@ -632,12 +642,15 @@ __device__ __forceinline__ void ptile_body(const StepArgs<float>& A, const int x
                 if (tile) sFC[(Q + a) * NB + k] = fma2(bc(-A.hf), adv[Q + a], gc);
             }
         }
-        PairCell<TH> c;
+        PairMom<TH> c;
         c.build(fs, es, A, Y.ro, TH ? Y.to : 0.0f);
+        V2 hv[Q], hg[Q];
+        c.relax_f(fs, A, A.omh, A.hF, hv);
+        if constexpr (TH) c.relax_g(es, A.omgh, hg);
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
-            sHs[a * NB + k] = fma2(bc(A.omh), c.feqd[a] - fs[a], fma2(bc(A.hF), c.F[a], fs[a]));
-            if constexpr (TH) sHs[(Q + a) * NB + k] = fma2(bc(A.omgh), c.geqd[a] - es[a], es[a]);
+            sHs[a * NB + k] = hv[a];
+            if constexpr (TH) sHs[(Q + a) * NB + k] = hg[a];
         }
     }
     __syncthreads();
@@ -715,19 +728,26 @@ __global__ void __launch_bounds__(NTH) k_fv_split_a(const StepArgs<float> A) {
             }
         }
         const float4 o = __ldg(reinterpret_cast<const float4*>(A.rowtab + 20 * gy) + 3);
-        PairCell<TH> c;
+        PairMom<TH> c;
         c.build(d, e, A, o.y, TH ? o.z : 0.0f);
         const bool inT = px >= 1 && px < BW - 1 && ey >= 2 && ey < BH - 2;
         const int kt = (ey - 2) * TW + (px - 1);
+        V2 hv[Q], hg[Q];
+        c.relax_f(d, A, A.omh, A.hF, hv);
+        if constexpr (TH) c.relax_g(e, A.omgh, hg);
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
-            const V2 neq = c.feqd[a] - d[a];
-            sH[a * NB + k] = fma2(bc(A.omh), neq, fma2(bc(A.hF), c.F[a], d[a]));
-            if (inT) sFC[a * NT + kt] = fma2(bc(A.om), neq, fma2(bc(A.cf), c.F[a], d[a]));
-            if constexpr (TH) {
-                const V2 neqg = c.geqd[a] - e[a];
-                sH[(Q + a) * NB + k] = fma2(bc(A.omgh), neqg, e[a]);
-                if (inT) sFC[(Q + a) * NT + kt] = fma2(bc(A.omg), neqg, e[a]);
+            sH[a * NB + k] = hv[a];
+            if constexpr (TH) sH[(Q + a) * NB + k] = hg[a];
+        }
+        if (inT) {
+            V2 pv[Q], pg[Q];
+            c.relax_f(d, A, A.om, A.cf, pv);
+            if constexpr (TH) c.relax_g(e, A.omg, pg);
+#pragma unroll
+            for (int a = 0; a < Q; ++a) {
+                sFC[a * NT + kt] = pv[a];
+                if constexpr (TH) sFC[(Q + a) * NT + kt] = pg[a];
             }
         }
     }
@@ -758,19 +778,20 @@ __global__ void __launch_bounds__(NTH) k_fv_split_a(const StepArgs<float> A) {
             if (a < Q) fs[a] = st;
             else if constexpr (TH) es[a - Q] = st;
         }
-        PairCell<TH> c;
+        PairMom<TH> c;
         c.build(fs, es, A, Y.ro, TH ? Y.to : 0.0f);
+        V2 hv[Q], hgv[Q];
+        c.relax_f(fs, A, A.omh, A.hF, hv);
+        if constexpr (TH) c.relax_g(es, A.omgh, hgv);
 #pragma unroll
         for (int a = 0; a < Q; ++a) {
-            const V2 hs = fma2(bc(A.omh), c.feqd[a] - fs[a], fma2(bc(A.hF), c.F[a], fs[a]));
             float* p = A.xh + a * A.plane + at;
-            if (both) PairIO<float>::st(p, hs);
-            else *p = hs.v.x;
+            if (both) PairIO<float>::st(p, hv[a]);
+            else *p = hv[a].v.x;
             if constexpr (TH) {
-                const V2 hg = fma2(bc(A.omgh), c.geqd[a] - es[a], es[a]);
                 float* q = A.xh + (Q + a) * A.plane + at;
-                if (both) PairIO<float>::st(q, hg);
-                else *q = hg.v.x;
+                if (both) PairIO<float>::st(q, hgv[a]);
+                else *q = hgv[a].v.x;
             }
         }
     }

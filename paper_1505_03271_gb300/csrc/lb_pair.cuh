@@ -158,5 +158,96 @@ __device__ __forceinline__ void collide_units(const V2* d, const StepArgs<float>
     }
 }
 
+// Moments of a pair of cells and the relaxations the FV stages build from
+// them: stage A needs two of one cell (the advected field h and f~ + Coll),
+// stage B one (h*).  In the base-state frame (d = f - w rho_r, rp = sum d =
+// rho - rho_r, e = g - w T_r, Td = sum e = T - T_r)
+//   relax_f: out_a = d_a + k1 (feqd_a - d_a) + k2 F_a
+//          = (1 - k1) d_a + k1 w rp + w rho (S +- D)   (a and b = inv(a)),
+//     with cu3 = 3 c_a.u, t = 3 c_a.a, C0 = k1 (-1.5 u.u) + k2 (-3 u.a),
+//     g = (k1/2) cu3 + k2 t, S = cu3 g + C0, D = g + (k1/2) cu3: the even
+//     part S and the odd part D of f_eq and F (Sec. II A) shared by the pair;
+//   relax_g: out_a = e_a + k (geqd_a - e_a), geqd_a = w (Td + T (3 c.u +
+//     4.5 (c.u)^2 - 1.5 u.u)).
+// The thermal buoyancy makes a_y a per-cell value: a_y + beta g (T - T0).
+template <bool TH>
+struct PairMom {
+    V2 rp, rho, ux3, uy3, ay, uuneg, ua3neg, Td, T;
+
+    __device__ __forceinline__ void build(const V2* d, const V2* e, const StepArgs<float>& A, float ro, float to) {
+        const V2 e1 = d[1] - d[3], e2 = d[2] - d[4], e57 = d[5] - d[7], e68 = d[6] - d[8];
+        rp = ((d[0] + d[1]) + (d[2] + d[3])) + ((d[4] + d[5]) + (d[6] + d[7])) + d[8];
+        const V2 jx = (e1 + e57) - e68, jy = (e2 + e57) + e68;
+        rho = rp + bc(1.0f + ro);
+        const V2 ir = mk(__fdividef(1.0f, rho.v.x), __fdividef(1.0f, rho.v.y));
+        if constexpr (TH) {
+            Td = ((e[0] + e[1]) + (e[2] + e[3])) + ((e[4] + e[5]) + (e[6] + e[7])) + e[8];
+            const V2 dT0 = Td + bc(to);
+            T = dT0 + bc(A.T0);
+            ay = fma2(bc(A.bg), dT0, bc(A.ay));
+        } else {
+            ay = bc(A.ay);
+        }
+        const V2 ux = fma2(jx, ir, bc(A.hf * A.ax));
+        const V2 uy = fma2(ay, bc(A.hf), jy * ir);
+        ux3 = ux * bc(3.0f);
+        uy3 = uy * bc(3.0f);
+        uuneg = fma2(ux, ux, uy * uy) * bc(-1.5f);
+        ua3neg = fma2(uy3, ay, ux3 * bc(A.ax)) * bc(-1.0f);
+    }
+
+    template <int a>
+    __device__ __forceinline__ V2 cu3_of() const {
+        if constexpr (a == 1) return ux3;
+        else if constexpr (a == 2) return uy3;
+        else if constexpr (a == 5) return ux3 + uy3;
+        else return uy3 - ux3;  // a == 6: c = (-1, 1)
+    }
+
+    __device__ __forceinline__ void relax_f(const V2* d, const StepArgs<float>& A, float k1, float k2, V2* out) const {
+        const float k1h = 0.5f * k1, k1c = 1.0f - k1;
+        const V2 C0 = fma2(bc(k1), uuneg, bc(k2) * ua3neg);
+        const V2 cty = ay * bc(3.0f * k2);
+        const float ctx = 3.0f * k2 * A.ax;
+        out[0] = fma2(rho * bc(wgt<float>(0)), C0, fma2(bc(k1c), d[0], rp * bc(k1 * wgt<float>(0))));
+        const V2 wrA = rho * bc(wgt<float>(1)), wrD = rho * bc(wgt<float>(5));
+        const V2 bA = rp * bc(k1 * wgt<float>(1)), bD = rp * bc(k1 * wgt<float>(5));
+        pair_f<1>(d, k1h, k1c, C0, bc(ctx), wrA, bA, out);
+        pair_f<2>(d, k1h, k1c, C0, cty, wrA, bA, out);
+        pair_f<5>(d, k1h, k1c, C0, cty + bc(ctx), wrD, bD, out);
+        pair_f<6>(d, k1h, k1c, C0, cty - bc(ctx), wrD, bD, out);
+    }
+
+    template <int a>
+    __device__ __forceinline__ void pair_f(const V2* d, float k1h, float k1c, V2 C0, V2 ct, V2 wr, V2 bb,
+                                           V2* out) const {
+        constexpr int b = inv(a);
+        const V2 cu3 = cu3_of<a>();
+        const V2 g = fma2(cu3, bc(k1h), ct);
+        const V2 Sv = fma2(cu3, g, C0), Dv = fma2(cu3, bc(k1h), g);
+        out[a] = fma2(wr, Sv + Dv, fma2(bc(k1c), d[a], bb));
+        out[b] = fma2(wr, Sv - Dv, fma2(bc(k1c), d[b], bb));
+    }
+
+    __device__ __forceinline__ void relax_g(const V2* e, float k, V2* out) const {
+        const float w0 = wgt<float>(0);
+        out[0] = fma2(bc(k), fma2(T * bc(w0), uuneg, Td * bc(w0)) - e[0], e[0]);
+        pair_g<1>(e, k, out);
+        pair_g<2>(e, k, out);
+        pair_g<5>(e, k, out);
+        pair_g<6>(e, k, out);
+    }
+
+    template <int a>
+    __device__ __forceinline__ void pair_g(const V2* e, float k, V2* out) const {
+        constexpr int b = inv(a);
+        const V2 cu3 = cu3_of<a>();
+        const V2 q = fma2(cu3 * bc(0.5f), cu3, uuneg);  // 4.5 (c.u)^2 - 1.5 u.u
+        const V2 wT = T * bc(wgt<float>(a)), wTd = Td * bc(wgt<float>(a));
+        out[a] = fma2(bc(k), fma2(wT, cu3 + q, wTd) - e[a], e[a]);
+        out[b] = fma2(bc(k), fma2(wT, q - cu3, wTd) - e[b], e[b]);
+    }
+};
+
 }  // namespace pairmath
 }  // namespace lbgb
