@@ -316,7 +316,7 @@ def extra_lines(lb, torch, cfg, stream, peak, peak_kind, flush, serving=None, cp
     specs = [("st8192_bf16dev", cfg.st_sweep(8192, lb.LB_STORE_BF16DEV), 20, ("st4096_bf16dev", 4)),
              ("st8192_f16dev", cfg.st_sweep(8192, lb.LB_STORE_F16DEV), 20, ("st4096_f16dev", 4)),
              ("fv4096_f32", _fv_big(cfg, 4096), 10, "fv4096"),
-             ("fv_rb1024_f32", cfg.rayleigh_benard(1024, 1e8, store=lb.LB_STORE_F32), 20, "rb1024"),
+             ("fv_rb1024_f32", cfg.rayleigh_benard(1024, 1e8, store=lb.LB_STORE_F32), 20, "rb1024_f32"),
              ("rb3d_fv_f32", cfg.rb3d_table("fv"), 10, "rb3d_fv"),
              ("rb3d_st_f32", cfg.rb3d_table("st"), 20, "rb3d_st")]
     for name, w, k, case in specs:
