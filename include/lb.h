@@ -120,7 +120,12 @@ lb_status lb_create_grid(const lb_grid_desc* desc, lb_grid** out);
 /* Set parameters and initial state: f~ = f_eq(rho, u) - dt/2 F (Appendix A,
  * tilded variables at equilibrium) and g~ = (T/rho) f_eq (Eq. (LBg)).
  * Clears the poisoned flag.  LB_ERR_ARG on bad parameters (tau <= 0,
- * dt <= 0, a thermal preset on a flow-only grid, NULL arrays where needed). */
+ * dt <= 0, a thermal preset on a flow-only grid, NULL arrays where needed).
+ * LB_INIT_FIELDS: each given host array is copied to the device as it is
+ * (a DMA when the caller's memory is page-locked), absent ones are filled on
+ * the device, and rho > 0 is checked there before any population is
+ * written: LB_ERR_ARG names the first cell that fails, and the populations
+ * stay as they were.  The host arrays are read before the call returns. */
 lb_status lb_init(lb_grid* grid, const lb_params* params, const lb_init_desc* init);
 
 /* Advance nsteps FV time steps (Sec. II B 2, Eq. (semi-heun)): the advected

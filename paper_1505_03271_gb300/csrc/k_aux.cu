@@ -90,6 +90,40 @@ cudaError_t launch_init(Prec p, bool th, const InitArgs& a, cudaStream_t s) {
     return cudaErrorInvalidValue;
 }
 
+// Host fields of LB_INIT_FIELDS go to the device as they are; an absent
+// field is filled here, and the density is checked here rather than on the
+// host, so lb_init reads each host array once, by DMA.
+__global__ void k_fill(double* p, long long n, double v) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        p[i] = v;
+}
+
+// Smallest index whose density is not > 0 (NaN included) into *first,
+// which the caller sets to all ones beforehand.
+__global__ void k_first_nonpositive(const double* rho, long long n, unsigned long long* first) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        if (!(rho[i] > 0.0)) atomicMin(first, (unsigned long long)i);
+}
+
+static int aux_blocks(long long n) {
+    const long long b = (n + 255) / 256;
+    return (int)(b < 4096 ? (b > 0 ? b : 1) : 4096);
+}
+
+cudaError_t launch_fill(double* p, long long n, double v, cudaStream_t s) {
+    k_fill<<<aux_blocks(n), 256, 0, s>>>(p, n, v);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_first_nonpositive(const double* rho, long long n, unsigned long long* first, cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(first, 0xff, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    k_first_nonpositive<<<aux_blocks(n), 256, 0, s>>>(rho, n, first);
+    count_launch();
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------ pack / unpack --
 
 template <typename S>

@@ -543,18 +543,26 @@ lb_status lb_init(lb_grid* G, const lb_params* p, const lb_init_desc* in) {
     a.fields = G->fields;
     a.rho_norm = rho_norm;
     if (in->kind == LB_INIT_FIELDS) {
-        const size_t n = (size_t)G->nx * G->ny;
-        std::vector<double> h(4 * n);
-        for (size_t c = 0; c < n; ++c) {
-            h[c] = in->rho ? in->rho[c] : 1.0;
-            h[n + c] = in->ux ? in->ux[c] : 0.0;
-            h[2 * n + c] = in->uy ? in->uy[c] : 0.0;
-            h[3 * n + c] = in->T ? in->T[c] : p->T0;
-            if (!(h[c] > 0)) return fail(LB_ERR_ARG, "density must be > 0 (cell %zu)", c);
+        // each host field straight into the staging buffer (a DMA when the
+        // caller's memory is pinned); absent fields filled on the device
+        const long long n = (long long)G->nx * G->ny;
+        const double* src[4] = {in->rho, in->ux, in->uy, in->T};
+        const double fill[4] = {1.0, 0.0, 0.0, p->T0};
+        for (int k = 0; k < 4; ++k) {
+            if (src[k])
+                CK(cudaMemcpyAsync(G->fields + k * n, src[k], sizeof(double) * n, cudaMemcpyHostToDevice, G->stream));
+            else
+                CK(launch_fill(G->fields + k * n, n, fill[k], G->stream));
         }
-        CK(cudaMemcpyAsync(G->fields, h.data(), sizeof(double) * 4 * n, cudaMemcpyHostToDevice, G->stream));
+        // the density is checked before the populations are touched, so a
+        // rejected call leaves the grid's state as it was
+        unsigned long long* first = reinterpret_cast<unsigned long long*>(G->red);
+        unsigned long long bad = ~0ULL;
+        CK(launch_first_nonpositive(G->fields, n, first, G->stream));
+        CK(cudaMemcpyAsync(&bad, first, sizeof(bad), cudaMemcpyDeviceToHost, G->stream));
+        CK(cudaStreamSynchronize(G->stream));  // the host arrays are read before return
+        if (bad != ~0ULL) return fail(LB_ERR_ARG, "density must be > 0 (cell %llu)", bad);
         CK(launch_init(G->prec, G->d.thermal != 0, a, G->stream));
-        CK(cudaStreamSynchronize(G->stream));  // h is released on return
     } else {
         CK(launch_init(G->prec, G->d.thermal != 0, a, G->stream));
     }

@@ -269,6 +269,10 @@ struct InitArgs {
     const double* fields;  // LB_INIT_FIELDS: [4][ny][nx] rho, ux, uy, T on device
 };
 cudaError_t launch_init(Prec p, bool thermal, const InitArgs& a, cudaStream_t s);
+// n doubles at p set to v; and the smallest index i with !(rho[i] > 0) into
+// *first (all ones when there is none)
+cudaError_t launch_fill(double* p, long long n, double v, cudaStream_t s);
+cudaError_t launch_first_nonpositive(const double* rho, long long n, unsigned long long* first, cudaStream_t s);
 
 void count_launch();
 

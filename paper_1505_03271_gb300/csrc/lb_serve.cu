@@ -74,7 +74,9 @@ struct lb_server {
     int4* h_tiles = nullptr;
     int* h_ntiles = nullptr;
     cudaGraphExec_t graph = nullptr;
-    int graph_cap = 0;
+    // the captured launches hold the table pointers: a graph is replayed
+    // only while the tables it was captured with are still the current ones
+    unsigned long long table_gen = 0, graph_gen = 0;
     bool graph_paired = false;
     bool warmed = false;
     bool all_periodic_x = true;  // every active request has a periodic x axis
@@ -103,6 +105,7 @@ lb_status ensure_capacity(lb_server* S, int nreq, int ntiles) {
     S->d_tiles = nullptr;
     S->h_reqs = nullptr;
     S->h_tiles = nullptr;
+    ++S->table_gen;  // the old tables are gone: any captured graph is stale
     const size_t rs = req_size(S->prec);
     if (cudaMalloc(&S->d_reqs, rs * cr) != cudaSuccess || cudaMalloc((void**)&S->d_tiles, sizeof(int4) * ct) != cudaSuccess ||
         cudaMallocHost(&S->h_reqs, rs * cr) != cudaSuccess ||
@@ -145,14 +148,15 @@ lb_status launch_steps(lb_server* S, int ncap) {
 
 // K batched launches: plain launches the first time (so that per-kernel
 // attributes are set outside any capture), then a captured graph replayed
-// while the tile capacity stays the same.
+// while the device tables it was captured with are still in place (both
+// are reallocated when either capacity grows).
 lb_status run_batch(lb_server* S) {
     const int ncap = S->cap_tiles;
     if (!S->warmed) {
         S->warmed = true;
         return launch_steps(S, ncap);
     }
-    if (!S->graph || S->graph_cap != ncap || S->graph_paired != paired(S)) {
+    if (!S->graph || S->graph_gen != S->table_gen || S->graph_paired != paired(S)) {
         if (S->graph) cudaGraphExecDestroy(S->graph);
         S->graph = nullptr;
         cudaGraph_t g = nullptr;
@@ -165,7 +169,7 @@ lb_status run_batch(lb_server* S) {
         e = cudaGraphInstantiate(&S->graph, g, 0);
         cudaGraphDestroy(g);
         if (e != cudaSuccess) return fail(LB_ERR_CUDA, std::string("instantiate: ") + cudaGetErrorString(e));
-        S->graph_cap = ncap;
+        S->graph_gen = S->table_gen;
         S->graph_paired = paired(S);
     }
     cudaError_t e = cudaGraphLaunch(S->graph, S->stream);

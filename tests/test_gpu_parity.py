@@ -637,6 +637,30 @@ def test_rb_nusselt_storage_errors(lbgpu, oracle, store, tol):
 
 # ------------------------------------------------------- errors and edges --
 
+def test_init_fields_rejects_nonpositive_density(lbgpu, oracle):
+    """lb_init from host fields copies each given field to the device, fills
+    the absent ones there (rho = 1, u = 0, T = T0) and checks rho > 0 on the
+    device before any population is written: a bad density fails with
+    LB_ERR_ARG naming the first bad cell, and the grid keeps its state."""
+    lb = lbgpu
+    nx, ny = 24, 12
+    kw = dict(tau=0.3, dt=1.0, tau_g=0.3, beta=0.01, grav=1.0, T0=1.2)
+    g, r = pair(lb, oracle, nx, ny, lb.LB_STORE_F64, thermal=True, **kw)  # every field absent
+    r.init_fields()
+    for a, b in zip(g.get_pops(), r.get_pops()):
+        assert np.abs(a - b).max() < 1e-15
+    before = [p.copy() for p in g.get_pops()]
+    rho = np.ones((ny, nx))
+    rho[9, 2] = np.nan
+    rho[5, 7] = -1.0
+    with pytest.raises(lb.LBError) as e:
+        g.init(**kw, rho=rho)
+    assert e.value.status == lb.LB_ERR_ARG
+    assert "cell %d)" % (5 * nx + 7) in str(e.value)
+    for a, b in zip(before, g.get_pops()):
+        assert np.array_equal(a, b)
+
+
 def test_error_statuses(lbgpu):
     lb = lbgpu
     with pytest.raises(lb.LBError) as e:

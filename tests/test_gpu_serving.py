@@ -76,6 +76,33 @@ def test_alone_equals_mix(lbgpu, store, policy):
         assert res["t_submit"] <= res["t_admit"] <= res["t_done"]
 
 
+def test_table_growth_recaptures_the_graph(lbgpu):
+    """The server replays a captured graph of its batched launches, which
+    holds the device tables' addresses.  When the request table outgrows its
+    capacity (64) while the tile table does not, both tables are
+    reallocated, and the next pump must capture a new graph.  Seventy
+    one-tile requests join after three pumps of the first one; every result
+    equals the request's solo run."""
+    lb = lbgpu
+    small = dict(nx=16, ny=16, bcy=1, dt=0.2, amp=1e-2, **{**RB, "tau": 0.1, "tau_g": 0.1})
+    s = lb.Server(store="f32", thermal=True, steps_per_launch=2)
+    s.submit(rid=0, nsteps=40, seed=100, **small)
+    out = {}
+    for _ in range(3):  # plain launches, a captured graph, a replay
+        s.pump()
+        out.update({r["id"]: r for r in s.results()})
+    for i in range(1, 71):
+        s.submit(rid=i, nsteps=6, seed=100 + i, **small)
+    out.update(_drain(s))
+    assert len(out) == 71 and all(r["status"] == lb.LB_OK for r in out.values())
+    for i in (0, 1, 35, 70):
+        one = lb.Server(store="f32", thermal=True, steps_per_launch=2)
+        one.submit(rid=i, nsteps=40 if i == 0 else 6, seed=100 + i, **small)
+        alone = _drain(one)[i]
+        assert (alone["nu_vol"], alone["nu_bot"], alone["mass"]) == (out[i]["nu_vol"], out[i]["nu_bot"],
+                                                                     out[i]["mass"])
+
+
 def test_admission_waits_for_memory(lbgpu):
     """A budget that holds one request at a time: they run one after another."""
     lb = lbgpu
