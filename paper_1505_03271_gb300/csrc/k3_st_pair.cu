@@ -11,8 +11,7 @@
 // warp's or the row's ends add single stores, wrapping periodically.  Rows
 // next to a wall (half-way bounce-back for f, anti-bounce-back through the
 // plate temperature for g) store value by value.
-#include "lb3.cuh"
-#include "lb_pair.cuh"
+#include "lb3_pair.cuh"
 
 namespace lbgb {
 
@@ -20,66 +19,15 @@ namespace {
 
 using namespace pairmath;
 
-// Moments and equilibria of a pair of cells from deviations d = f - w,
-// e = g - w T0 (the arithmetic of the scalar D3Q19 cell, on pairs).
-template <bool TH>
-struct Cell3P {
-    V2 rp, rho, ux, uy, uz, Td, T, az, uu, ua;
-    __device__ __forceinline__ void moments(const V2* d, const V2* e, const Args3<float>& A) {
-        V2 r = bc(0.0f), jx = bc(0.0f), jy = bc(0.0f), jz = bc(0.0f);
-#pragma unroll
-        for (int a = 0; a < Q3; ++a) {
-            r = r + d[a];
-            if (c3x(a) != 0) jx = c3x(a) > 0 ? jx + d[a] : jx - d[a];
-            if (c3y(a) != 0) jy = c3y(a) > 0 ? jy + d[a] : jy - d[a];
-            if (c3z(a) != 0) jz = c3z(a) > 0 ? jz + d[a] : jz - d[a];
-        }
-        Td = bc(0.0f);
-        if constexpr (TH) {
-#pragma unroll
-            for (int a = 0; a < Q3; ++a) Td = Td + e[a];
-        }
-        rp = r;
-        rho = r + bc(1.0f);
-        T = Td + bc(A.T0);
-        az = TH ? fma2(bc(A.bg), Td, bc(A.az)) : bc(A.az);
-        const V2 ir = mk(__fdividef(1.0f, rho.v.x), __fdividef(1.0f, rho.v.y));
-        ux = fma2(jx, ir, bc(A.hf * A.ax));
-        uy = fma2(jy, ir, bc(A.hf * A.ay));
-        uz = fma2(az, bc(A.hf), jz * ir);
-        uu = fma2(ux, ux, fma2(uy, uy, uz * uz));
-        ua = fma2(ux, bc(A.ax), fma2(uy, bc(A.ay), uz * az));
-    }
-    // post-collision values of population a (f and, if thermal, g)
-    template <int a>
-    __device__ __forceinline__ void post(const V2 d, const V2 e, const Args3<float>& A, V2& pf, V2& pg) const {
-        const float w = w3<float>(a);
-        V2 cu = bc(0.0f), ca = bc(0.0f);
-        if constexpr (c3x(a) != 0) {
-            cu = ux * bc(float(c3x(a)));
-            ca = bc(float(c3x(a)) * A.ax);
-        }
-        if constexpr (c3y(a) != 0) {
-            cu = fma2(uy, bc(float(c3y(a))), cu);
-            ca = ca + bc(float(c3y(a)) * A.ay);
-        }
-        if constexpr (c3z(a) != 0) {
-            cu = fma2(uz, bc(float(c3z(a))), cu);
-            ca = fma2(az, bc(float(c3z(a))), ca);
-        }
-        // 3 c.u + 4.5 (c.u)^2 - 1.5 u.u
-        const V2 poly = fma2(cu, fma2(cu, bc(4.5f), bc(3.0f)), uu * bc(-1.5f));
-        const V2 feqd = (rp + rho * poly) * bc(w);
-        const V2 F = (rho * bc(w)) * fma2(bc(9.0f), cu * ca, (ca - ua) * bc(3.0f));
-        pf = fma2(bc(A.om), feqd - d, fma2(bc(A.cf), F, d));
-        if constexpr (TH) {
-            const V2 geqd = (Td + T * poly) * bc(w);
-            pg = fma2(bc(A.omg), geqd - e, e);
-        } else {
-            pg = bc(0.0f);
-        }
-    }
-};
+// The ST relaxation of population a of the pair: post-collision f (and g).
+template <bool TH, int a>
+__device__ __forceinline__ void post(const Cell3P<TH>& m, const V2 d, const V2 e, const Args3<float>& A, V2& pf,
+                                     V2& pg) {
+    V2 feqd, F, geqd;
+    m.template eq<a>(A, feqd, F, geqd);
+    pf = fma2(bc(A.om), feqd - d, fma2(bc(A.cf), F, d));
+    pg = TH ? fma2(bc(A.omg), geqd - e, e) : bc(0.0f);
+}
 
 __device__ __forceinline__ int wrapi(int v, int n) { return v < 0 ? v + n : (v >= n ? v - n : v); }
 
@@ -168,7 +116,7 @@ __device__ __forceinline__ void do_pop(const Cell3P<TH>& m, const V2* d, const V
                                        float* fo, float* go, bool fast, int i, int j, int k, int lane, bool on,
                                        bool right_on) {
     V2 pf, pg;
-    m.template post<a>(d[a], TH ? e[a] : bc(0.0f), A, pf, pg);
+    post<TH, a>(m, d[a], TH ? e[a] : bc(0.0f), A, pf, pg);
     if (fast) {
         const int jj = wrapi(j + c3y(a), A.n[1]), kk = wrapi(k + c3z(a), A.n[2]);
         const long long base = a * A.N + ((long long)kk * A.n[1] + jj) * A.n[0];

@@ -19,6 +19,10 @@ CASES = [
     # the smallest z extents: every plane is a ghost source (walls need two cells)
     dict(nx=5, ny=4, nz=2, bcx=1, bcz=1),
     dict(nx=7, ny=3, nz=1),
+    # even nx: the paired FP32 collision and star passes, with a partial last
+    # warp in x, and a three-plane thermal grid whose planes all feed ghosts
+    dict(nx=130, ny=5, nz=4, bcy=1),
+    dict(nx=6, ny=4, nz=3, bcz=1, thermal=True),
 ]
 
 
