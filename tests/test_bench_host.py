@@ -97,3 +97,30 @@ def test_oracle_sample_threads_and_cpu_model():
     assert ux.shape == (32, 16) and np.isfinite(ux).all()
     model = bench.cpu_model()
     assert isinstance(model, str) and model
+
+
+def test_st_schedule_names_follow_the_dispatch():
+    """The bench names an ST line by the kernel the library dispatches
+    (lb_step_st: the four-cell kernels on x-periodic flow grids with nx a
+    multiple of 4, FP32 or 16-bit; the pair kernels elsewhere), and the
+    committed traffic entries of the ST lines carry those names."""
+    import types
+    import paper_1505_03271_gb300 as lb
+
+    def grid(store, nx, bcx=lb.LB_BC_PERIODIC, thermal=False):
+        return types.SimpleNamespace(store=store, nx=nx, thermal=thermal, desc=types.SimpleNamespace(bcx=bcx))
+
+    quad32 = "st quad (128-bit words, f32x2), four cells per thread"
+    quad16 = "st quad (64-bit words, f32x2), four cells of two rows per thread"
+    assert bench.schedule_name(lb, grid(lb.LB_STORE_F32, 8192), "st") == quad32
+    assert bench.schedule_name(lb, grid(lb.LB_STORE_F32, 8190), "st") == "st pair (f32x2), two cells per thread"
+    assert bench.schedule_name(lb, grid(lb.LB_STORE_F32, 8192, bcx=lb.LB_BC_WALLS), "st") != quad32
+    assert bench.schedule_name(lb, grid(lb.LB_STORE_F32, 8192, thermal=True), "st") != quad32
+    for store in (lb.LB_STORE_F16DEV, lb.LB_STORE_BF16DEV):
+        assert bench.schedule_name(lb, grid(store, 8192), "st") == quad16
+        assert bench.schedule_name(lb, grid(store, 8190), "st") == "st pair (f32x2), two cells of two rows per thread"
+    assert bench.schedule_name(lb, grid(lb.LB_STORE_F64, 64), "st") == "st push, one thread per cell"
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+        keys = set(json.load(fh))
+    assert quad32 + "|st4096" in keys
+    assert quad16 + "|st4096_f16dev" in keys and quad16 + "|st4096_bf16dev" in keys
